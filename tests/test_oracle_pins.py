@@ -1,0 +1,501 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against a closed form, an invariant, a hand-worked example or a
+brute-force search that does not go through the oracle's own code path, chosen so that a
+dropped term, a wrong sign or index, or a transposed operand in the oracle fails one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import ndimage, optimize
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- pyramid (Sec. 3.1)
+def test_pyr_down_preserves_ramp_in_interior():
+    h, w = 29, 37
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    a, b, c = 3.0, -2.0, 7.0
+    out = oracle.pyr_down(a * x + b * y + c)
+    assert out.shape == (15, 19)
+    yo, xo = np.mgrid[0:15, 0:19].astype(float)
+    ref = a * 2 * xo + b * 2 * yo + c
+    inner = (2 * xo - 2 >= 0) & (2 * xo + 2 <= w - 1) & (2 * yo - 2 >= 0) & (2 * yo + 2 <= h - 1)
+    assert np.abs(out - ref)[inner].max() < 1e-12
+
+
+@pytest.mark.parametrize("pos", [(10, 8), (11, 9)])
+def test_pyr_down_impulse_gives_binomial_weights(pos):
+    # an impulse at (col, row) = pos lands on the even-sampled [1 4 6 4 1]/16 weights
+    img = np.zeros((20, 24))
+    img[pos[1], pos[0]] = 1.0
+    out = oracle.pyr_down(img)
+    k = {-2: 1 / 16, -1: 4 / 16, 0: 6 / 16, 1: 4 / 16, 2: 1 / 16}
+    ref = np.zeros_like(out)
+    for yo in range(out.shape[0]):
+        for xo in range(out.shape[1]):
+            i, j = pos[0] - 2 * xo, pos[1] - 2 * yo
+            if abs(i) <= 2 and abs(j) <= 2:
+                ref[yo, xo] = k[i] * k[j]
+    assert np.abs(out - ref).max() < 1e-15
+    assert abs(out.sum() - (1.0 / 4.0 if pos == (10, 8) else 1.0 / 4.0)) < 1e-15
+
+
+def test_pyr_down_replicated_border_and_sizes():
+    img = np.zeros((7, 9))
+    img[0, 0] = 1.0
+    out = oracle.pyr_down(img)
+    assert out.shape == (4, 5)
+    # offsets -2, -1, 0 all clamp onto pixel 0: weight (1 + 4 + 6) / 16 per axis
+    assert abs(out[0, 0] - (11 / 16) ** 2) < 1e-15
+    const = oracle.pyr_down(np.full((5, 6), 4.25))
+    assert np.abs(const - 4.25).max() < 1e-15 and const.shape == (3, 3)
+
+
+# ---------------------------------------------------------------- gradients
+def test_sobel_ramp_interior_border_and_constant():
+    h, w = 12, 15
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    a, b = 3.0, -2.0
+    gx, gy = oracle.sobel(a * x + b * y + 1.0)
+    assert np.abs(gx[1:-1, 1:-1] - a).max() < 1e-12
+    assert np.abs(gy[1:-1, 1:-1] - b).max() < 1e-12
+    # replicated border: one-sided difference over two pixels -> half the slope
+    assert np.abs(gx[1:-1, 0] - a / 2).max() < 1e-12 and np.abs(gx[1:-1, -1] - a / 2).max() < 1e-12
+    assert np.abs(gy[0, 1:-1] - b / 2).max() < 1e-12
+    cx, cy = oracle.sobel(np.full((6, 5), 9.0))
+    assert np.abs(cx).max() == 0.0 and np.abs(cy).max() == 0.0
+
+
+def test_sobel_exact_on_bilinear_function():
+    h, w = 10, 11
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    gx, gy = oracle.sobel(0.5 + 0.3 * x - 0.7 * y + 0.05 * x * y)
+    assert np.abs(gx[1:-1, 1:-1] - (0.3 + 0.05 * y[1:-1, 1:-1])).max() < 1e-12
+    assert np.abs(gy[1:-1, 1:-1] - (-0.7 + 0.05 * x[1:-1, 1:-1])).max() < 1e-12
+
+
+# ---------------------------------------------------------------- bilinear sampling
+def test_bilinear_exact_and_clamped():
+    h, w = 9, 13
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    f = lambda X, Y: 1.0 + 0.2 * X - 0.4 * Y + 0.03 * X * Y  # noqa: E731
+    img = f(x, y)
+    g = np.random.default_rng(1)
+    for _ in range(200):
+        X, Y = g.uniform(0, w - 1), g.uniform(0, h - 1)
+        assert abs(oracle.bilinear(img, X, Y) - f(X, Y)) < 1e-12
+    # outside the image the coordinate is clamped first
+    assert abs(oracle.bilinear(img, -3.2, 4.5) - f(0, 4.5)) < 1e-12
+    assert abs(oracle.bilinear(img, w + 5.0, h + 1.0) - f(w - 1, h - 1)) < 1e-12
+    assert abs(oracle.bilinear(img, w - 1.0, 2.25) - f(w - 1, 2.25)) < 1e-12
+
+
+# ---------------------------------------------------------------- grid and levels
+def test_stride_reading_and_counts():
+    assert oracle.stride(8, 0.3) == 6 and oracle.stride(8, 0.4) == 5
+    assert oracle.stride(12, 0.75) == 3 and oracle.stride(8, 0.5) == 4
+    assert oracle.stride(8, 0.3, 4) == 4 and oracle.stride(8, 0.99) == 1
+    # 128x96, stride 4: levels 128x96, 64x48, 32x24
+    assert [oracle.grid_n(W, 8, 4) * oracle.grid_n(H, 8, 4) for W, H in [(128, 96), (64, 48), (32, 24)]] == [713, 165, 35]
+    # 1024x436, theta_ps 8, theta_ov 0.3: levels 4, 3, 2
+    assert [oracle.grid_n(W, 8, 6) * oracle.grid_n(H, 8, 6) for W, H in [(64, 28), (128, 55), (256, 109)]] == [55, 189, 774]
+    assert oracle.grid_n(1024, 12, 3) * oracle.grid_n(436, 12, 3) == 339 * 143 == 48477
+    assert oracle.grid_n(7, 8, 4) == 0 and oracle.grid_n(8, 8, 4) == 1
+
+
+@pytest.mark.parametrize("L,ps,st", [(37, 8, 6), (64, 8, 4), (8, 8, 3), (436, 12, 3), (29, 12, 5)])
+def test_grid_covers_every_pixel_and_stays_inside(L, ps, st):
+    n = oracle.grid_n(L, ps, st)
+    pos = [oracle.grid_pos(i, L, ps, st) for i in range(n)]
+    assert pos[0] == 0 and pos[-1] == L - ps
+    assert all(0 <= p <= L - ps for p in pos) and pos == sorted(pos)
+    cover = np.zeros(L, int)
+    for p in pos:
+        cover[p:p + ps] += 1
+    assert cover.min() >= 1
+
+
+def test_paper_values_levels():
+    gv = json.load(open(os.path.join(GOLDEN, "paper_values.json")))
+    for case in gv["theta_ss_examples"]["cases"]:
+        rc, ss, sf = oracle.levels(case["width"], case["height"], oracle.params(patch_size=case["ps"]))
+        assert rc == 0 and ss == case["theta_ss"]
+    p = oracle.params()
+    assert (p.delta, p.gamma, p.alpha) == tuple(gv["delta_gamma_alpha"]["value"])
+    assert p.var_inner == gv["theta_vi"]["value"]
+    # a coarsest level smaller than a patch is lowered (auto) or refused (explicit)
+    assert oracle.levels(64, 20, oracle.params(patch_size=8))[1] == 1
+    assert oracle.levels(64, 20, oracle.params(patch_size=8, coarsest_scale=3))[0] == 4
+    assert oracle.levels(6, 6, oracle.params(patch_size=8))[0] == 4
+
+
+# ---------------------------------------------------------------- inverse search (Sec. 2.1, supp. A)
+def _bilinear_scene(h, w, c, t):
+    """I0 = f(x), I1 = f(x - t) for f = c0 + c1 x + c2 y + c3 x y, with exact gradients."""
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    f = lambda X, Y: c[0] + c[1] * X + c[2] * Y + c[3] * X * Y  # noqa: E731
+    I0, I1 = f(x, y), f(x - t[0], y - t[1])
+    return I0, I1, c[1] + c[3] * y, c[2] + c[3] * x
+
+
+def _patch_index(w, ps, st, px, py):
+    nx = oracle.grid_n(w, ps, st)
+    return (py // st) * nx + (px // st)
+
+
+@pytest.mark.parametrize("ps", [8, 12])
+def test_search_saddle_centred_on_patch_converges_in_one_step(ps):
+    # f = c3 (x - x0)(y - y0) with (x0, y0) the patch centre: mean gradient 0, so the
+    # mean-normalised residual is linear in the error and one update is exact.
+    h = w = 48
+    px = py = 16
+    x0 = y0 = px + (ps - 1) / 2
+    c3, t = 0.8, (1.37, -0.61)
+    c = (c3 * x0 * y0 + 5.0, -c3 * y0, -c3 * x0, c3)
+    I0, I1, gx, gy = _bilinear_scene(h, w, c, t)
+    u, ui, st = oracle.search_level(I0, gx, gy, I1, ps, 16, 1)
+    k = _patch_index(w, ps, 16, px, py)
+    uu = u.reshape(-1, 2)[k]
+    assert np.abs(uu - np.array(t)).max() < 1e-12 and st.reshape(-1)[k] == 0
+
+
+def test_search_off_centre_contracts_by_closed_form_matrix():
+    # delta_{k+1} = M delta_k with M = n H'^-1 gbar gbar^T (error dynamics of the
+    # inverse-compositional step with mean-normalisation on a bilinear image).
+    h = w = 64
+    ps, st_, px, py = 8, 8, 24, 32
+    c = (2.0, 0.4, -0.3, 0.05)
+    t = np.array([0.8, 0.45])
+    I0, I1, gx, gy = _bilinear_scene(h, w, c, t)
+    Y, X = np.mgrid[py:py + ps, px:px + ps].astype(float)
+    G = np.stack([(c[1] + c[3] * Y).ravel(), (c[2] + c[3] * X).ravel()], 1)
+    Hm = G.T @ G
+    gbar = G.mean(0)
+    M = ps * ps * np.linalg.solve(Hm, np.outer(gbar, gbar))
+    k = _patch_index(w, ps, st_, px, py)
+    for iters in range(1, 6):
+        u, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, iters)
+        err = u.reshape(-1, 2)[k] - t
+        ref = np.linalg.matrix_power(M, iters) @ (-t)
+        assert np.abs(err - ref).max() < 1e-11, (iters, err, ref)
+
+
+def test_search_integer_translation_is_fixed_point():
+    g = np.random.default_rng(7)
+    h, w, t = 40, 44, (3, -2)
+    I0 = ndimage.gaussian_filter(g.standard_normal((h, w)), 1.5) * 50 + 100
+    I1 = g.uniform(0, 255, (h, w))
+    I1[max(0, t[1]):h + min(0, t[1]), max(0, t[0]):w + min(0, t[0])] = \
+        I0[max(0, -t[1]):h - max(0, t[1]), max(0, -t[0]):w - max(0, t[0])]
+    gx, gy = oracle.sobel(I0)
+    Uc = np.zeros((h, w, 2))
+    Uc[..., 0], Uc[..., 1] = t
+    u, ui, st = oracle.search_level(I0, gx, gy, I1, 8, 4, 12, Uc=Uc, cscale=1.0)
+    nx, ny = oracle.grid_n(w, 8, 4), oracle.grid_n(h, 8, 4)
+    checked = 0
+    for j in range(ny):
+        for i in range(nx):
+            px, py = oracle.grid_pos(i, w, 8, 4), oracle.grid_pos(j, h, 8, 4)
+            if px + t[0] >= 0 and px + 7 + t[0] <= w - 1 and py + t[1] >= 0 and py + 7 + t[1] <= h - 1:
+                assert np.abs(u[j, i] - t).max() < 1e-9
+                checked += 1
+    assert checked > 20
+
+
+def test_search_matches_brute_force_ssd_minimum():
+    # noise-free sub-pixel translation of a smooth texture, one 8x8 patch in a 16x16 image
+    h = w = 16
+    t = (0.37, -0.61)
+    f = lambda X, Y: 100 + 30 * np.sin(0.35 * X + 0.2) * np.cos(0.28 * Y - 0.4) + 12 * np.sin(0.21 * (X + Y))  # noqa
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    I0, I1 = f(x, y), f(x - t[0], y - t[1])
+    gx, gy = oracle.sobel(I0)
+    u, _, st = oracle.search_level(I0, gx, gy, I1, 8, 4, 300)
+    u_ic = u[1, 1]
+    P = I0[4:12, 4:12]
+    T = P - P.mean()
+    Yp, Xp = np.mgrid[4:12, 4:12].astype(float)
+
+    def ssd(v):
+        wv = ndimage.map_coordinates(I1, [Yp + v[1], Xp + v[0]], order=1, mode="nearest")
+        return float(((wv - wv.mean() - T) ** 2).sum())
+
+    grid = np.arange(-2, 2.0001, 1 / 16)
+    vals = np.array([[ssd((a, b)) for a in grid] for b in grid])
+    jb, ib = np.unravel_index(np.argmin(vals), vals.shape)
+    res = optimize.minimize(ssd, [grid[ib], grid[jb]], method="Nelder-Mead",
+                            options=dict(xatol=1e-7, fatol=1e-12, maxiter=4000))
+    assert np.abs(u_ic - res.x).max() < 5e-3, (u_ic, res.x)
+    assert np.abs(u_ic - np.array(t)).max() < 2e-2
+
+
+@pytest.mark.parametrize("tx,expect_reset", [(7.0, False), (9.0, True)])
+def test_search_outlier_reset_threshold(tx, expect_reset):
+    # converges to t on a saddle-dominated bilinear image; |t| > theta_ps resets to u_init
+    h = w = 72
+    ps, px, py = 8, 32, 32
+    x0 = y0 = px + 3.5
+    c = (0.6 * x0 * y0 + 3.0, -0.6 * y0 + 0.1, -0.6 * x0, 0.6)
+    t = (tx, 0.0)
+    I0, I1, gx, gy = _bilinear_scene(h, w, c, t)
+    u, ui, st = oracle.search_level(I0, gx, gy, I1, ps, 8, 400)
+    k = _patch_index(w, ps, 8, px, py)
+    if expect_reset:
+        assert st.reshape(-1)[k] == 1 and np.abs(u.reshape(-1, 2)[k]).max() == 0.0
+    else:
+        assert st.reshape(-1)[k] == 0 and np.abs(u.reshape(-1, 2)[k] - t).max() < 1e-9
+
+
+def test_search_init_from_coarser_level_and_flat_patches():
+    # theta_it = 0 exposes u_init = 2 U_{s+1}(c / 2) at the patch centre c = p + (ps - 1)/2
+    h, w, ps, st_ = 40, 52, 8, 4
+    hc, wc = 20, 26
+    yc, xc = np.mgrid[0:hc, 0:wc].astype(float)
+    Uc = np.stack([0.1 * xc - 0.05 * yc + 0.3, -0.02 * xc + 0.07 * yc - 0.2], -1)
+    g = np.random.default_rng(3)
+    I0 = g.uniform(0, 255, (h, w))
+    gx, gy = oracle.sobel(I0)
+    u, ui, st = oracle.search_level(I0, gx, gy, I0, ps, st_, 0, Uc=Uc, cscale=2.0)
+    for j in range(ui.shape[0]):
+        for i in range(ui.shape[1]):
+            cx = oracle.grid_pos(i, w, ps, st_) + 3.5
+            cy = oracle.grid_pos(j, h, ps, st_) + 3.5
+            ref = 2 * np.array([0.1 * cx / 2 - 0.05 * cy / 2 + 0.3, -0.02 * cx / 2 + 0.07 * cy / 2 - 0.2])
+            assert np.abs(ui[j, i] - ref).max() < 1e-12
+    assert np.array_equal(u, ui)
+    flat = np.full((h, w), 77.0)
+    fx, fy = oracle.sobel(flat)
+    u2, ui2, st2 = oracle.search_level(flat, fx, fy, I0, ps, st_, 10, Uc=Uc)
+    assert (st2 == 2).all() and np.array_equal(u2, ui2)
+
+
+# ---------------------------------------------------------------- densification (Eq. 3)
+def test_densify_constant_patch_flow_is_reproduced():
+    g = np.random.default_rng(5)
+    I0, I1 = g.uniform(0, 255, (30, 41)), g.uniform(0, 255, (30, 41))
+    ps, st_ = 8, 3
+    nx, ny = oracle.grid_n(41, ps, st_), oracle.grid_n(30, ps, st_)
+    u = np.tile(np.array([1.25, -0.5]), (ny, nx, 1))
+    U = oracle.densify_level(I0, I1, u, ps, st_)
+    assert np.abs(U - np.array([1.25, -0.5])).max() < 1e-12
+
+
+def test_densify_without_overlap_copies_patch_flow():
+    g = np.random.default_rng(6)
+    I0, I1 = g.uniform(0, 255, (16, 24)), g.uniform(0, 255, (16, 24))
+    u = g.uniform(-3, 3, (2, 3, 2))
+    U = oracle.densify_level(I0, I1, u, 8, 8)
+    ref = np.repeat(np.repeat(u, 8, 0), 8, 1)
+    assert np.abs(U - ref).max() < 1e-12
+
+
+def test_densify_two_patch_hand_example():
+    # 12x8 image, theta_ps 8, stride 4: patches at x = 0 and x = 4, both covering x = 4..7.
+    # I0 = 0; I1 varies along x.  At x = 5: d_0 = I1(6) = -3 for u_0 = (1, 0) and
+    # d_1 = I1(5) = 0.5 for u_1 = (0, 0): weights 1/3 and 1 -> U = (1/3) / (4/3) = 0.25.
+    I0 = np.zeros((8, 12))
+    row = np.array([0, 0, 0, 0, 0.25, 0.5, -3.0, 2.0, 0.0, 0, 0, 0])
+    I1 = np.tile(row, (8, 1))
+    u = np.array([[[1.0, 0.0], [0.0, 0.0]]])
+    U = oracle.densify_level(I0, I1, u, 8, 4)
+    assert abs(U[3, 5, 0] - 0.25) < 1e-15 and U[3, 5, 1] == 0.0
+    # x = 4: d_0 = I1(5) = 0.5, d_1 = I1(4) = 0.25 -> both weights 1 -> 0.5
+    assert abs(U[3, 4, 0] - 0.5) < 1e-15
+    # x = 6: d_0 = I1(7) = 2 -> 1/2, d_1 = I1(6) = -3 -> 1/3 -> (1/2) / (5/6) = 0.6
+    assert abs(U[3, 6, 0] - 0.6) < 1e-15
+    # x = 2: only patch 0; x = 10: only patch 1
+    assert U[0, 2, 0] == 1.0 and U[0, 10, 0] == 0.0
+
+
+# ---------------------------------------------------------------- refinement (Sec. 2.3)
+def test_refine_two_pixel_hand_sweep():
+    # delta = gamma = 0: pure smoothing.  2x1 image, U = [(1,0), (0,0)], both pixels have
+    # |grad u|^2 = 1/4 so equal weights w.  Red pixel 0: d = (0 - 1) -> dU0 = -omega;
+    # black pixel 1: d = 1 - omega - 0 -> dU1 = omega (1 - omega).
+    I = np.zeros((1, 2))
+    U = np.array([[[1.0, 0.0], [0.0, 0.0]]])
+    om = 1.6
+    out = oracle.refine_level(I, I, U, 1, 1, delta=0.0, gamma=0.0, alpha=10.0, omega=om)
+    assert abs(out[0, 0, 0] - (1 - om)) < 1e-14 and abs(out[0, 1, 0] - om * (1 - om)) < 1e-14
+    # the same along y (1x2 image) with the v component
+    Uy = np.array([[[0.0, 1.0]], [[0.0, 0.0]]])
+    outy = oracle.refine_level(I.T.copy(), I.T.copy(), Uy, 1, 1, delta=0.0, gamma=0.0, alpha=3.0, omega=om)
+    assert abs(outy[0, 0, 1] - (1 - om)) < 1e-14 and abs(outy[1, 0, 1] - om * (1 - om)) < 1e-14
+
+
+def test_refine_three_pixel_hand_sweep_unequal_weights():
+    # 3x1, U = [(1,0), (0,0), (0,0)]: central differences give |grad u|^2 = 1/4 at pixels 0
+    # and 1 and 0 at pixel 2, so psi_S = alpha / (2 sqrt(E_S + eps^2)) is a, a, b.
+    # Red (0, 2) first: pixel 0 -> d = -1, pixel 2 -> d = 0.  Black pixel 1 with edge weights
+    # w01 = a and w12 = (a + b)/2:  d = w01 (1 - omega) / (w01 + w12).
+    alpha, om, eps = 10.0, 1.6, 1e-3
+    a = alpha / (2 * math.sqrt(0.25 + eps * eps))
+    b = alpha / (2 * eps)
+    I = np.zeros((1, 3))
+    U = np.array([[[1.0, 0.0], [0.0, 0.0], [0.0, 0.0]]])
+    out = oracle.refine_level(I, I, U, 1, 1, delta=0.0, gamma=0.0, alpha=alpha, omega=om)
+    d1 = a * (1 - om) / (a + 0.5 * (a + b))
+    assert abs(out[0, 0, 0] - (1 - om)) < 1e-14
+    assert abs(out[0, 1, 0] - om * d1) < 1e-14 and abs(out[0, 2, 0]) < 1e-14
+
+
+def test_refine_pure_smoothing_invariants():
+    g = np.random.default_rng(11)
+    I0, I1 = g.uniform(0, 255, (14, 17)), g.uniform(0, 255, (14, 17))
+    U = np.tile(np.array([0.7, -1.1]), (14, 17, 1))
+    out = oracle.refine_level(I0, I1, U, 3, 5, delta=0.0, gamma=0.0)
+    assert np.abs(out - U).max() < 1e-13
+    U2 = g.uniform(-1, 1, (14, 17, 2))
+    out2 = oracle.refine_level(I0, I1, U2, 40, 10, delta=0.0, gamma=0.0, omega=1.0)
+    assert (out2.max((0, 1)) - out2.min((0, 1))).max() < 1e-3 < (U2.max((0, 1)) - U2.min((0, 1))).min()
+
+
+def test_refine_zero_residual_is_fixed_point():
+    g = np.random.default_rng(12)
+    I0 = ndimage.gaussian_filter(g.uniform(0, 255, (20, 23)), 1.0)
+    U = np.zeros((20, 23, 2))
+    out = oracle.refine_level(I0, I0, U, 2, 5)
+    assert np.abs(out).max() < 1e-13
+
+
+def _ramp_pair(h, w, a, b, t):
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    return a * x + b * y, a * (x - t[0]) + b * (y - t[1])
+
+
+def test_refine_brightness_term_recovers_translation():
+    # two channels with independent ramp directions translated by t: the brightness term
+    # (one Psi over the channel sum) has full rank and its minimiser is t itself; the
+    # gradient term vanishes on ramps.
+    h = w = 40
+    t = (0.7, -0.4)
+    c0 = _ramp_pair(h, w, 3.0, -2.0, t)
+    c1 = _ramp_pair(h, w, 1.0, 2.5, t)
+    I0, I1 = np.stack([c0[0], c1[0]]), np.stack([c0[1], c1[1]])
+    out = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 80, delta=5.0, gamma=10.0, alpha=1e-4)
+    assert np.abs(out[15:25, 15:25] - np.array(t)).max() < 1e-8
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_refine_gradient_term_recovers_translation_of_quadratic(axis):
+    # I0 = q^2, I1 = (q - t)^2 along one axis q: I_qq = 2, I_qz = -2t, so the gradient
+    # constancy term alone gives the displacement t along that axis.
+    h = w = 36
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    q = x if axis == 0 else y
+    t = 0.35
+    I0, I1 = 0.2 * q ** 2, 0.2 * (q - t) ** 2
+    out = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 80, delta=0.0, gamma=10.0, alpha=1e-4)
+    ref = np.zeros(2)
+    ref[axis] = t
+    assert np.abs(out[12:24, 12:24] - ref).max() < 1e-8
+
+
+def test_refine_brightness_term_exact_on_quadratics():
+    # Ibar = (I0 + I1w) / 2 makes the brightness linearisation exact for quadratics:
+    # I0 = a q^2, I1 = a (q - t)^2 gives I_q = a (2q - t), I_z = -a t (2q - t) -> d = t.
+    h = w = 36
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    t = (0.35, -0.25)
+    I0 = np.stack([0.2 * x ** 2, 0.3 * y ** 2])
+    I1 = np.stack([0.2 * (x - t[0]) ** 2, 0.3 * (y - t[1]) ** 2])
+    out = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 80, delta=5.0, gamma=0.0, alpha=1e-4)
+    assert np.abs(out[12:24, 12:24] - np.array(t)).max() < 1e-8
+
+
+def test_refine_both_terms_on_diagonal_quadratics():
+    # channels a (x + y)^2 and b (x - y)^2 moved by t: every second derivative (I_xy too) is
+    # non-zero, both data terms fix du + dv and du - dv, so the minimiser is t.
+    h = w = 40
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    t = (0.3, -0.45)
+    I0 = np.stack([0.05 * (x + y) ** 2, 0.08 * (x - y) ** 2])
+    I1 = np.stack([0.05 * (x - t[0] + y - t[1]) ** 2, 0.08 * (x - t[0] - y + t[1]) ** 2])
+    out = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 100, delta=5.0, gamma=10.0, alpha=1e-4)
+    assert np.abs(out[14:26, 14:26] - np.array(t)).max() < 1e-8
+    g_only = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 100, delta=0.0, gamma=10.0, alpha=1e-4)
+    assert np.abs(g_only[14:26, 14:26] - np.array(t)).max() < 1e-8
+
+
+def test_refine_beta_normalisation_balances_channels():
+    # two channels with opposite-consistent ramps of slopes a1, a2 moving by t1, t2 along x:
+    # the brightness term's minimiser is sum_c beta_c a_c^2 t_c / sum_c beta_c a_c^2 with
+    # beta_c = 1 / (a_c^2 + 0.01); a third flat channel adds nothing.
+    h = w = 30
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    a1, a2, t1, t2 = 1.0, 5.0, 0.2, 0.6
+    I0 = np.stack([a1 * x, a2 * x, np.full((h, w), 9.0)])
+    I1 = np.stack([a1 * (x - t1), a2 * (x - t2), np.full((h, w), 9.0)])
+    out = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 80, delta=5.0, gamma=0.0, alpha=1e-4)
+    b1, b2 = 1 / (a1 ** 2 + 0.01), 1 / (a2 ** 2 + 0.01)
+    ref = (b1 * a1 ** 2 * t1 + b2 * a2 ** 2 * t2) / (b1 * a1 ** 2 + b2 * a2 ** 2)
+    assert np.abs(out[10:20, 10:20, 0] - ref).max() < 1e-8
+    assert np.abs(out[10:20, 10:20, 1]).max() < 1e-8
+
+
+def test_refine_gradient_term_beta_normalisation():
+    h = w = 30
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    a1, a2, t1, t2 = 0.1, 2.0, 0.3, -0.2
+    I0 = np.stack([a1 * x ** 2, a2 * x ** 2])
+    I1 = np.stack([a1 * (x - t1) ** 2, a2 * (x - t2) ** 2])
+    out = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 120, delta=0.0, gamma=10.0, alpha=1e-5)
+    # per channel I_xx = 2 a_c, I_xy = 0, I_xz = -2 a_c t_c: beta_x = 1 / (4 a_c^2 + 0.01)
+    wts = [(2 * a) ** 2 / ((2 * a) ** 2 + 0.01) for a in (a1, a2)]
+    ref = (wts[0] * t1 + wts[1] * t2) / (wts[0] + wts[1])
+    assert np.abs(out[10:20, 10:20, 0] - ref).max() < 1e-7
+
+
+# ---------------------------------------------------------------- up-scaling and pipeline
+def test_upsample_linear_field():
+    hi, wi = 7, 9
+    y, x = np.mgrid[0:hi, 0:wi].astype(float)
+    U = np.stack([0.5 * x - 0.25 * y + 1.0, 0.1 * x + 0.2 * y - 0.3], -1)
+    out = oracle.upsample_flow(U, 2.0, (13, 17))
+    yo, xo = np.mgrid[0:13, 0:17].astype(float)
+    ref = np.stack([0.5 * xo - 0.25 * yo + 2.0, 0.1 * xo + 0.2 * yo - 0.6], -1)
+    assert np.abs(out - ref).max() < 1e-12
+    assert np.array_equal(oracle.upsample_flow(U, 1.0, (hi, wi)), U)
+
+
+def test_pipeline_recovers_translation_of_saddle_image():
+    # bilinear (saddle) scene: every pyramid level stays bilinear in its interior, interior
+    # patches contract exactly onto t / 2^s, so interior pixels of the final flow equal t.
+    h = w = 48
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    t = (1.3, -0.7)
+    f = lambda X, Y: 0.5 * (X - 23.5) * (Y - 23.5) + 100.0  # noqa: E731
+    I0, I1 = f(x, y), f(x - t[0], y - t[1])
+    p = oracle.params(patch_size=8, stride_override=4, grad_iters=5000, coarsest_scale=1, refine=0,
+                      intensity_scale=1.0)
+    flow = oracle.dis_flow(I0, I1, p)
+    assert np.abs(flow[12:36, 12:36] - np.array(t)).max() < 1e-6
+
+
+def test_pipeline_translation_sanity_and_frozen_replay():
+    from paper_1603_03590_gb300 import synth
+    I0, I1, gt = synth.translation_pair(0)
+    p = oracle.params(patch_size=8, stride_override=4, grad_iters=16, coarsest_scale=2, var_outer=1)
+    flow, rec, hv = oracle.dis_flow(I0, I1, p, record=True, want_hash=True)
+    epe = np.linalg.norm(flow - gt, axis=-1)
+    assert epe[8:-8, 8:-8].mean() < 0.1
+    assert rec.shape == (oracle.total_patches(128, 96, p), 2) == (713 + 165 + 35, 2)
+    again, hv2 = oracle.dis_flow(I0, I1, p, frozen=rec, want_hash=True)
+    assert np.abs(again - flow).max() < 1e-12
+    flow3, hv3 = oracle.dis_flow(I0, I1, p, want_hash=True)
+    assert hv3 == hv and np.array_equal(flow3, flow)
+
+
+def test_charbonnier_loss_closed_forms():
+    g = np.random.default_rng(2)
+    I0 = g.uniform(0, 1, (9, 10))
+    zero = np.zeros((9, 10, 2))
+    assert abs(oracle.charbonnier_loss(I0, I0, zero, 1e-3) - 1e-3) < 1e-15
+    assert abs(oracle.charbonnier_loss(I0, I0 + 0.25, zero, 1e-3) - math.sqrt(0.0625 + 1e-6)) < 1e-12
