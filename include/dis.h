@@ -1,0 +1,193 @@
+/*
+ * dis.h - C ABI of the GB300 (sm_103a) implementation of Dense Inverse Search optical flow
+ * (Kroeger, Timofte, Dai, Van Gool, "Fast Optical Flow using Dense Inverse Search").
+ *
+ * The problem (Sec. 2.1, Eq. 1; Alg. 1): given a reference frame I_t (I0) and a query frame
+ * I_{t+1} (I1), return a dense displacement field U with I1(x + U(x)) ~ I0(x).  U is in
+ * full-resolution pixels, u along x (columns) and v along y (rows), stored interleaved
+ * H x W x 2 float.
+ *
+ * Conventions shared by every entry point:
+ *  - Every image, flow and patch pointer is caller-owned DEVICE memory (cudaMalloc'd or a
+ *    torch CUDA tensor), FP32, row-major.  Images have a row pitch given in elements
+ *    (>= width); colour images are planar C x H x W with planes pitch * H elements apart.
+ *    Flow fields are dense (row pitch = width), interleaved (u, v).
+ *  - Intensities are expected in [0, 1]; internally they are multiplied by
+ *    dis_params.intensity_scale (255) so that the max(1, |d|) rule of Eq. 3 acts on the
+ *    paper's 8-bit scale.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is enqueued
+ *    asynchronously on it; the call returns as soon as it is enqueued.  Host-detectable
+ *    errors (bad arguments, sizes, allocation failure, launch failure) are returned
+ *    immediately and leave every output untouched; device-side failures surface as
+ *    DIS_ERR_CUDA on a later call.
+ *  - Handles are not thread-safe: use one handle per host thread / stream.
+ *  - No entry point throws; no entry point allocates device memory except dis_create.
+ */
+#ifndef DIS_H
+#define DIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dis_status {
+    DIS_OK = 0,
+    DIS_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad parameter */
+    DIS_ERR_OUT_OF_MEMORY = 2, /* device allocation in dis_create failed */
+    DIS_ERR_CUDA = 3,          /* a CUDA call or kernel launch failed */
+    DIS_ERR_TOO_SMALL = 4,     /* the image is smaller than one patch at the coarsest level */
+    DIS_ERR_TIMEOUT = 5,       /* reserved: a bounded device-side wait gave up */
+    DIS_ERR_NOT_SUPPORTED = 6  /* valid request outside what this build implements */
+} dis_status;
+
+/* Parameters of the method (Table 1, Sec. 3.1).  dis_default_params fills the paper's
+ * defaults; `struct_size` must be sizeof(dis_params) (ABI versioning). */
+typedef struct dis_params {
+    uint32_t struct_size;
+    int32_t patch_size;      /* theta_ps, 2..16 */
+    float overlap;           /* theta_ov in [0,1); stride = ps - floor(ov * ps) (>= 1) */
+    int32_t stride_override; /* > 0: patch stride in pixels, overriding theta_ov */
+    int32_t grad_iters;      /* theta_it >= 0: inverse-search iterations per patch */
+    int32_t coarsest_scale;  /* theta_ss; -1: ceil(log2(2 W / (8 theta_ps))) (Sec. 3.1) */
+    int32_t finest_scale;    /* theta_sf >= 0 */
+    int32_t refine;          /* 1: variational refinement on each level (Sec. 2.3) */
+    int32_t var_outer;       /* theta_vo; -1: s + 1 at scale s (Sec. 3.1) */
+    int32_t var_inner;       /* theta_vi: red-black SOR sweeps per outer iteration */
+    float delta, gamma, alpha; /* intensity / gradient / smoothness weights (5, 10, 10) */
+    float sor_omega;         /* SOR over-relaxation, (0, 2) (the paper does not state it: 1.6) */
+    float intensity_scale;   /* 255 */
+    int32_t channels;        /* 1 (grayscale) or 3 (RGB, planar) */
+} dis_params;
+
+/* Presets for dis_default_params.  OP1..OP4 are the paper's operating points
+ * (Sec. 3.3: theta_sf/theta_it/theta_ps/theta_ov = 3/16/8/0.30 without refinement,
+ * 3/12/8/0.40, 1/16/12/0.75, 0/256/12/0.75).  FAST/MEDIUM/DENSE are the workload presets
+ * used by the benchmarks (patch 8 / 30 % / 16 it / finest 2 / no refinement; patch 8 / 50 %
+ * / 32 it / refinement; patch 12 / 75 % / 128 it / refinement). */
+enum {
+    DIS_PRESET_DEFAULT = 0,
+    DIS_PRESET_OP1 = 1,
+    DIS_PRESET_OP2 = 2,
+    DIS_PRESET_OP3 = 3,
+    DIS_PRESET_OP4 = 4,
+    DIS_PRESET_FAST = 5,
+    DIS_PRESET_MEDIUM = 6,
+    DIS_PRESET_DENSE = 7
+};
+
+typedef struct dis_handle dis_handle;
+
+/* One frame pair of a batched call: device pointers, sizes and pitch as for
+ * dis_compute_flow.  Pairs of one call may all differ in size. */
+typedef struct dis_pair {
+    const float* I0;
+    const float* I1;
+    int32_t width;
+    int32_t height;
+    int64_t pitch;   /* row pitch of I0 / I1 in elements */
+    float* flow_out; /* height * width * 2 */
+} dis_pair;
+
+/* Fill `p` with a preset.  Never fails; p == NULL is ignored. */
+void dis_default_params(dis_params* p, int preset);
+
+/* Resolve the pyramid of a W x H frame under `p` (Sec. 3.1 and Alg. 1): coarsest and finest
+ * processed scale, and the number of patches over all processed levels.  Returns
+ * DIS_ERR_TOO_SMALL when the coarsest level cannot hold one patch. */
+dis_status dis_levels(int width, int height, const dis_params* p, int* coarsest, int* finest, int64_t* total_patches);
+
+/* Create a handle owning one device arena (the paper allocates all memory at once,
+ * supplementary Sec. C) large enough for `max_batch` pairs of up to max_w x max_h with
+ * `channels` channels.  Allocates on the current device.  *out is NULL on error. */
+dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int channels);
+
+/* Release the arena, cached CUDA graphs and the handle.  NULL is ignored.  Synchronises
+ * the handle's internal stream first. */
+void dis_destroy(dis_handle* h);
+
+/* Message of the last error on `h` (or of the last handle-less call in this thread when
+ * h == NULL).  Never NULL; valid until the next call on the same handle / thread. */
+const char* dis_last_error_string(const dis_handle* h);
+
+/* Bytes of device memory owned by the handle (the arena). */
+int64_t dis_arena_bytes(const dis_handle* h);
+
+/* Whole method (Alg. 1) on one pair: pyramid, then per level s = theta_ss .. theta_sf:
+ * patch grid, initialisation, inverse search, densification (Eq. 3), variational
+ * refinement; finally bilinear up-scaling to full resolution (Sec. 3.1).
+ * I0 / I1: `channels` planes of hgt x w, row pitch `pitch` elements; flow_out: hgt*w*2.
+ * Requires w <= max_w, hgt <= max_h of the handle and p->channels == handle channels. */
+dis_status dis_compute_flow(dis_handle* h, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                            const dis_params* p, float* flow_out, void* stream);
+
+/* Same as dis_compute_flow, with the differentiable form's extras (not in the paper):
+ *  init_flow   (nullable): replaces the zero flow above the coarsest level (Alg. 1 line 1);
+ *              given at the resolution of level theta_ss, in that level's pixels.
+ *  frozen_in   (nullable): total_patches x 2 per-patch increments u_i - u_init,i, coarsest
+ *              level first, replayed instead of searching (stop-gradient search).
+ *  record_out  (nullable): receives those increments (0 for reset and flat patches).
+ *  checkpoints (nullable): receives the densified flow U_s of every processed level,
+ *              coarsest first, each level's w_s*h_s*2 floats back to back (dis_levels
+ *              gives the sizes); used by dis_backward. */
+dis_status dis_compute_flow_ex(dis_handle* h, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                               const dis_params* p, const float* init_flow, const float* frozen_in,
+                               float* record_out, float* checkpoints, float* flow_out, void* stream);
+
+/* Batched form (not in the paper): n pairs of arbitrary sizes (each within the handle's
+ * max size; n <= max_batch) in one pass.  Every phase (pyramid level, search, densification,
+ * refinement sweep) runs as one persistent kernel over a flattened work list of all pairs,
+ * and the whole call is replayed from a cached CUDA graph when the sizes and parameters
+ * repeat. */
+dis_status dis_compute_flow_batched(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream);
+
+/* ---- per-stage entry points (one pyramid level; used for per-stage parity tests and by
+ * callers that drive the level loop themselves).  No allocation; caller-owned buffers. */
+
+/* Pyramid step (Sec. 3.1, theta_sd = 2): out = even samples of [1 4 6 4 1]/16 separable
+ * blur of `in` (replicated border).  out is ceil(w/2) x ceil(h/2) with pitch out_pitch. */
+dis_status dis_pyr_down(const float* in, int w, int h, int64_t in_pitch, float* out, int64_t out_pitch,
+                        void* stream);
+
+/* Image gradients (Sec. 3.1 "image pyramid including image gradients"): 3x3 Sobel / 8 with
+ * replicated border; gx along x, gy along y, both with pitch out_pitch. */
+dis_status dis_sobel(const float* in, int w, int h, int64_t pitch, float* gx, float* gy, int64_t out_pitch,
+                     void* stream);
+
+/* Steps 1-3 of Alg. 1 on one level (Sec. 2.1, supplementary Sec. A): for every patch of the
+ * grid (row-major), u_init = cscale * Uc(c / cscale) at the patch centre c (Uc NULL: zero;
+ * cscale = theta_sd = 2 for the coarser level's flow), theta_it inverse-compositional
+ * updates with mean-normalised patches, then the outlier reset |u - u_init| > theta_ps.
+ * I0, I1: search images of the level, 0..255 scale, row pitch `pitch`; the Sobel gradients
+ * of I0 are computed inside.  u_out / uinit_out: nx*ny*2; status_out: nx*ny ints
+ * (0 ok, 1 reset, 2 flat).  uinit_out and status_out are nullable. */
+dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
+                            int hc, float cscale, int ps, int stride, int iters, float* u_out, float* uinit_out,
+                            int* status_out, void* stream);
+
+/* Step 4 of Alg. 1 (Eq. 3): U(x) = sum_i w_i(x) u_i / sum_i w_i(x) over the patches covering
+ * x, w_i(x) = 1 / max(1, |I1(x + u_i) - I0(x)|).  u: nx*ny*2 patch flows; U_out: w*h*2.
+ * Uc / cscale give the fallback for uncovered pixels as in dis_search_level. */
+dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* u, int ps,
+                             int stride, const float* Uc, int wc, int hc, float cscale, float* U_out, void* stream);
+
+/* Step 5 of Alg. 1 (Sec. 2.3): `outer` lagged-nonlinearity iterations of `inner` red-black
+ * SOR sweeps on the intensity + gradient + smoothness energy; U (w*h*2) is refined in place.
+ * I0 / I1: `channels` planes each, 0..255 scale, row pitch `pitch`, planes pitch*h apart.
+ * Uses the handle's arena as scratch (w, h within its max size). */
+dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
+                            int channels, float* U, int outer, int inner, float delta, float gamma, float alpha,
+                            float omega, void* stream);
+
+/* Up-scaling (Sec. 3.1, last paragraph): Uout(x) = factor * Uin(x / factor), bilinear with
+ * clamping.  Uin: wi*hi*2, Uout: wo*ho*2. */
+dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, float* Uout, int wo, int ho,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIS_H */

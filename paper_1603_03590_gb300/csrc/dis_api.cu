@@ -1,0 +1,789 @@
+// Host side of the DIS library: parameter validation, level arithmetic, the device arena,
+// the per-call plan (job tables for every phase), CUDA-graph caching, and the C ABI
+// declared in include/dis.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dis.h"
+#include "dis_internal.cuh"
+
+using dis::Jobs;
+using dis::LevelJob;
+using dis::PrepJob;
+using dis::PyrJob;
+using dis::UpJob;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+constexpr int kMaxPatch = 16;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int pitch_of(int w) { return (w + 31) / 32 * 32; }
+int level_dim(int d, int s)
+{
+    for (int i = 0; i < s; ++i) d = (d + 1) / 2;
+    return d;
+}
+
+// ---- parameters -------------------------------------------------------------------------
+struct Resolved {
+    int ps, stride, iters, ss, sf, refine, inner, outer_fixed, C;
+    float delta, gamma, alpha, omega, scale;
+};
+
+bool finite(float v) { return std::isfinite(v); }
+
+// stride = ps - floor(ov * ps) (Alg. 1 step 1: the overlap is floored to whole pixels).  The
+// product ov * ps is formed in double from the float parameter, with a 1e-4 guard so that a
+// decimal overlap such as 0.7 (0.69999999 in float) floors like its decimal value.
+int stride_of(const dis_params& p)
+{
+    if (p.stride_override > 0) return p.stride_override;
+    const int ov = (int)std::floor((double)p.overlap * (double)p.patch_size + 1e-4);
+    return std::max(1, p.patch_size - ov);
+}
+
+dis_status validate(const dis_params* p, std::string& err)
+{
+    if (!p) {
+        err = "params is NULL";
+        return DIS_ERR_INVALID_ARG;
+    }
+    if (p->struct_size != sizeof(dis_params)) {
+        err = "params.struct_size != sizeof(dis_params) (call dis_default_params first)";
+        return DIS_ERR_INVALID_ARG;
+    }
+    if (p->patch_size < 2 || p->patch_size > kMaxPatch) {
+        err = "patch_size must be in [2, 16]";
+        return DIS_ERR_INVALID_ARG;
+    }
+    if (!(p->overlap >= 0.0f && p->overlap < 1.0f)) {
+        err = "overlap must be in [0, 1)";
+        return DIS_ERR_INVALID_ARG;
+    }
+    if (p->stride_override < 0 || p->grad_iters < 0 || p->grad_iters > (1 << 24) || p->finest_scale < 0 ||
+        p->finest_scale > 30 || p->coarsest_scale < -1 || p->coarsest_scale > 30 || p->var_inner < 0 ||
+        p->var_inner > (1 << 16) || p->var_outer < -1 || p->var_outer > (1 << 16)) {
+        err = "an iteration count, scale or stride is out of range";
+        return DIS_ERR_INVALID_ARG;
+    }
+    if (p->channels != 1 && p->channels != 3) {
+        err = "channels must be 1 or 3";
+        return DIS_ERR_INVALID_ARG;
+    }
+    if (!finite(p->delta) || !finite(p->gamma) || !finite(p->alpha) || p->delta < 0 || p->gamma < 0 ||
+        p->alpha < 0 || !(p->sor_omega > 0.0f && p->sor_omega < 2.0f) || !finite(p->intensity_scale) ||
+        p->intensity_scale <= 0.0f) {
+        err = "refinement weights must be finite and >= 0, sor_omega in (0, 2), intensity_scale > 0";
+        return DIS_ERR_INVALID_ARG;
+    }
+    return DIS_OK;
+}
+
+// theta_ss = ceil(log2(2 W / (f theta_ps))), f = 8 (Sec. 3.1), lowered until the coarsest
+// level holds a patch; an explicit theta_ss that cannot hold one is refused.
+dis_status resolve_levels(int W, int H, const dis_params& p, int& ss, int& sf, std::string& err)
+{
+    const int ps = p.patch_size;
+    sf = p.finest_scale;
+    ss = p.coarsest_scale;
+    if (ss < 0) {
+        const double v = 2.0 * (double)W / (8.0 * (double)ps);
+        ss = v <= 1.0 ? 0 : (int)std::ceil(std::log2(v));
+        while (ss > sf && (level_dim(W, ss) < ps || level_dim(H, ss) < ps)) --ss;
+    }
+    if (ss < sf || level_dim(W, ss) < ps || level_dim(H, ss) < ps) {
+        err = "image too small: the coarsest processed level cannot hold one patch";
+        return DIS_ERR_TOO_SMALL;
+    }
+    return DIS_OK;
+}
+
+int grid_n(int L, int ps, int stride) { return L < ps ? 0 : (L - ps + stride - 1) / stride + 1; }
+
+}  // namespace
+
+// ---- handle and arena -------------------------------------------------------------------
+struct dis_handle {
+    int max_w = 0, max_h = 0, max_batch = 0, C = 1, levels = 0, device = 0;
+    char* arena = nullptr;
+    size_t arena_bytes = 0, slot_bytes = 0;
+    std::vector<size_t> off_img, off_U, off_pu, off_pui, off_pst;  // per level, within a slot
+    size_t off_rs = 0;
+    size_t rs_floats = 0;  // capacity of the refinement scratch (floats)
+    char* jobs_dev = nullptr;
+    size_t jobs_bytes = 0;
+    char* jobs_pinned = nullptr;
+    cudaEvent_t jobs_ev = nullptr;
+    bool jobs_valid = false;
+    std::vector<char> jobs_last;
+    cudaStream_t cap_stream = nullptr;
+    struct Graph {
+        std::vector<int64_t> key;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    dis::LaunchCfg lc{};
+    bool use_graphs = true;
+    std::string err = "no error";
+};
+
+namespace {
+
+dis_status fail(dis_handle* h, dis_status st, const std::string& msg)
+{
+    if (h)
+        h->err = msg;
+    else
+        g_err = msg;
+    return st;
+}
+
+dis_status cuda_fail(dis_handle* h, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, DIS_ERR_CUDA, m);
+}
+
+// ---- plan: job tables of every phase of one call ----------------------------------------
+struct PairIn {
+    const float* I0;
+    const float* I1;
+    int w, h;
+    long long pitch;
+    float* flow;
+    const float* init;
+    const float* frozen;
+    float* record;
+    float* ckpt;
+};
+
+struct Phase {
+    enum Kind { PREP, PYR, LEVEL, UP } kind;
+    size_t off;  // byte offset of the table in the job blob
+    int n;
+    long long total, total2, total3;
+    int s;
+};
+
+struct Plan {
+    std::vector<char> blob;
+    std::vector<Phase> phases;
+    std::vector<int64_t> key;
+    bool graphable = true;
+    // checkpoint copies (single pair): per level (dst, src, bytes)
+    struct Copy {
+        int s;
+        void* dst;
+        const void* src;
+        size_t bytes;
+    };
+    std::vector<Copy> copies;
+};
+
+template <class J>
+size_t push_table(std::vector<char>& blob, const std::vector<J>& t)
+{
+    size_t off = align_up(blob.size(), 16);
+    blob.resize(off + sizeof(J) * t.size());
+    if (!t.empty()) std::memcpy(blob.data() + off, t.data(), sizeof(J) * t.size());
+    return off;
+}
+
+dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const dis_params& p, Plan& plan)
+{
+    const int C = p.channels, ps = p.patch_size, stride = stride_of(p);
+    const bool refine = p.refine != 0;
+    const int n = (int)pairs.size();
+    std::vector<int> ss(n), sf(n);
+    int max_ss = 0, fsf = p.finest_scale;
+    for (int i = 0; i < n; ++i) {
+        std::string e;
+        dis_status st = resolve_levels(pairs[i].w, pairs[i].h, p, ss[i], sf[i], e);
+        if (st != DIS_OK) return fail(hd, st, "pair " + std::to_string(i) + ": " + e);
+        if (ss[i] >= hd->levels) return fail(hd, DIS_ERR_INVALID_ARG, "coarsest scale exceeds the handle's pyramid");
+        max_ss = std::max(max_ss, ss[i]);
+    }
+    const bool colour_planes = (C == 3) && refine;
+    const int nplanes = colour_planes ? 2 + 2 * C : 2;
+    plan.blob.clear();
+    plan.phases.clear();
+    plan.copies.clear();
+    plan.key.clear();
+    plan.graphable = true;
+    plan.key.push_back(n);
+    const int32_t* pw = reinterpret_cast<const int32_t*>(&p);
+    for (size_t i = 0; i < sizeof(dis_params) / 4; ++i) plan.key.push_back(pw[i]);
+
+    auto slot = [&](int i) { return hd->arena + (size_t)i * hd->slot_bytes; };
+    auto img = [&](int i, int s) { return reinterpret_cast<float*>(slot(i) + hd->off_img[s]); };
+    auto lw = [&](int i, int s) { return level_dim(pairs[i].w, s); };
+    auto lh = [&](int i, int s) { return level_dim(pairs[i].h, s); };
+    auto Uof = [&](int i, int s) -> float2* {
+        if (s == 0 && sf[i] == 0) return reinterpret_cast<float2*>(pairs[i].flow);
+        return reinterpret_cast<float2*>(slot(i) + hd->off_U[s]);
+    };
+
+    // level 0 preparation
+    {
+        std::vector<PrepJob> t(n);
+        long long base = 0;
+        for (int i = 0; i < n; ++i) {
+            PrepJob& J = t[i];
+            std::memset(&J, 0, sizeof(J));
+            const int w = pairs[i].w, h = pairs[i].h, pit = pitch_of(w);
+            J.I0 = pairs[i].I0;
+            J.I1 = pairs[i].I1;
+            J.in_plane = pairs[i].pitch * (long long)h;
+            J.in_pitch = (int)pairs[i].pitch;
+            J.S0 = img(i, 0);
+            J.S1 = J.S0 + (long long)pit * h;
+            J.P0 = colour_planes ? J.S1 + (long long)pit * h : nullptr;
+            J.P1 = colour_planes ? J.P0 + (long long)C * pit * h : nullptr;
+            J.out_plane = (long long)pit * h;
+            J.out_pitch = pit;
+            J.w = w;
+            J.h = h;
+            J.C = C;
+            J.scale = p.intensity_scale;
+            J.base = base;
+            base += (long long)w * h;
+            plan.key.push_back(w);
+            plan.key.push_back(h);
+            plan.key.push_back(pairs[i].pitch);
+            plan.key.push_back((pairs[i].init ? 1 : 0) | (pairs[i].frozen ? 2 : 0) | (pairs[i].record ? 4 : 0));
+        }
+        plan.phases.push_back({Phase::PREP, push_table(plan.blob, t), n, base, 0, 0, 0});
+    }
+    // pyramid
+    for (int s = 1; s <= max_ss; ++s) {
+        std::vector<PyrJob> t;
+        long long base = 0;
+        for (int i = 0; i < n; ++i) {
+            if (ss[i] < s) continue;
+            PyrJob J;
+            std::memset(&J, 0, sizeof(J));
+            J.win = lw(i, s - 1);
+            J.hin = lh(i, s - 1);
+            J.pin = pitch_of(J.win);
+            J.wout = lw(i, s);
+            J.hout = lh(i, s);
+            J.pout = pitch_of(J.wout);
+            J.in = img(i, s - 1);
+            J.out = img(i, s);
+            J.in_plane = (long long)J.pin * J.hin;
+            J.out_plane = (long long)J.pout * J.hout;
+            J.nplanes = nplanes;
+            J.base = base;
+            base += (long long)nplanes * J.wout * J.hout;
+            t.push_back(J);
+        }
+        plan.phases.push_back({Phase::PYR, push_table(plan.blob, t), (int)t.size(), base, 0, 0, s});
+    }
+    // per-level chain
+    for (int s = max_ss; s >= fsf; --s) {
+        std::vector<LevelJob> t;
+        long long pb = 0, xb = 0, hb = 0;
+        for (int i = 0; i < n; ++i) {
+            if (ss[i] < s) continue;
+            LevelJob J;
+            std::memset(&J, 0, sizeof(J));
+            const int w = lw(i, s), h = lh(i, s), pit = pitch_of(w);
+            J.w = w;
+            J.h = h;
+            J.pitch = pit;
+            J.plane = (long long)pit * h;
+            J.S0 = img(i, s);
+            J.S1 = J.S0 + J.plane;
+            J.P0 = colour_planes ? J.S1 + J.plane : J.S0;
+            J.P1 = colour_planes ? J.P0 + (long long)C * J.plane : J.S1;
+            J.C = C;
+            if (s == ss[i]) {
+                J.Uc = reinterpret_cast<const float2*>(pairs[i].init);
+                J.wc = w;
+                J.hc = h;
+                J.cscale = 1.0f;
+            } else {
+                J.Uc = Uof(i, s + 1);
+                J.wc = lw(i, s + 1);
+                J.hc = lh(i, s + 1);
+                J.cscale = 2.0f;
+            }
+            J.U = Uof(i, s);
+            J.pu = reinterpret_cast<float2*>(slot(i) + hd->off_pu[s]);
+            J.pui = nullptr;
+            J.pst = nullptr;
+            J.nx = grid_n(w, ps, stride);
+            J.ny = grid_n(h, ps, stride);
+            // increments of earlier (coarser) levels come first in frozen / record
+            long long before = 0;
+            for (int q = ss[i]; q > s; --q)
+                before += (long long)grid_n(lw(i, q), ps, stride) * grid_n(lh(i, q), ps, stride);
+            J.frozen = pairs[i].frozen ? reinterpret_cast<const float2*>(pairs[i].frozen) + before : nullptr;
+            J.record = pairs[i].record ? reinterpret_cast<float2*>(pairs[i].record) + before : nullptr;
+            J.rs = reinterpret_cast<float*>(slot(i) + hd->off_rs);
+            J.patch_base = pb;
+            J.pix_base = xb;
+            J.half_base = hb;
+            pb += (long long)J.nx * J.ny;
+            xb += (long long)w * h;
+            hb += (long long)h * ((w + 1) / 2);
+            t.push_back(J);
+            if (pairs[i].ckpt) {
+                long long cb = 0;
+                for (int q = ss[i]; q > s; --q) cb += (long long)lw(i, q) * lh(i, q) * 2;
+                plan.copies.push_back({s, pairs[i].ckpt + cb, J.U, sizeof(float2) * (size_t)w * h});
+                plan.graphable = false;
+            }
+        }
+        plan.phases.push_back({Phase::LEVEL, push_table(plan.blob, t), (int)t.size(), pb, xb, hb, s});
+    }
+    // final up-scaling
+    if (fsf > 0) {
+        std::vector<UpJob> t(n);
+        long long base = 0;
+        for (int i = 0; i < n; ++i) {
+            UpJob& J = t[i];
+            std::memset(&J, 0, sizeof(J));
+            J.in = Uof(i, fsf);
+            J.wi = lw(i, fsf);
+            J.hi = lh(i, fsf);
+            J.out = reinterpret_cast<float2*>(pairs[i].flow);
+            J.wo = pairs[i].w;
+            J.ho = pairs[i].h;
+            J.factor = (float)(1 << fsf);
+            J.base = base;
+            base += (long long)J.wo * J.ho;
+        }
+        plan.phases.push_back({Phase::UP, push_table(plan.blob, t), n, base, 0, 0, fsf});
+    }
+    if (plan.blob.size() > hd->jobs_bytes) return fail(hd, DIS_ERR_INVALID_ARG, "job tables exceed the handle's job region");
+    return DIS_OK;
+}
+
+cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaStream_t s)
+{
+    const int ps = p.patch_size, stride = stride_of(p);
+    cudaError_t e = cudaSuccess;
+    for (const Phase& ph : plan.phases) {
+        const char* tab = hd->jobs_dev + ph.off;
+        switch (ph.kind) {
+            case Phase::PREP:
+                e = dis::launch_prep(dis::device_jobs(reinterpret_cast<const PrepJob*>(tab), ph.n), ph.total, hd->lc, s);
+                break;
+            case Phase::PYR:
+                e = dis::launch_pyr_down(dis::device_jobs(reinterpret_cast<const PyrJob*>(tab), ph.n), ph.total, hd->lc,
+                                         s);
+                break;
+            case Phase::LEVEL: {
+                auto js = dis::device_jobs(reinterpret_cast<const LevelJob*>(tab), ph.n);
+                e = dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s);
+                if (e == cudaSuccess) e = dis::launch_densify(js, ph.total2, ps, stride, hd->lc, s);
+                for (const auto& c : plan.copies)
+                    if (e == cudaSuccess && c.s == ph.s) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess && p.refine) {
+                    dis::RefineArgs a;
+                    a.outer = p.var_outer < 0 ? ph.s + 1 : p.var_outer;
+                    a.inner = p.var_inner;
+                    a.delta = p.delta;
+                    a.gamma = p.gamma;
+                    a.alpha = p.alpha;
+                    a.omega = p.sor_omega;
+                    e = dis::launch_refine(js, ph.total2, ph.total3, a, hd->lc, s);
+                }
+                break;
+            }
+            case Phase::UP:
+                e = dis::launch_upsample(dis::device_jobs(reinterpret_cast<const UpJob*>(tab), ph.n), ph.total, hd->lc, s);
+                break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaStream_t s)
+{
+    cudaError_t e;
+    // upload the job tables when they changed (stream-ordered, from a pinned buffer whose
+    // previous copy has completed)
+    if (!hd->jobs_valid || hd->jobs_last != plan.blob) {
+        if ((e = cudaEventSynchronize(hd->jobs_ev)) != cudaSuccess) return cuda_fail(hd, e, "job upload wait");
+        std::memcpy(hd->jobs_pinned, plan.blob.data(), plan.blob.size());
+        if ((e = cudaMemcpyAsync(hd->jobs_dev, hd->jobs_pinned, plan.blob.size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return cuda_fail(hd, e, "job upload");
+        if ((e = cudaEventRecord(hd->jobs_ev, s)) != cudaSuccess) return cuda_fail(hd, e, "job upload event");
+        hd->jobs_last = plan.blob;
+        hd->jobs_valid = true;
+    }
+    if (!hd->use_graphs || !plan.graphable) {
+        if ((e = record_plan(hd, plan, p, s)) != cudaSuccess) return cuda_fail(hd, e, "kernel launch");
+        return DIS_OK;
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : hd->graphs)
+        if (g.key == plan.key) exec = g.exec;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        if ((e = cudaStreamBeginCapture(hd->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(hd, e, "graph capture begin");
+        cudaError_t le = record_plan(hd, plan, p, hd->cap_stream);
+        e = cudaStreamEndCapture(hd->cap_stream, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(hd, le, "kernel launch (capture)");
+        }
+        if (e != cudaSuccess) return cuda_fail(hd, e, "graph capture end");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(hd, e, "graph instantiate");
+        if (hd->graphs.size() >= 8) {
+            cudaGraphExecDestroy(hd->graphs.front().exec);
+            hd->graphs.erase(hd->graphs.begin());
+        }
+        hd->graphs.push_back({plan.key, exec});
+    }
+    if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(hd, e, "graph launch");
+    return DIS_OK;
+}
+
+dis_status check_pair(dis_handle* hd, const PairIn& q, int idx)
+{
+    const std::string tag = "pair " + std::to_string(idx) + ": ";
+    if (!q.I0 || !q.I1 || !q.flow) return fail(hd, DIS_ERR_INVALID_ARG, tag + "null image or flow pointer");
+    if (q.w < 1 || q.h < 1 || q.w > hd->max_w || q.h > hd->max_h)
+        return fail(hd, DIS_ERR_INVALID_ARG, tag + "size outside [1, handle max]");
+    if (q.pitch < q.w || q.pitch > (1LL << 30)) return fail(hd, DIS_ERR_INVALID_ARG, tag + "pitch < width");
+    return DIS_OK;
+}
+
+}  // namespace
+
+// ---- C ABI ------------------------------------------------------------------------------
+extern "C" {
+
+void dis_default_params(dis_params* p, int preset)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(dis_params);
+    p->patch_size = 8;
+    p->overlap = 0.3f;
+    p->stride_override = 0;
+    p->grad_iters = 16;
+    p->coarsest_scale = -1;
+    p->finest_scale = 0;
+    p->refine = 1;
+    p->var_outer = -1;
+    p->var_inner = 5;
+    p->delta = 5.0f;
+    p->gamma = 10.0f;
+    p->alpha = 10.0f;
+    p->sor_omega = 1.6f;
+    p->intensity_scale = 255.0f;
+    p->channels = 1;
+    switch (preset) {
+        case DIS_PRESET_OP1: p->finest_scale = 3; p->grad_iters = 16; p->patch_size = 8; p->overlap = 0.30f; p->refine = 0; break;
+        case DIS_PRESET_OP2: p->finest_scale = 3; p->grad_iters = 12; p->patch_size = 8; p->overlap = 0.40f; break;
+        case DIS_PRESET_OP3: p->finest_scale = 1; p->grad_iters = 16; p->patch_size = 12; p->overlap = 0.75f; break;
+        case DIS_PRESET_OP4: p->finest_scale = 0; p->grad_iters = 256; p->patch_size = 12; p->overlap = 0.75f; break;
+        case DIS_PRESET_FAST: p->finest_scale = 2; p->grad_iters = 16; p->patch_size = 8; p->overlap = 0.30f; p->refine = 0; break;
+        case DIS_PRESET_MEDIUM: p->finest_scale = 0; p->grad_iters = 32; p->patch_size = 8; p->overlap = 0.50f; break;
+        case DIS_PRESET_DENSE: p->finest_scale = 0; p->grad_iters = 128; p->patch_size = 12; p->overlap = 0.75f; break;
+        default: break;
+    }
+}
+
+dis_status dis_levels(int width, int height, const dis_params* p, int* coarsest, int* finest, int64_t* total_patches)
+{
+    std::string e;
+    dis_status st = validate(p, e);
+    if (st != DIS_OK) return fail(nullptr, st, e);
+    if (width < 1 || height < 1) return fail(nullptr, DIS_ERR_INVALID_ARG, "size must be positive");
+    int ss, sf;
+    if ((st = resolve_levels(width, height, *p, ss, sf, e)) != DIS_OK) return fail(nullptr, st, e);
+    const int stride = stride_of(*p);
+    int64_t tot = 0;
+    for (int s = ss; s >= sf; --s)
+        tot += (int64_t)grid_n(level_dim(width, s), p->patch_size, stride) *
+               grid_n(level_dim(height, s), p->patch_size, stride);
+    if (coarsest) *coarsest = ss;
+    if (finest) *finest = sf;
+    if (total_patches) *total_patches = tot;
+    return DIS_OK;
+}
+
+dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int channels)
+{
+    if (!out) return fail(nullptr, DIS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_w < 1 || max_h < 1 || max_batch < 1 || (channels != 1 && channels != 3) || max_w > (1 << 16) ||
+        max_h > (1 << 16) || max_batch > 4096)
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "invalid handle size");
+    dis_handle* h = new dis_handle();
+    h->max_w = max_w;
+    h->max_h = max_h;
+    h->max_batch = max_batch;
+    h->C = channels;
+    cudaGetDevice(&h->device);
+    // pyramid depth: until both dimensions are 1
+    int L = 1;
+    for (int w = max_w, hh = max_h; w > 1 || hh > 1; w = (w + 1) / 2, hh = (hh + 1) / 2) ++L;
+    h->levels = L;
+    const int nplanes = channels == 3 ? 2 + 2 * channels : 2;
+    size_t off = 0;
+    for (int s = 0; s < L; ++s) {
+        const size_t w = level_dim(max_w, s), hh = level_dim(max_h, s), pit = pitch_of((int)w);
+        h->off_img.push_back(off);
+        off = align_up(off + sizeof(float) * nplanes * pit * hh, kAlign);
+        h->off_U.push_back(off);
+        off = align_up(off + sizeof(float) * 2 * w * hh, kAlign);
+        h->off_pu.push_back(off);
+        off = align_up(off + sizeof(float) * 2 * w * hh, kAlign);
+        h->off_pui.push_back(off);
+        off = align_up(off + sizeof(float) * 2 * w * hh, kAlign);
+        h->off_pst.push_back(off);
+        off = align_up(off + sizeof(int) * w * hh, kAlign);
+    }
+    h->off_rs = off;
+    h->rs_floats = (size_t)dis::rs_planes(channels) * pitch_of(max_w) * max_h;
+    off = align_up(off + sizeof(float) * h->rs_floats, kAlign);
+    h->slot_bytes = off;
+    h->jobs_bytes = align_up((size_t)max_batch * (4 + 2 * L) * 256 + 4096, kAlign);
+    h->arena_bytes = h->slot_bytes * max_batch + h->jobs_bytes;
+    cudaError_t e = cudaMalloc(&h->arena, h->arena_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, DIS_ERR_OUT_OF_MEMORY, std::string("arena allocation failed: ") + cudaGetErrorString(e));
+    }
+    h->jobs_dev = h->arena + h->slot_bytes * max_batch;
+    if ((e = cudaMallocHost(&h->jobs_pinned, h->jobs_bytes)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->jobs_ev, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        dis_destroy(h);
+        return fail(nullptr, DIS_ERR_CUDA, std::string("handle setup failed: ") + cudaGetErrorString(e));
+    }
+    cudaEventRecord(h->jobs_ev, h->cap_stream);
+    h->lc = dis::query_launch_cfg();
+    const char* ng = std::getenv("DIS_NO_GRAPH");
+    h->use_graphs = !(ng && ng[0] == '1');
+    *out = h;
+    return DIS_OK;
+}
+
+void dis_destroy(dis_handle* h)
+{
+    if (!h) return;
+    if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
+    if (h->jobs_ev) cudaEventSynchronize(h->jobs_ev);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    if (h->arena) cudaFree(h->arena);
+    if (h->jobs_pinned) cudaFreeHost(h->jobs_pinned);
+    if (h->jobs_ev) cudaEventDestroy(h->jobs_ev);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+const char* dis_last_error_string(const dis_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int64_t dis_arena_bytes(const dis_handle* h) { return h ? (int64_t)h->arena_bytes : 0; }
+
+dis_status dis_compute_flow_ex(dis_handle* hd, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                               const dis_params* p, const float* init_flow, const float* frozen_in,
+                               float* record_out, float* checkpoints, float* flow_out, void* stream)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    std::string e;
+    dis_status st = validate(p, e);
+    if (st != DIS_OK) return fail(hd, st, e);
+    if (p->channels != hd->C) return fail(hd, DIS_ERR_INVALID_ARG, "params.channels differs from the handle's");
+    PairIn q{I0, I1, w, hgt, pitch, flow_out, init_flow, frozen_in, record_out, checkpoints};
+    if ((st = check_pair(hd, q, 0)) != DIS_OK) return st;
+    Plan plan;
+    if ((st = build_plan(hd, {q}, *p, plan)) != DIS_OK) return st;
+    return run_plan(hd, plan, *p, (cudaStream_t)stream);
+}
+
+dis_status dis_compute_flow(dis_handle* hd, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                            const dis_params* p, float* flow_out, void* stream)
+{
+    return dis_compute_flow_ex(hd, I0, I1, w, hgt, pitch, p, nullptr, nullptr, nullptr, nullptr, flow_out, stream);
+}
+
+dis_status dis_compute_flow_batched(dis_handle* hd, const dis_pair* pairs, int n, const dis_params* p, void* stream)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    std::string e;
+    dis_status st = validate(p, e);
+    if (st != DIS_OK) return fail(hd, st, e);
+    if (p->channels != hd->C) return fail(hd, DIS_ERR_INVALID_ARG, "params.channels differs from the handle's");
+    if (!pairs || n < 1 || n > hd->max_batch) return fail(hd, DIS_ERR_INVALID_ARG, "pairs NULL or n outside [1, max_batch]");
+    std::vector<PairIn> v;
+    v.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        PairIn q{pairs[i].I0, pairs[i].I1, pairs[i].width, pairs[i].height, (long long)pairs[i].pitch,
+                 pairs[i].flow_out, nullptr, nullptr, nullptr, nullptr};
+        if ((st = check_pair(hd, q, i)) != DIS_OK) return st;
+        v.push_back(q);
+    }
+    Plan plan;
+    if ((st = build_plan(hd, v, *p, plan)) != DIS_OK) return st;
+    return run_plan(hd, plan, *p, (cudaStream_t)stream);
+}
+
+// ---- per-stage entry points -------------------------------------------------------------
+static dis::LaunchCfg stage_lc()
+{
+    static thread_local bool init = false;
+    static thread_local dis::LaunchCfg lc;
+    if (!init) {
+        lc = dis::query_launch_cfg();
+        init = true;
+    }
+    return lc;
+}
+
+dis_status dis_pyr_down(const float* in, int w, int h, int64_t in_pitch, float* out, int64_t out_pitch, void* stream)
+{
+    if (!in || !out || w < 1 || h < 1 || in_pitch < w || out_pitch < (w + 1) / 2)
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_pyr_down: bad pointer, size or pitch");
+    PyrJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.in = in;
+    J.out = out;
+    J.win = w;
+    J.hin = h;
+    J.pin = (int)in_pitch;
+    J.wout = (w + 1) / 2;
+    J.hout = (h + 1) / 2;
+    J.pout = (int)out_pitch;
+    J.nplanes = 1;
+    cudaError_t e = dis::launch_pyr_down(dis::single_job(J), (long long)J.wout * J.hout, stage_lc(), (cudaStream_t)stream);
+    return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_pyr_down");
+}
+
+dis_status dis_sobel(const float* in, int w, int h, int64_t pitch, float* gx, float* gy, int64_t out_pitch,
+                     void* stream)
+{
+    if (!in || !gx || !gy || w < 1 || h < 1 || pitch < w || out_pitch < w)
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_sobel: bad pointer, size or pitch");
+    cudaError_t e = dis::launch_sobel(in, w, h, (int)pitch, gx, gy, (int)out_pitch, stage_lc(), (cudaStream_t)stream);
+    return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_sobel");
+}
+
+static bool level_args_ok(int w, int h, int64_t pitch, int ps, int stride, const float* Uc, int wc, int hc, float cscale)
+{
+    if (w < 1 || h < 1 || pitch < w || ps < 2 || ps > kMaxPatch || stride < 1 || w < ps || h < ps) return false;
+    if (Uc && (wc < 1 || hc < 1 || !(cscale > 0.0f))) return false;
+    return true;
+}
+
+dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
+                            int hc, float cscale, int ps, int stride, int iters, float* u_out, float* uinit_out,
+                            int* status_out, void* stream)
+{
+    if (!I0 || !I1 || !u_out || iters < 0 || !level_args_ok(w, h, pitch, ps, stride, Uc, wc, hc, cscale))
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: bad pointer, size, pitch or grid");
+    LevelJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.S0 = I0;
+    J.S1 = I1;
+    J.w = w;
+    J.h = h;
+    J.pitch = (int)pitch;
+    J.Uc = reinterpret_cast<const float2*>(Uc);
+    J.wc = wc;
+    J.hc = hc;
+    J.cscale = cscale;
+    J.pu = reinterpret_cast<float2*>(u_out);
+    J.pui = reinterpret_cast<float2*>(uinit_out);
+    J.pst = status_out;
+    J.nx = grid_n(w, ps, stride);
+    J.ny = grid_n(h, ps, stride);
+    J.C = 1;
+    cudaError_t e = dis::launch_search(dis::single_job(J), (long long)J.nx * J.ny, ps, stride, iters, stage_lc(),
+                                       (cudaStream_t)stream);
+    return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_search_level");
+}
+
+dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* u, int ps,
+                             int stride, const float* Uc, int wc, int hc, float cscale, float* U_out, void* stream)
+{
+    if (!I0 || !I1 || !u || !U_out || !level_args_ok(w, h, pitch, ps, stride, Uc, wc, hc, cscale))
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_densify_level: bad pointer, size, pitch or grid");
+    LevelJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.S0 = I0;
+    J.S1 = I1;
+    J.w = w;
+    J.h = h;
+    J.pitch = (int)pitch;
+    J.Uc = reinterpret_cast<const float2*>(Uc);
+    J.wc = wc;
+    J.hc = hc;
+    J.cscale = cscale;
+    J.pu = reinterpret_cast<float2*>(const_cast<float*>(u));
+    J.U = reinterpret_cast<float2*>(U_out);
+    J.nx = grid_n(w, ps, stride);
+    J.ny = grid_n(h, ps, stride);
+    J.C = 1;
+    cudaError_t e = dis::launch_densify(dis::single_job(J), (long long)w * h, ps, stride, stage_lc(), (cudaStream_t)stream);
+    return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_densify_level");
+}
+
+dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
+                            int channels, float* U, int outer, int inner, float delta, float gamma, float alpha,
+                            float omega, void* stream)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    if (!I0 || !I1 || !U || w < 1 || h < 1 || pitch < w || channels < 1 || channels > 3 || outer < 0 || inner < 0 ||
+        !finite(delta) || !finite(gamma) || !finite(alpha) || !(omega > 0.0f && omega < 2.0f))
+        return fail(hd, DIS_ERR_INVALID_ARG, "dis_refine_level: bad pointer, size, pitch or parameter");
+    if ((size_t)dis::rs_planes(channels) * (size_t)pitch * (size_t)h > hd->rs_floats)
+        return fail(hd, DIS_ERR_INVALID_ARG, "dis_refine_level: level larger than the handle's scratch");
+    LevelJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.P0 = I0;
+    J.P1 = I1;
+    J.w = w;
+    J.h = h;
+    J.pitch = (int)pitch;
+    J.plane = (long long)pitch * h;
+    J.C = channels;
+    J.U = reinterpret_cast<float2*>(U);
+    J.rs = reinterpret_cast<float*>(hd->arena + hd->off_rs);
+    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega};
+    const long long tp = (long long)w * h, th = (long long)h * ((w + 1) / 2);
+    cudaError_t e = dis::launch_refine(dis::single_job(J), tp, th, a, hd->lc, (cudaStream_t)stream);
+    return e == cudaSuccess ? DIS_OK : cuda_fail(hd, e, "dis_refine_level");
+}
+
+dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, float* Uout, int wo, int ho, void* stream)
+{
+    if (!Uin || !Uout || wi < 1 || hi < 1 || wo < 1 || ho < 1 || !(factor > 0.0f) || !finite(factor))
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_upsample_flow: bad pointer, size or factor");
+    UpJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.in = reinterpret_cast<const float2*>(Uin);
+    J.out = reinterpret_cast<float2*>(Uout);
+    J.wi = wi;
+    J.hi = hi;
+    J.wo = wo;
+    J.ho = ho;
+    J.factor = factor;
+    cudaError_t e = dis::launch_upsample(dis::single_job(J), (long long)wo * ho, stage_lc(), (cudaStream_t)stream);
+    return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_upsample_flow");
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal declarations of the DIS CUDA path: job descriptors and kernel launchers.
+//
+// Every kernel works on a flattened list of work items (pixels, patches, same-colour
+// pixels) spanning one or many "jobs" (a frame pair at one pyramid level).  A job list is
+// either a device array (batched form, built once per plan) or one job passed by value in
+// the kernel parameters (single pair, per-stage entry points: no device allocation).
+// Kernels are grid-stride loops, so one persistent launch covers all pairs of a phase.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dis {
+
+// Patch / pyramid / refinement work of one frame pair at one pyramid level.
+struct LevelJob {
+    const float* S0;      // search image of frame t (channel mean), row pitch `pitch`
+    const float* S1;      // search image of frame t+1
+    const float* P0;      // channel planes of frame t (C planes, `plane` floats apart)
+    const float* P1;      // channel planes of frame t+1
+    const float2* Uc;     // flow the patches start from (coarser level or initial flow), or null
+    float2* U;            // dense flow of this level, w*h
+    float2* pu;           // patch flows, nx*ny
+    float2* pui;          // patch initial flows (nullable)
+    int* pst;             // patch status (nullable): 0 ok, 1 reset, 2 flat
+    const float2* frozen; // replayed increments (nullable)
+    float2* record;       // recorded increments (nullable)
+    float* rs;            // refinement scratch: (15 C + 8) planes of `plane` floats
+    long long plane;      // pitch * h
+    long long patch_base; // first flattened patch of this job
+    long long pix_base;   // first flattened pixel
+    long long half_base;  // first flattened same-colour pixel (h * ceil(w/2) per colour)
+    int w, h, pitch;
+    int wc, hc;
+    float cscale;
+    int nx, ny;
+    int C;
+};
+
+// One pyramid step of `nplanes` consecutive planes.
+struct PyrJob {
+    const float* in;
+    float* out;
+    long long in_plane, out_plane;
+    long long base;  // first flattened (plane, output pixel) item
+    int win, hin, pin, wout, hout, pout, nplanes;
+};
+
+// Level-0 preparation: scale the caller's frames, form the channel mean.
+struct PrepJob {
+    const float* I0;
+    const float* I1;
+    long long in_plane;
+    float* S0;
+    float* S1;
+    float* P0;  // null when the channel planes are not needed (C == 1 or no refinement)
+    float* P1;
+    long long out_plane;
+    long long base;
+    int w, h, in_pitch, out_pitch, C;
+    float scale;
+};
+
+// Bilinear up-scaling of a flow field.
+struct UpJob {
+    const float2* in;
+    float2* out;
+    long long base;
+    int wi, hi, wo, ho;
+    float factor;
+};
+
+// A job list: device array (dev != null, n entries) or a single job by value.
+template <class J>
+struct Jobs {
+    const J* dev;
+    J one;
+    int n;
+};
+
+template <class J>
+inline Jobs<J> single_job(const J& j)
+{
+    Jobs<J> r;
+    r.dev = nullptr;
+    r.one = j;
+    r.n = 1;
+    return r;
+}
+
+template <class J>
+inline Jobs<J> device_jobs(const J* dev, int n)
+{
+    Jobs<J> r = {};
+    r.dev = dev;
+    r.n = n;
+    return r;
+}
+
+// Refinement scratch plane indices (per channel c: intermediate, data; then shared planes).
+// Intermediate (6 C): I1w, Ix, Iy, Iz, Ixz, Iyz.  Data (9 C): sqrt(b0)(Ix, Iy, Iz),
+// sqrt(bx)(Ixx, Ixy, Ixz), sqrt(by)(Ixy, Iyy, Iyz).  System (6): A11 A12 A22 b1 b2 psiS.
+// Increment (2): du, dv.
+__host__ __device__ inline int rs_mid(int C, int c, int k) { return c * 6 + k; }
+__host__ __device__ inline int rs_dat(int C, int c, int k) { return 6 * C + c * 9 + k; }
+__host__ __device__ inline int rs_sys(int C, int k) { return 15 * C + k; }
+__host__ __device__ inline int rs_du(int C, int k) { return 15 * C + 6 + k; }
+__host__ __device__ inline int rs_planes(int C) { return 15 * C + 8; }
+
+struct LaunchCfg {
+    int sm_count;
+    int max_blocks_256;  // resident 256-thread blocks per SM for the elementwise kernels
+};
+
+// Launchers (return the launch error).  `total` = number of flattened items.
+cudaError_t launch_prep(const Jobs<PrepJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_sobel(const float* in, int w, int h, int pitch, float* gx, float* gy, int out_pitch,
+                         const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
+                          const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, int stride, const LaunchCfg& lc,
+                           cudaStream_t s);
+struct RefineArgs {
+    int outer, inner;
+    float delta, gamma, alpha, omega;
+};
+cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, const RefineArgs& a,
+                          const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_upsample(const Jobs<UpJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
+
+LaunchCfg query_launch_cfg();
+
+}  // namespace dis

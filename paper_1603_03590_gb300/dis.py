@@ -1,0 +1,196 @@
+"""Python binding of libdis.so (include/dis.h): argument marshalling only.
+
+Every function has the C name and argument order; tensors are passed as device pointers
+(``tensor.data_ptr()``) and the stream as ``torch.cuda.current_stream().cuda_stream`` unless
+given.  All compute runs in the library's CUDA kernels; there is no fallback: importing this
+module raises when libdis.so is missing, and every non-zero status raises DisError with the
+library's message.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdis.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libdis.so is not built (%s); run __graft_entry__.build() or "
+                      "python paper_1603_03590_gb300/build.py" % LIB_PATH)
+_lib = ctypes.CDLL(LIB_PATH)
+
+DIS_OK, DIS_ERR_INVALID_ARG, DIS_ERR_OUT_OF_MEMORY, DIS_ERR_CUDA = 0, 1, 2, 3
+DIS_ERR_TOO_SMALL, DIS_ERR_TIMEOUT, DIS_ERR_NOT_SUPPORTED = 4, 5, 6
+PRESETS = {"default": 0, "op1": 1, "op2": 2, "op3": 3, "op4": 4, "fast": 5, "medium": 6, "dense": 7}
+
+
+class DisError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("dis status %d: %s" % (status, msg))
+        self.status = status
+
+
+class dis_params(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("patch_size", ctypes.c_int32),
+        ("overlap", ctypes.c_float),
+        ("stride_override", ctypes.c_int32),
+        ("grad_iters", ctypes.c_int32),
+        ("coarsest_scale", ctypes.c_int32),
+        ("finest_scale", ctypes.c_int32),
+        ("refine", ctypes.c_int32),
+        ("var_outer", ctypes.c_int32),
+        ("var_inner", ctypes.c_int32),
+        ("delta", ctypes.c_float),
+        ("gamma", ctypes.c_float),
+        ("alpha", ctypes.c_float),
+        ("sor_omega", ctypes.c_float),
+        ("intensity_scale", ctypes.c_float),
+        ("channels", ctypes.c_int32),
+    ]
+
+
+class dis_pair(ctypes.Structure):
+    _fields_ = [
+        ("I0", ctypes.c_void_p),
+        ("I1", ctypes.c_void_p),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("pitch", ctypes.c_int64),
+        ("flow_out", ctypes.c_void_p),
+    ]
+
+
+_vp, _i, _f, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_int64
+_P = ctypes.POINTER(dis_params)
+_SIGS = {
+    "dis_default_params": (None, [_P, _i]),
+    "dis_levels": (_i, [_i, _i, _P, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i64)]),
+    "dis_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i]),
+    "dis_destroy": (None, [_vp]),
+    "dis_last_error_string": (ctypes.c_char_p, [_vp]),
+    "dis_arena_bytes": (_i64, [_vp]),
+    "dis_compute_flow": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp]),
+    "dis_compute_flow_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "dis_compute_flow_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp]),
+    "dis_pyr_down": (_i, [_vp, _i, _i, _i64, _vp, _i64, _vp]),
+    "dis_sobel": (_i, [_vp, _i, _i, _i64, _vp, _vp, _i64, _vp]),
+    "dis_search_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "dis_densify_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _vp, _i, _i, _f, _vp, _vp]),
+    "dis_refine_level": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
+    "dis_upsample_flow": (_i, [_vp, _i, _i, _f, _vp, _i, _i, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def _ptr(t):
+    """Device pointer of a tensor (or None / int passthrough)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status, handle=None):
+    if status != DIS_OK:
+        msg = _lib.dis_last_error_string(handle)
+        raise DisError(status, msg.decode() if msg else "")
+
+
+def dis_default_params(preset="default", **overrides):
+    """dis_params of a preset (name or number) with keyword overrides."""
+    p = dis_params()
+    _lib.dis_default_params(ctypes.byref(p), PRESETS[preset] if isinstance(preset, str) else int(preset))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def dis_levels(width, height, params):
+    ss, sf, tot = _i(), _i(), _i64()
+    _check(_lib.dis_levels(width, height, ctypes.byref(params), ctypes.byref(ss), ctypes.byref(sf), ctypes.byref(tot)))
+    return ss.value, sf.value, tot.value
+
+
+def dis_create(max_w, max_h, max_batch=1, channels=1):
+    h = _vp()
+    _check(_lib.dis_create(ctypes.byref(h), max_w, max_h, max_batch, channels))
+    return h.value
+
+
+def dis_destroy(handle):
+    _lib.dis_destroy(handle)
+
+
+def dis_last_error_string(handle=None):
+    return _lib.dis_last_error_string(handle).decode()
+
+
+def dis_arena_bytes(handle):
+    return _lib.dis_arena_bytes(handle)
+
+
+def dis_compute_flow(handle, I0, I1, w, h, pitch, params, flow_out, stream=None):
+    _check(_lib.dis_compute_flow(handle, _ptr(I0), _ptr(I1), w, h, pitch, ctypes.byref(params), _ptr(flow_out),
+                                 _stream(stream)), handle)
+
+
+def dis_compute_flow_ex(handle, I0, I1, w, h, pitch, params, init_flow, frozen_in, record_out, checkpoints,
+                        flow_out, stream=None):
+    _check(_lib.dis_compute_flow_ex(handle, _ptr(I0), _ptr(I1), w, h, pitch, ctypes.byref(params), _ptr(init_flow),
+                                    _ptr(frozen_in), _ptr(record_out), _ptr(checkpoints), _ptr(flow_out),
+                                    _stream(stream)), handle)
+
+
+def make_pairs(items):
+    """dis_pair array from (I0, I1, width, height, pitch, flow_out) tuples."""
+    arr = (dis_pair * len(items))()
+    for k, (a, b, w, h, pitch, f) in enumerate(items):
+        arr[k].I0, arr[k].I1, arr[k].width, arr[k].height = _ptr(a), _ptr(b), w, h
+        arr[k].pitch, arr[k].flow_out = pitch, _ptr(f)
+    return arr
+
+
+def dis_compute_flow_batched(handle, pairs, n, params, stream=None):
+    _check(_lib.dis_compute_flow_batched(handle, pairs, n, ctypes.byref(params), _stream(stream)), handle)
+
+
+def dis_pyr_down(inp, w, h, in_pitch, out, out_pitch, stream=None):
+    _check(_lib.dis_pyr_down(_ptr(inp), w, h, in_pitch, _ptr(out), out_pitch, _stream(stream)))
+
+
+def dis_sobel(inp, w, h, pitch, gx, gy, out_pitch, stream=None):
+    _check(_lib.dis_sobel(_ptr(inp), w, h, pitch, _ptr(gx), _ptr(gy), out_pitch, _stream(stream)))
+
+
+def dis_search_level(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, u_out, uinit_out=None,
+                     status_out=None, stream=None):
+    _check(_lib.dis_search_level(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(Uc), wc, hc, cscale, ps, stride, iters,
+                                 _ptr(u_out), _ptr(uinit_out), _ptr(status_out), _stream(stream)))
+
+
+def dis_densify_level(I0, I1, w, h, pitch, u, ps, stride, Uc, wc, hc, cscale, U_out, stream=None):
+    _check(_lib.dis_densify_level(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(u), ps, stride, _ptr(Uc), wc, hc, cscale,
+                                  _ptr(U_out), _stream(stream)))
+
+
+def dis_refine_level(handle, I0, I1, w, h, pitch, channels, U, outer, inner, delta=5.0, gamma=10.0, alpha=10.0,
+                     omega=1.6, stream=None):
+    _check(_lib.dis_refine_level(handle, _ptr(I0), _ptr(I1), w, h, pitch, channels, _ptr(U), outer, inner, delta,
+                                 gamma, alpha, omega, _stream(stream)), handle)
+
+
+def dis_upsample_flow(Uin, wi, hi, factor, Uout, wo, ho, stream=None):
+    _check(_lib.dis_upsample_flow(_ptr(Uin), wi, hi, factor, _ptr(Uout), wo, ho, _stream(stream)))

@@ -1,0 +1,111 @@
+"""CPU tests of the C-ABI library: it loads, exports every entry point include/dis.h declares,
+and its host logic (presets, stride and level arithmetic, argument checks) agrees with the
+oracle's readings.  No call here reaches the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dis():
+    from paper_1603_03590_gb300 import build
+    build.build()
+    from paper_1603_03590_gb300 import dis as d
+    return d
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dis.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dis_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(dis):
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(dis.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    src = tmp_path / "t.c"
+    src.write_text('#include "dis.h"\nint main(void){dis_params p; dis_default_params(&p, 0); return p.patch_size != 8;}\n')
+    import subprocess
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-c", str(src), "-I", os.path.join(ROOT, "include"),
+                        "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_presets_match_paper_operating_points(dis):
+    import json
+    gv = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_values.json")))
+    for k, (sf, it, ps, ov) in enumerate(gv["operating_points"]["points"], start=1):
+        p = dis.dis_default_params(k)
+        assert (p.finest_scale, p.grad_iters, p.patch_size) == (sf, it, ps)
+        assert abs(p.overlap - ov) < 1e-6
+        assert p.refine == (0 if k == 1 else 1)
+    p = dis.dis_default_params()
+    assert (p.delta, p.gamma, p.alpha, p.var_inner, p.var_outer) == (5.0, 10.0, 10.0, 5, -1)
+    assert p.struct_size == ctypes.sizeof(dis.dis_params)
+
+
+@pytest.mark.parametrize("W,H", [(1024, 436), (640, 480), (128, 96), (3840, 2160), (320, 240), (1920, 1080),
+                                 (13, 9), (8, 8), (1242, 375), (173, 91)])
+@pytest.mark.parametrize("preset", ["op1", "op2", "op3", "op4", "fast", "medium", "dense"])
+def test_levels_and_patch_counts_match_oracle(dis, W, H, preset):
+    p = dis.dis_default_params(preset)
+    q = oracle.params(patch_size=p.patch_size, overlap=round(p.overlap, 6), grad_iters=p.grad_iters,
+                      finest_scale=p.finest_scale, refine=p.refine)
+    rc, ss, sf = oracle.levels(W, H, q)
+    if rc != 0:
+        with pytest.raises(dis.DisError) as e:
+            dis.dis_levels(W, H, p)
+        assert e.value.status == dis.DIS_ERR_TOO_SMALL
+        return
+    gss, gsf, tot = dis.dis_levels(W, H, p)
+    assert (gss, gsf) == (ss, sf)
+    assert tot == oracle.total_patches(W, H, q)
+
+
+def test_host_side_errors_need_no_gpu(dis):
+    p = dis.dis_default_params()
+    lib = dis._lib
+    assert lib.dis_compute_flow(None, None, None, 8, 8, 8, ctypes.byref(p), None, None) == dis.DIS_ERR_INVALID_ARG
+    assert lib.dis_search_level(None, None, 8, 8, 8, None, 0, 0, 2.0, 8, 4, 4, None, None, None, None) == \
+        dis.DIS_ERR_INVALID_ARG
+    assert "dis_search_level" in dis.dis_last_error_string(None)
+    h = ctypes.c_void_p()
+    assert lib.dis_create(ctypes.byref(h), 0, 10, 1, 1) == dis.DIS_ERR_INVALID_ARG and not h.value
+    assert lib.dis_create(ctypes.byref(h), 10, 10, 1, 2) == dis.DIS_ERR_INVALID_ARG
+    bad = dis.dis_default_params()
+    bad.struct_size = 4
+    with pytest.raises(dis.DisError):
+        dis.dis_levels(100, 100, bad)
+    for field, val in [("patch_size", 1), ("patch_size", 17), ("overlap", 1.0), ("overlap", -0.1), ("sor_omega", 2.0),
+                       ("channels", 2), ("grad_iters", -1), ("alpha", float("nan"))]:
+        q = dis.dis_default_params()
+        setattr(q, field, val)
+        with pytest.raises(dis.DisError) as e:
+            dis.dis_levels(100, 100, q)
+        assert e.value.status == dis.DIS_ERR_INVALID_ARG, field
+    with pytest.raises(dis.DisError) as e:
+        dis.dis_levels(7, 7, dis.dis_default_params(coarsest_scale=0))
+    assert e.value.status == dis.DIS_ERR_TOO_SMALL
+    lib.dis_destroy(None)
+
+
+def test_stride_reading_matches_oracle_for_decimal_overlaps(dis):
+    for ps in range(2, 17):
+        for k in range(0, 100):
+            ov = k / 100.0
+            p = dis.dis_default_params(patch_size=ps, overlap=ov, coarsest_scale=0, finest_scale=0)
+            q = oracle.params(patch_size=ps, overlap=ov, coarsest_scale=0, finest_scale=0)
+            W = H = 64
+            assert dis.dis_levels(W, H, p)[2] == oracle.total_patches(W, H, q), (ps, ov)

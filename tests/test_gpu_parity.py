@@ -1,0 +1,364 @@
+"""GPU-vs-oracle parity through the C ABI.
+
+Per stage, each stage's input is produced on the GPU, widened to FP64 and fed to the oracle's
+stage; the bar is max |du| <= 1e-3 px.  End to end the bar is mean |du| <= 0.01 px and
+99.9th percentile <= 0.05 px.  Discrete decisions (outlier reset, flat patch) taken on
+either side of the threshold by FP32 and FP64 are counted, checked to be borderline in FP64,
+and excluded from the element-wise comparison.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_03590_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+STAGE_TOL = 1e-3        # px, per stage on identical inputs
+E2E_MEAN, E2E_P999 = 0.01, 0.05  # px, end to end
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_03590_gb300 import build
+    build.build()
+    from paper_1603_03590_gb300 import dis
+    return torch, dis, torch.device("cuda:0")
+
+
+def to_dev(torch, a, dev, pitch=None):
+    """(H, W) or (C, H, W) float array -> device tensor view with row pitch `pitch`."""
+    a = np.asarray(a, dtype=np.float32)
+    H, W = a.shape[-2:]
+    pitch = W if pitch is None else pitch
+    buf = torch.zeros(a.shape[:-1] + (pitch,), dtype=torch.float32, device=dev)
+    buf[..., :W] = torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    return buf
+
+
+def host(t, W=None):
+    a = t.detach().cpu().numpy().astype(np.float64)
+    return a if W is None else a[..., :W]
+
+
+def gpu_level_images(torch, dis, dev, I0, I1, levels, scale=255.0):
+    """Scaled level-0 images and `levels` GPU pyramid steps (pitched), as device tensors."""
+    out = []
+    a, b = to_dev(torch, I0 * scale, dev, pitch=I0.shape[1] + 7), to_dev(torch, I1 * scale, dev, pitch=I0.shape[1] + 7)
+    H, W = I0.shape
+    out.append((a, b, W, H, a.shape[-1]))
+    for _ in range(levels):
+        w2, h2 = (W + 1) // 2, (H + 1) // 2
+        pa = torch.zeros((h2, w2 + 3), device=dev)
+        pb = torch.zeros((h2, w2 + 3), device=dev)
+        dis.dis_pyr_down(a, W, H, a.shape[-1], pa, pa.shape[-1])
+        dis.dis_pyr_down(b, W, H, b.shape[-1], pb, pb.shape[-1])
+        a, b, W, H = pa, pb, w2, h2
+        out.append((a, b, W, H, a.shape[-1]))
+    return out
+
+
+# ------------------------------------------------------------------------------ stages
+@pytest.mark.parametrize("H,W", [(96, 128), (91, 173), (436, 1024), (5, 3)])
+def test_pyr_down_and_sobel(env, H, W):
+    torch, dis, dev = env
+    g = np.random.default_rng(H * 1000 + W)
+    img = g.uniform(0, 255, (H, W))
+    a = to_dev(torch, img, dev, pitch=W + 5)
+    w2, h2 = (W + 1) // 2, (H + 1) // 2
+    out = torch.full((h2, w2 + 2), -1.0, device=dev)
+    dis.dis_pyr_down(a, W, H, W + 5, out, w2 + 2)
+    gx = torch.full((H, W + 1), -1.0, device=dev)
+    gy = torch.full((H, W + 1), -1.0, device=dev)
+    dis.dis_sobel(a, W, H, W + 5, gx, gy, W + 1)
+    torch.cuda.synchronize()
+    img32 = host(a, W)
+    np.testing.assert_allclose(host(out, w2), oracle.pyr_down(img32), rtol=0, atol=2e-4)
+    assert (host(out)[:, w2:] == -1.0).all()  # padding untouched
+    ox, oy = oracle.sobel(img32)
+    np.testing.assert_allclose(host(gx, W), ox, rtol=0, atol=2e-4)
+    np.testing.assert_allclose(host(gy, W), oy, rtol=0, atol=2e-4)
+
+
+def _flat_borderline(I0, ps, stride, idx):
+    """FP64 det / (tr/2)^2 of the Hessian of patch idx (for flat-decision checks)."""
+    gx, gy = oracle.sobel(I0)
+    h, w = I0.shape
+    nx = oracle.grid_n(w, ps, stride)
+    j, i = divmod(idx, nx)
+    px, py = oracle.grid_pos(i, w, ps, stride), oracle.grid_pos(j, h, ps, stride)
+    X, Y = gx[py:py + ps, px:px + ps], gy[py:py + ps, px:px + ps]
+    h00, h01, h11 = (X * X).sum(), (X * Y).sum(), (Y * Y).sum()
+    return (h00 * h11 - h01 * h01) / (0.5 * (h00 + h11)) ** 2
+
+
+def compare_search(I0, I1, Uc, cscale, ps, stride, iters, u_g, ui_g, st_g):
+    gx, gy = oracle.sobel(I0)
+    u_o, ui_o, st_o = oracle.search_level(I0, gx, gy, I1, ps, stride, iters, Uc=Uc, cscale=cscale)
+    u_o, ui_o, st_o = u_o.reshape(-1, 2), ui_o.reshape(-1, 2), st_o.reshape(-1)
+    assert np.abs(ui_g - ui_o).max() <= 1e-4
+    differ = np.nonzero(st_g != st_o)[0]
+    for k in differ:
+        if 2 in (st_g[k], st_o[k]):
+            r = _flat_borderline(I0, ps, stride, k)
+            assert abs(r - 1e-6) < 1e-7, ("flat decision not borderline", k, r)
+        else:
+            # one side reset, the other did not: the non-resetting side's distance from
+            # u_init must sit at theta_ps
+            uu, base = (u_g[k], ui_g[k]) if st_g[k] == 0 else (u_o[k], ui_o[k])
+            dist = float(np.hypot(*(uu - base)))
+            assert abs(dist - ps) < 1e-2, ("reset decision not borderline", k, dist)
+    same = st_g == st_o
+    err = np.abs(u_g - u_o)[same]
+    return err.max() if err.size else 0.0, len(differ), u_o
+
+
+@pytest.mark.parametrize("case", ["translate", "layered-dense", "layered-fast", "ragged"])
+def test_search_stage(env, case):
+    torch, dis, dev = env
+    if case == "translate":
+        I0, I1, _ = synth.translation_pair(0)
+        lv, ps, stride, iters = 0, 8, 4, 16
+    elif case == "ragged":
+        I0, I1, _ = synth.layered_pair(11, width=173, height=91, max_disp=6.0)
+        lv, ps, stride, iters = 0, 9, 4, 40
+    else:
+        I0, I1, _ = synth.layered_pair(1000)
+        lv, ps, stride, iters = (2, 12, 3, 128) if case == "layered-dense" else (2, 8, 6, 16)
+    a, b, W, H, pitch = gpu_level_images(torch, dis, dev, I0, I1, lv)[lv]
+    g = np.random.default_rng(5)
+    wc, hc = (W + 1) // 2, (H + 1) // 2
+    Uc_h = (ndimage_smooth(g.normal(0, 1.5, (hc, wc, 2))) * 1.0).astype(np.float32)
+    Uc = torch.from_numpy(Uc_h).to(dev)
+    nx, ny = oracle.grid_n(W, ps, stride), oracle.grid_n(H, ps, stride)
+    u = torch.zeros((ny * nx, 2), device=dev)
+    ui = torch.zeros((ny * nx, 2), device=dev)
+    st = torch.zeros(ny * nx, dtype=torch.int32, device=dev)
+    dis.dis_search_level(a, b, W, H, pitch, Uc, wc, hc, 2.0, ps, stride, iters, u, ui, st)
+    torch.cuda.synchronize()
+    e, ndiff, _ = compare_search(host(a, W), host(b, W), Uc_h.astype(np.float64), 2.0, ps, stride, iters, host(u),
+                                 host(ui), st.cpu().numpy())
+    print("search %s: %d patches, max |du| %.2e, decisions differing %d" % (case, nx * ny, e, ndiff))
+    assert e <= STAGE_TOL
+
+
+def ndimage_smooth(a):
+    from scipy import ndimage
+    return np.stack([ndimage.gaussian_filter(a[..., k], 3.0) for k in range(a.shape[-1])], -1)
+
+
+@pytest.mark.parametrize("case", ["translate", "layered-dense"])
+def test_densify_stage(env, case):
+    torch, dis, dev = env
+    if case == "translate":
+        I0, I1, _ = synth.translation_pair(1)
+        lv, ps, stride, iters = 0, 8, 4, 16
+    else:
+        I0, I1, _ = synth.layered_pair(1001)
+        lv, ps, stride, iters = 1, 12, 3, 64
+    a, b, W, H, pitch = gpu_level_images(torch, dis, dev, I0, I1, lv)[lv]
+    nx, ny = oracle.grid_n(W, ps, stride), oracle.grid_n(H, ps, stride)
+    u = torch.zeros((ny * nx, 2), device=dev)
+    dis.dis_search_level(a, b, W, H, pitch, None, 0, 0, 2.0, ps, stride, iters, u)
+    U = torch.zeros((H, W, 2), device=dev)
+    dis.dis_densify_level(a, b, W, H, pitch, u, ps, stride, None, 0, 0, 2.0, U)
+    torch.cuda.synchronize()
+    Uo = oracle.densify_level(host(a, W), host(b, W), host(u), ps, stride)
+    e = np.abs(host(U) - Uo).max()
+    print("densify %s: max |dU| %.2e" % (case, e))
+    assert e <= STAGE_TOL
+
+
+@pytest.mark.parametrize("case", ["translate", "layered", "rgb", "ragged"])
+def test_refine_stage(env, case):
+    torch, dis, dev = env
+    outer, inner = 2, 5
+    if case == "translate":
+        I0, I1, _ = synth.translation_pair(2)
+        lv = 0
+    elif case == "ragged":
+        I0, I1, _ = synth.layered_pair(12, width=173, height=91, max_disp=6.0)
+        lv, outer, inner = 0, 3, 7
+    elif case == "rgb":
+        I0, I1, _ = synth.layered_pair(13, width=160, height=120, max_disp=8.0, channels=3)
+        lv = 0
+    else:
+        I0, I1, _ = synth.layered_pair(1002)
+        lv, outer = 1, 2
+    C = 1 if I0.ndim == 2 else 3
+    H, W = I0.shape[-2:]
+    Hl, Wl = H, W
+    for _ in range(lv):
+        Wl, Hl = (Wl + 1) // 2, (Hl + 1) // 2
+    # level images built by the oracle's pyramid (inputs only; FP32 on both sides)
+    P0, P1 = [], []
+    for c in range(C):
+        x0 = (I0 if C == 1 else I0[c]) * 255.0
+        x1 = (I1 if C == 1 else I1[c]) * 255.0
+        for _ in range(lv):
+            x0, x1 = oracle.pyr_down(x0), oracle.pyr_down(x1)
+        P0.append(x0)
+        P1.append(x1)
+    P0 = np.stack(P0).astype(np.float32)
+    P1 = np.stack(P1).astype(np.float32)
+    pitch = Wl + 9
+    a, b = to_dev(torch, P0, dev, pitch), to_dev(torch, P1, dev, pitch)
+    g = np.random.default_rng(3)
+    U0 = ndimage_smooth(g.normal(0, 2.0, (Hl, Wl, 2))).astype(np.float32) * 3.0
+    U = torch.from_numpy(U0).to(dev)
+    h = dis.dis_create(W, H, 1, C)
+    try:
+        dis.dis_refine_level(h, a, b, Wl, Hl, pitch, C, U, outer, inner)
+        torch.cuda.synchronize()
+    finally:
+        dis.dis_destroy(h)
+    Uo = oracle.refine_level(P0.astype(np.float64), P1.astype(np.float64), U0.astype(np.float64), outer, inner)
+    e = np.abs(host(U) - Uo).max()
+    print("refine %s: max |dU| %.2e (update magnitude %.2e)" % (case, e, np.abs(Uo - U0).max()))
+    assert e <= STAGE_TOL
+
+
+@pytest.mark.parametrize("factor,src,dst", [(2.0, (55, 128), (109, 256)), (4.0, (28, 64), (109, 256)),
+                                            (1.0, (17, 13), (17, 13))])
+def test_upsample_stage(env, factor, src, dst):
+    torch, dis, dev = env
+    g = np.random.default_rng(9)
+    Uin = g.normal(0, 3, src + (2,)).astype(np.float32)
+    out = torch.zeros(dst + (2,), device=dev)
+    dis.dis_upsample_flow(torch.from_numpy(Uin).to(dev), src[1], src[0], factor, out, dst[1], dst[0])
+    torch.cuda.synchronize()
+    ref = oracle.upsample_flow(Uin.astype(np.float64), factor, dst)
+    assert np.abs(host(out) - ref).max() <= 1e-4
+
+
+# ------------------------------------------------------------------------------ end to end
+def run_gpu(torch, dis, dev, I0, I1, params, pitch_pad=0, init=None, frozen=None, record=False):
+    C = 1 if I0.ndim == 2 else 3
+    H, W = I0.shape[-2:]
+    pitch = W + pitch_pad
+    a, b = to_dev(torch, I0, dev, pitch), to_dev(torch, I1, dev, pitch)
+    flow = torch.full((H, W, 2), float("nan"), device=dev)
+    h = dis.dis_create(W, H, 1, C)
+    try:
+        rec = None
+        if init is None and frozen is None and not record:
+            dis.dis_compute_flow(h, a, b, W, H, pitch, params, flow)
+        else:
+            n = dis.dis_levels(W, H, params)[2]
+            rec = torch.zeros((n, 2), device=dev) if record else None
+            it = None if init is None else torch.from_numpy(np.asarray(init, np.float32)).to(dev)
+            fz = None if frozen is None else torch.from_numpy(np.asarray(frozen, np.float32)).to(dev)
+            dis.dis_compute_flow_ex(h, a, b, W, H, pitch, params, it, fz, rec, None, flow)
+        torch.cuda.synchronize()
+    finally:
+        dis.dis_destroy(h)
+    return host(flow), (None if rec is None else host(rec))
+
+
+def oracle_params(p):
+    return oracle.params(patch_size=p.patch_size, overlap=round(float(p.overlap), 6), stride_override=p.stride_override,
+                         grad_iters=p.grad_iters, coarsest_scale=p.coarsest_scale, finest_scale=p.finest_scale,
+                         refine=p.refine, var_outer=p.var_outer, var_inner=p.var_inner, delta=p.delta,
+                         gamma=p.gamma, alpha=p.alpha, sor_omega=round(float(p.sor_omega), 6),
+                         intensity_scale=p.intensity_scale, channels=p.channels)
+
+
+def check_e2e(name, got, ref, gt=None):
+    d = np.abs(got - ref)
+    mean, p999 = d.mean(), np.quantile(d, 0.999)
+    msg = "%s: mean |du| %.2e  p99.9 %.2e  max %.2e" % (name, mean, p999, d.max())
+    if gt is not None:
+        msg += "  EPE gpu %.3f oracle %.3f" % (np.linalg.norm(got - gt, axis=-1).mean(),
+                                              np.linalg.norm(ref - gt, axis=-1).mean())
+    print(msg)
+    assert np.isfinite(got).all()
+    assert mean <= E2E_MEAN and p999 <= E2E_P999, msg
+
+
+def test_e2e_translation_128x96(env):
+    torch, dis, dev = env
+    I0, I1, gt = synth.translation_pair(0)
+    p = dis.dis_default_params(patch_size=8, stride_override=4, grad_iters=16, coarsest_scale=2, var_outer=1)
+    got, _ = run_gpu(torch, dis, dev, I0, I1, p, pitch_pad=3)
+    check_e2e("translate128x96", got, oracle.dis_flow(I0, I1, oracle_params(p)), gt)
+
+
+@pytest.mark.parametrize("preset", ["fast", "dense", "op2", "medium"])
+def test_e2e_layered_1024x436(env, preset):
+    torch, dis, dev = env
+    I0, I1, gt = synth.layered_pair(1000)
+    p = dis.dis_default_params(preset, coarsest_scale=4 if preset in ("fast", "dense") else -1)
+    got, _ = run_gpu(torch, dis, dev, I0, I1, p)
+    check_e2e("layered1024x436-" + preset, got, oracle.dis_flow(I0, I1, oracle_params(p)), gt)
+
+
+@pytest.mark.parametrize("W,H,kw", [(12, 12, dict(patch_size=12, coarsest_scale=0)),
+                                    (13, 9, dict(patch_size=8, stride_override=3)),
+                                    (37, 29, dict(patch_size=5, overlap=0.6, grad_iters=0)),
+                                    (67, 45, dict(patch_size=16, overlap=0.5, finest_scale=1)),
+                                    (100, 64, dict(patch_size=7, overlap=0.9, grad_iters=24, refine=0))])
+def test_e2e_edge_sizes(env, W, H, kw):
+    torch, dis, dev = env
+    I0, I1, gt = synth.layered_pair(17, width=W, height=H, n_ellipses=2, max_disp=2.0)
+    p = dis.dis_default_params(**kw)
+    got, _ = run_gpu(torch, dis, dev, I0, I1, p, pitch_pad=1)
+    check_e2e("edge %dx%d" % (W, H), got, oracle.dis_flow(I0, I1, oracle_params(p)))
+
+
+def test_e2e_rgb(env):
+    torch, dis, dev = env
+    I0, I1, gt = synth.layered_pair(4000, width=256, height=144, max_disp=10.0, channels=3, rotation_deg=2.0)
+    p = dis.dis_default_params("dense", channels=3, grad_iters=32)
+    got, _ = run_gpu(torch, dis, dev, I0, I1, p, pitch_pad=4)
+    check_e2e("rgb256x144", got, oracle.dis_flow(I0, I1, oracle_params(p)), gt)
+
+
+def test_too_small_is_refused(env):
+    torch, dis, dev = env
+    I0 = np.zeros((6, 6), np.float32)
+    with pytest.raises(dis.DisError) as e:
+        run_gpu(torch, dis, dev, I0, I0, dis.dis_default_params(patch_size=8))
+    assert e.value.status == dis.DIS_ERR_TOO_SMALL
+
+
+def test_record_replay_and_init_flow(env):
+    torch, dis, dev = env
+    I0, I1, gt = synth.layered_pair(3000, width=512, height=256, max_disp=20.0)
+    p = dis.dis_default_params(patch_size=8, overlap=0.5, grad_iters=16, coarsest_scale=3, var_outer=1, var_inner=10)
+    flow, rec = run_gpu(torch, dis, dev, I0, I1, p, record=True)
+    again, _ = run_gpu(torch, dis, dev, I0, I1, p, frozen=rec)
+    assert np.array_equal(flow, again)
+    q = oracle_params(p)
+    ref_frozen = oracle.dis_flow(I0, I1, q, frozen=rec)
+    check_e2e("frozen replay", again, ref_frozen)
+    # an initial flow at the coarsest level's resolution (64 x 32 at theta_ss = 3)
+    g = np.random.default_rng(1)
+    init = ndimage_smooth(g.normal(0, 1.0, (32, 64, 2)))
+    got, _ = run_gpu(torch, dis, dev, I0, I1, p, init=init)
+    check_e2e("init flow", got, oracle.dis_flow(I0, I1, q, init_flow=init.astype(np.float32)))
+
+
+def test_batched_matches_plain_bit_exact(env):
+    torch, dis, dev = env
+    sizes = [(128, 96), (173, 91), (320, 240), (64, 48), (256, 109)]
+    pairs = [synth.layered_pair(50 + k, width=w, height=h, n_ellipses=4, max_disp=0.04 * w) for k, (w, h) in
+             enumerate(sizes)]
+    for preset in ["medium", "fast"]:
+        p = dis.dis_default_params(preset)
+        plain = [run_gpu(torch, dis, dev, a, b, p)[0] for a, b, _ in pairs]
+        h = dis.dis_create(320, 240, len(pairs), 1)
+        try:
+            dev_pairs = [(to_dev(torch, a, dev), to_dev(torch, b, dev)) for a, b, _ in pairs]
+            flows = [torch.full((a.shape[0], a.shape[1], 2), float("nan"), device=dev) for a, _, _ in pairs]
+            items = [(da, db, da.shape[1], da.shape[0], da.shape[1], f) for (da, db), f in zip(dev_pairs, flows)]
+            arr = dis.make_pairs(items)
+            for _ in range(2):  # second call replays the cached graph
+                dis.dis_compute_flow_batched(h, arr, len(items), p)
+            torch.cuda.synchronize()
+        finally:
+            dis.dis_destroy(h)
+        for k, f in enumerate(flows):
+            assert np.array_equal(host(f), plain[k]), (preset, sizes[k])
