@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the DIS hot path: frame-pairs/s at 1024x436 on synthetic layered scenes.
+
+One step = the whole method (pyramid, per-level patch search, densification, variational
+refinement, up-scaling) over one batch of `--batch` frame pairs of 1024x436, run by the
+batched entry point (one CUDA-graph replay of persistent kernels over all pairs).  The same
+batch through sequential single-pair calls (the plain form) is timed beside it.  Inputs are
+resident in HBM for `value`; `e2e` adds the host->device copy of the inputs from pinned
+memory and the device->host read of the flows to every step.  L2 is flushed (a 256 MB
+write) between timed steps, outside the timed events.
+
+--impl reference times the FP64 CPU oracle (the correctness reference of this repository)
+on the host cores instead, on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): frame pairs are independent, so each rank runs its own batch
+(replicas, weak scaling, no collective on the data path); value = all ranks' pairs / max time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DIS flow frame-pairs/s at 1024x436 (batched)"
+UNIT = "frame-pairs/s"
+W, H = 1024, 436
+
+
+def preset_params(dis, name):
+    # five pyramid levels (theta_ss = 4) as in the 1024x436 workload
+    return dis.dis_default_params(name, coarsest_scale=4)
+
+
+def launches_per_call(dis, p, width, height):
+    """Kernels one call launches (mirrors the host plan: prep, pyramid, per level search +
+    densify (+ refinement: 3 setup, outer x (weights + 2 x inner), apply), final up-scaling)."""
+    ss, sf, _ = dis.dis_levels(width, height, p)
+    n = 1 + ss
+    for s in range(ss, sf - 1, -1):
+        n += 2
+        if p.refine:
+            outer = s + 1 if p.var_outer < 0 else p.var_outer
+            n += 3 + outer * (1 + 2 * p.var_inner) + 1
+    return n + (1 if sf > 0 else 0)
+
+
+def algorithmic_bytes(dis, p, width, height):
+    """Bytes each array of the method moves once per stage (float32), per pair."""
+    ss, sf, tot = dis.dis_levels(width, height, p)
+    dims = [(width, height)]
+    for _ in range(ss):
+        dims.append(((dims[-1][0] + 1) // 2, (dims[-1][1] + 1) // 2))
+    N = [w * h for w, h in dims]
+    b = 8 * N[0] + 8 * sum(N[1:ss + 1])                          # read frames, write pyramid
+    for s in range(ss, sf - 1, -1):
+        b += 8 * N[s] + 8 * (N[s + 1] if s < ss else 0) + 16 * tot // max(1, ss - sf + 1)  # search
+        b += 8 * N[s] + 8 * N[s]                                  # densify: frames, U write
+        if p.refine:
+            outer = s + 1 if p.var_outer < 0 else p.var_outer
+            b += outer * (16 + 8 + 8) * N[s]                      # refine per outer pass
+    if sf > 0:
+        b += 8 * N[0]
+    return b
+
+
+def search_flops(dis, p, width, height):
+    """Algorithmic FP32 operations of the inverse search of level theta_sf: 12 per bilinear
+    sample (3 lerps as sub+FMA, mean accumulation, residual, two FMA accumulations)."""
+    ss, sf, _ = dis.dis_levels(width, height, p)
+    w, h = width, height
+    for _ in range(sf):
+        w, h = (w + 1) // 2, (h + 1) // 2
+    ps = p.patch_size
+    stride = p.stride_override or max(1, ps - int(np.floor(p.overlap * ps + 1e-4)))
+    n = ((w - ps + stride - 1) // stride + 1) * ((h - ps + stride - 1) // stride + 1)
+    return n * p.grad_iters * ps * ps * 12, (w, h), n
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if "Active" in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(preset, seconds_hint=True):
+    """FP64 oracle on one pair of the workload cropped to 512x218 (a quarter of the area; the
+    method's cost is linear in area), scaled to pairs/s at 1024x436."""
+    import oracle
+    from paper_1603_03590_gb300 import synth
+    I0, I1, _ = synth.layered_pair(1000, width=512, height=218, max_disp=20.0)
+    from paper_1603_03590_gb300 import dis
+    p = preset_params(dis, preset)
+    q = oracle.params(patch_size=p.patch_size, overlap=round(float(p.overlap), 6), grad_iters=p.grad_iters,
+                      coarsest_scale=3, finest_scale=p.finest_scale, refine=p.refine)
+    oracle.build()
+    t = time.perf_counter()
+    oracle.dis_flow(I0, I1, q)
+    dt = time.perf_counter() - t
+    return {"value": 0.25 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one 512x218 pair (1/4 of the 1024x436 area, one level fewer), %s preset, %.1f s; "
+                      "scaled by area to pairs/s at 1024x436" % (preset, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps, warmup = args.steps, args.warmup
+    times = []
+    for k in range(warmup + steps):
+        r = cpu_baseline(args.preset)
+        if k >= warmup:
+            times.append(0.25 / r["value"])
+    dt = sum(times)
+    value = steps * 0.25 / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1000 * dt / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "layered 1024x436, %s preset, 5 levels" % args.preset, "batch": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step one 512x218 pair (1/4 area), scaled by area"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--preset", default="dense")
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--unique", type=int, default=4, help="distinct synthetic pairs cycled through the batch")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as tdist
+    from paper_1603_03590_gb300 import build, dis, synth
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    B = args.batch
+    uniq = [synth.layered_pair(1000 + k) for k in range(args.unique)]
+    p = preset_params(dis, args.preset)
+    h = dis.dis_create(W, H, B, 1)
+    I0d = [torch.from_numpy(uniq[k % len(uniq)][0]).to(dev) for k in range(B)]
+    I1d = [torch.from_numpy(uniq[k % len(uniq)][1]).to(dev) for k in range(B)]
+    flows = [torch.empty((H, W, 2), device=dev) for _ in range(B)]
+    arr = dis.make_pairs([(a, b, W, H, W, f) for a, b, f in zip(I0d, I1d, flows)])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step_batched():
+        dis.dis_compute_flow_batched(h, arr, B, p, stream)
+
+    def step_plain():
+        for k in range(B):
+            dis.dis_compute_flow(h, I0d[k], I1d[k], W, H, W, p, flows[k], stream)
+
+    def timed(fn, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        clk = Clocks(local) if sample_clocks else None
+        evs = []
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, wall, (clk.stop() if clk else None)
+
+    ms_b, wall_b, clocks = timed(step_batched, args.steps, args.warmup, sample_clocks=True)
+    plain_steps = max(3, args.steps // 4)
+    ms_p, _, _ = timed(step_plain, plain_steps, 3)
+
+    # end to end through the public API: pinned host inputs -> device, compute, flows -> host
+    hin0 = [torch.from_numpy(uniq[k % len(uniq)][0]).pin_memory() for k in range(B)]
+    hin1 = [torch.from_numpy(uniq[k % len(uniq)][1]).pin_memory() for k in range(B)]
+    hout = [torch.empty((H, W, 2), pin_memory=True) for _ in range(B)]
+
+    def step_e2e():
+        for k in range(B):
+            I0d[k].copy_(hin0[k], non_blocking=True)
+            I1d[k].copy_(hin1[k], non_blocking=True)
+        dis.dis_compute_flow_batched(h, arr, B, p, stream)
+        for k in range(B):
+            hout[k].copy_(flows[k], non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 4)
+    ms_e, _, _ = timed(step_e2e, e2e_steps, 3)
+    h2d = B * 2 * W * H * 4
+    d2h = B * W * H * 2 * 4
+
+    # dominant kernel, timed alone on its launch stream: the inverse search of level 0
+    flops, (lw, lh), npatch = search_flops(dis, p, W, H)
+    S0 = (I0d[0] * 255.0).contiguous()
+    S1 = (I1d[0] * 255.0).contiguous()
+    u = torch.empty((npatch, 2), device=dev)
+    ps = p.patch_size
+    stride = p.stride_override or max(1, ps - int(np.floor(p.overlap * ps + 1e-4)))
+    for _ in range(3):
+        dis.dis_search_level(S0, S1, lw, lh, lw, None, 0, 0, 2.0, ps, stride, p.grad_iters, u, stream=stream)
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        dis.dis_search_level(S0, S1, lw, lh, lw, None, 0, 0, 2.0, ps, stride, p.grad_iters, u, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    k_ms = e0.elapsed_time(e1) / reps
+
+    # max over ranks
+    t = torch.tensor([ms_b, ms_p, ms_e], device=dev, dtype=torch.float64)
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms_b, ms_p, ms_e = t.tolist()
+    dis.dis_destroy(h)
+    if rank != 0:
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s: 152 SMs x 128 FP32 lanes x FMA
+    value = world * B * args.steps / (ms_b / 1000.0)
+    plain = world * B * plain_steps / (ms_p / 1000.0)
+    e2e = world * B * e2e_steps / (ms_e / 1000.0)
+    abytes = algorithmic_bytes(dis, p, W, H)
+    achieved = flops / (k_ms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "layered 1024x436, %s preset, 5 levels, batch %d per GPU" % (args.preset, B),
+                   "batch_per_gpu": B, "preset": args.preset, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed events)"},
+        "plain": {"value": plain, "unit": UNIT, "ms_per_pair": ms_p / (B * plain_steps)},
+        "hbm_roofline": {"algorithmic_bytes_per_pair": abytes,
+                         "achieved_gbs": abytes * value / world / 1e9, "peak_gbs": hbm,
+                         "frac": abytes * value / world / 1e9 / hbm},
+        "roofline": {"kernel": "search_kernel (level 0, %d patches x %d iterations)" % (npatch, p.grad_iters),
+                     "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_call(dis, p, W, H) * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.preset)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -96,11 +96,27 @@ def _flat_borderline(I0, ps, stride, idx):
 
 
 def compare_search(I0, I1, Uc, cscale, ps, stride, iters, u_g, ui_g, st_g):
+    """Element-wise comparison of GPU and FP64 patch flows.
+
+    A patch whose FP64 result moves by more than 1e-4 px when I1 is perturbed by 1e-5 (the
+    size of FP32 rounding on the 0..255 scale) is not determined by its inputs at FP32
+    resolution (a search that cycles instead of converging); such patches are counted,
+    checked for validity and excluded.  Among the others a differing reset / flat decision
+    must be borderline in FP64."""
     gx, gy = oracle.sobel(I0)
     u_o, ui_o, st_o = oracle.search_level(I0, gx, gy, I1, ps, stride, iters, Uc=Uc, cscale=cscale)
     u_o, ui_o, st_o = u_o.reshape(-1, 2), ui_o.reshape(-1, 2), st_o.reshape(-1)
     assert np.abs(ui_g - ui_o).max() <= 1e-4
-    differ = np.nonzero(st_g != st_o)[0]
+    unstable = np.zeros(len(st_o), bool)
+    for seed in (1, 2):
+        I1p = I1 + 1e-5 * np.random.default_rng(seed).standard_normal(I1.shape)
+        u_p, _, st_p = oracle.search_level(I0, gx, gy, I1p, ps, stride, iters, Uc=Uc, cscale=cscale)
+        unstable |= (np.abs(u_p.reshape(-1, 2) - u_o).max(1) > 1e-4) | (st_p.reshape(-1) != st_o)
+    assert unstable.mean() < 0.02, unstable.mean()
+    assert np.isfinite(u_g).all()
+    # a result of an unstable patch is still a valid outcome: within theta_ps of u_init
+    assert (np.hypot(*(u_g - ui_g)[unstable].T) <= ps + 1e-3).all()
+    differ = np.nonzero((st_g != st_o) & ~unstable)[0]
     for k in differ:
         if 2 in (st_g[k], st_o[k]):
             r = _flat_borderline(I0, ps, stride, k)
@@ -111,9 +127,9 @@ def compare_search(I0, I1, Uc, cscale, ps, stride, iters, u_g, ui_g, st_g):
             uu, base = (u_g[k], ui_g[k]) if st_g[k] == 0 else (u_o[k], ui_o[k])
             dist = float(np.hypot(*(uu - base)))
             assert abs(dist - ps) < 1e-2, ("reset decision not borderline", k, dist)
-    same = st_g == st_o
+    same = (st_g == st_o) & ~unstable
     err = np.abs(u_g - u_o)[same]
-    return err.max() if err.size else 0.0, len(differ), u_o
+    return err.max() if err.size else 0.0, "%d decisions differ, %d unstable" % (len(differ), unstable.sum()), u_o
 
 
 @pytest.mark.parametrize("case", ["translate", "layered-dense", "layered-fast", "ragged"])
@@ -141,7 +157,7 @@ def test_search_stage(env, case):
     torch.cuda.synchronize()
     e, ndiff, _ = compare_search(host(a, W), host(b, W), Uc_h.astype(np.float64), 2.0, ps, stride, iters, host(u),
                                  host(ui), st.cpu().numpy())
-    print("search %s: %d patches, max |du| %.2e, decisions differing %d" % (case, nx * ny, e, ndiff))
+    print("search %s: %d patches, max |du| %.2e, %s" % (case, nx * ny, e, ndiff))
     assert e <= STAGE_TOL
 
 
