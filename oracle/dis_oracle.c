@@ -171,7 +171,9 @@ int or_grid_pos(int i, int len, int ps, int stride)
 
 /* ---- levels (Sec. 3.1) -------------------------------------------------------------
  * [R4] theta_ss = ceil(log2(2 W / (f theta_ps))) with f = 8, lowered until the coarsest
- * level still holds one patch.  Returns OR_OK and writes (ss, sf), or OR_ERR_TOO_SMALL. */
+ * level still holds one patch, and raised to theta_sf when it falls below it (Alg. 1 runs
+ * s from theta_ss down to theta_sf, so a coarsest scale below the finest would process no
+ * level).  Returns OR_OK and writes (ss, sf), or OR_ERR_TOO_SMALL. */
 static int level_dim(int d, int s)
 {
     for (int i = 0; i < s; i++) d = (d + 1) / 2;
@@ -186,6 +188,7 @@ int or_levels(int W, int H, const or_params* p, int* ss_out, int* sf_out)
         double v = 2.0 * (double)W / (8.0 * (double)ps);
         ss = v <= 1.0 ? 0 : (int)ceil(log2(v));
         while (ss > sf && (level_dim(W, ss) < ps || level_dim(H, ss) < ps)) ss--;
+        if (ss < sf) ss = sf;
     }
     if (ss < sf) return OR_ERR_TOO_SMALL;
     if (level_dim(W, ss) < ps || level_dim(H, ss) < ps) return OR_ERR_TOO_SMALL;

@@ -90,7 +90,8 @@ dis_status validate(const dis_params* p, std::string& err)
 }
 
 // theta_ss = ceil(log2(2 W / (f theta_ps))), f = 8 (Sec. 3.1), lowered until the coarsest
-// level holds a patch; an explicit theta_ss that cannot hold one is refused.
+// level holds a patch and raised to theta_sf if below it (Alg. 1 loops from theta_ss down
+// to theta_sf); an explicit theta_ss that cannot hold a patch is refused.
 dis_status resolve_levels(int W, int H, const dis_params& p, int& ss, int& sf, std::string& err)
 {
     const int ps = p.patch_size;
@@ -100,6 +101,7 @@ dis_status resolve_levels(int W, int H, const dis_params& p, int& ss, int& sf, s
         const double v = 2.0 * (double)W / (8.0 * (double)ps);
         ss = v <= 1.0 ? 0 : (int)std::ceil(std::log2(v));
         while (ss > sf && (level_dim(W, ss) < ps || level_dim(H, ss) < ps)) --ss;
+        ss = std::max(ss, sf);
     }
     if (ss < sf || level_dim(W, ss) < ps || level_dim(H, ss) < ps) {
         err = "image too small: the coarsest processed level cannot hold one patch";

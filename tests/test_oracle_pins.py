@@ -134,6 +134,9 @@ def test_paper_values_levels():
     assert oracle.levels(64, 20, oracle.params(patch_size=8))[1] == 1
     assert oracle.levels(64, 20, oracle.params(patch_size=8, coarsest_scale=3))[0] == 4
     assert oracle.levels(6, 6, oracle.params(patch_size=8))[0] == 4
+    # an automatic theta_ss below theta_sf is raised to theta_sf (Alg. 1 runs ss down to sf)
+    assert oracle.levels(64, 48, oracle.params(patch_size=8, finest_scale=2)) == (0, 2, 2)
+    assert oracle.levels(24, 24, oracle.params(patch_size=8, finest_scale=2))[0] == 4
 
 
 # ---------------------------------------------------------------- inverse search (Sec. 2.1, supp. A)
