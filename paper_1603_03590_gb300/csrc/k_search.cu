@@ -1,33 +1,48 @@
 // Inverse-compositional patch search of DIS (Sec. 2.1; supplementary Sec. A, Eq. solvereqinv;
 // Alg. 1 steps 1-3 and the outlier reset of step 4).
 //
-// One warp per patch.  The prologue stages the (ps+2)^2 window of I0 around the patch in
-// shared memory, computes the Sobel/8 gradients S' = grad T, the mean-normalised template T
-// and the 2x2 Hessian H' = sum S'^T S' (reduced with warp shuffles), all kept in registers.
-// Each of the theta_it iterations samples I1 bilinearly at x + u (one fractional weight pair
-// for the whole patch), removes the sample mean, and reduces b = sum S'^T (w - T) across the
-// warp; u <- u - H'^-1 b.  Lane l owns patch pixels l, l + 32, ... (M = ceil(ps^2 / 32)).
+// A group of LPP lanes (8, 16 or 32 by patch size) owns one patch; lane l of the group owns
+// patch pixels l, l + LPP, ... (PPL of them).  The prologue stages the (ps+2)^2 window of I0
+// around the patch in shared memory and computes, in registers, the Sobel/8 gradients
+// S' = grad T, the mean-normalised template T and the 2x2 Hessian H' = sum S'^T S' (group
+// shuffle reductions).
+//
+// Iterations.  u is shared by the whole patch, so every pixel samples I1 with the same
+// fractional weights (ax, ay): I1(x + u) = t0 + ax t1 + ay (t2 + ax t3) with the pixel's four
+// taps folded into t0..t3.  The taps stay in registers and are re-read only when the integer
+// part of u changes (the clamped taps also encode the image border), so a converged patch
+// iterates from registers alone: 3 FMA per sample.  The mean-normalised residual is reduced in
+// one pass relative to the previous iteration's mean m:
+//   S0 = sum (w - m),  Sg = sum S' (w - m - T),  b = Sg - (S0 / n) sum S'  ( = sum S'^T (w - mean w - T) )
+// which keeps the three group sums independent and their terms small.  u <- u - H'^-1 b.
+#include <climits>
+
 #include "dis_device.cuh"
 
 namespace dis {
 
-template <int M>
-__global__ void __launch_bounds__(256) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
-                                                     int ps, int stride, int iters)
+template <int LPP>
+__device__ __forceinline__ float group_sum(float v, unsigned mask)
+{
+#pragma unroll
+    for (int o = LPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+template <int LPP, int PPL>
+__global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total, int ps,
+                                                     int stride, int iters)
 {
     extern __shared__ float smem[];
+    constexpr int GPW = 32 / LPP;  // patches per warp
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int grp = lane / LPP, gl = lane % LPP;
+    const unsigned gmask = (LPP == 32) ? 0xffffffffu : (((1u << LPP) - 1u) << (grp * LPP));
     const int ws = ps + 2, n = ps * ps;
-    float* win = smem + wib * ws * ws;
+    float* win = smem + (wib * GPW + grp) * ws * ws;
     const float inv_n = 1.0f / (float)n;
-    int kx[M], ky[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const int k = lane + 32 * m;
-        kx[m] = k < n ? k % ps : 0;
-        ky[m] = k < n ? k / ps : 0;
-    }
-    for (long long g = (long long)blockIdx.x * wpb + wib; g < total; g += (long long)gridDim.x * wpb) {
+    const long long step = (long long)gridDim.x * wpb * GPW;
+    for (long long g = ((long long)blockIdx.x * wpb + wib) * GPW + grp; g < total; g += step) {
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::patch_base));
         const long long pk = g - J.patch_base;
         const int w = J.w, h = J.h, pitch = J.pitch;
@@ -42,18 +57,20 @@ __global__ void __launch_bounds__(256) search_kernel(const __grid_constant__ Job
             u += f.x;
             v += f.y;
         } else {
-            // ---- template, gradients, Hessian (computed once per patch)
-            for (int t = lane; t < ws * ws; t += 32) {
+            // ---- template window, gradients, template, Hessian (once per patch)
+            for (int t = gl; t < ws * ws; t += LPP) {
                 const int a = t % ws, b = t / ws;
                 win[t] = __ldg(J.S0 + (long long)clampi(py - 1 + b, 0, h - 1) * pitch + clampi(px - 1 + a, 0, w - 1));
             }
-            __syncwarp();
-            float T[M], gx[M], gy[M];
+            __syncwarp(gmask);
+            float T[PPL], gx[PPL], gy[PPL];
             float s0 = 0.0f;
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                if (lane + 32 * m < n) {
-                    const float* c0 = win + ky[m] * ws + kx[m];  // (x-1, y-1)
+            for (int m = 0; m < PPL; ++m) {
+                const int k = gl + LPP * m;
+                if (k < n) {
+                    const int kx = k % ps, ky = k / ps;
+                    const float* c0 = win + ky * ws + kx;  // (x-1, y-1)
                     const float* c1 = c0 + ws;
                     const float* c2 = c1 + ws;
                     T[m] = c1[1];
@@ -64,19 +81,23 @@ __global__ void __launch_bounds__(256) search_kernel(const __grid_constant__ Job
                     T[m] = gx[m] = gy[m] = 0.0f;
                 }
             }
-            __syncwarp();
-            const float mean0 = warp_sum(s0) * inv_n;
-            float h00 = 0.0f, h01 = 0.0f, h11 = 0.0f;
+            __syncwarp(gmask);
+            const float mean0 = group_sum<LPP>(s0, gmask) * inv_n;
+            float h00 = 0.0f, h01 = 0.0f, h11 = 0.0f, sgx = 0.0f, sgy = 0.0f;
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                if (lane + 32 * m < n) T[m] -= mean0;
+            for (int m = 0; m < PPL; ++m) {
+                if (gl + LPP * m < n) T[m] -= mean0;
                 h00 = fmaf(gx[m], gx[m], h00);
                 h01 = fmaf(gx[m], gy[m], h01);
                 h11 = fmaf(gy[m], gy[m], h11);
+                sgx += gx[m];
+                sgy += gy[m];
             }
-            h00 = warp_sum(h00);
-            h01 = warp_sum(h01);
-            h11 = warp_sum(h11);
+            h00 = group_sum<LPP>(h00, gmask);
+            h01 = group_sum<LPP>(h01, gmask);
+            h11 = group_sum<LPP>(h11, gmask);
+            sgx = group_sum<LPP>(sgx, gmask);
+            sgy = group_sum<LPP>(sgy, gmask);
             // 2x2 determinant with the product h01^2 split exactly (Kahan)
             const float p2 = h01 * h01;
             const float e2 = fmaf(h01, h01, -p2);
@@ -86,55 +107,70 @@ __global__ void __launch_bounds__(256) search_kernel(const __grid_constant__ Job
                 st = 2;
             } else {
                 const float idet = 1.0f / det;
+                float t0[PPL], t1[PPL], t2[PPL], t3[PPL];
+                int ciu = INT_MIN, civ = INT_MIN;
+                float mref = mean0;
                 for (int it = 0; it < iters; ++it) {
                     const float uc = fminf(fmaxf(u, -1.0e7f), 1.0e7f);
                     const float vc = fminf(fmaxf(v, -1.0e7f), 1.0e7f);
                     const float fu = floorf(uc), fv = floorf(vc);
                     const float ax = uc - fu, ay = vc - fv;
-                    const int xi = px + (int)fu, yi = py + (int)fv;
-                    float wv[M];
-                    float sw = 0.0f;
-                    if (xi >= 0 && yi >= 0 && xi + ps <= w - 1 && yi + ps <= h - 1) {
-                        const float* base = J.S1 + (long long)yi * pitch + xi;
+                    const int iu = (int)fu, iv = (int)fv;
+                    if (iu != ciu || iv != civ) {
+                        // the integer displacement moved: re-read the taps (clamped at the border)
+                        ciu = iu;
+                        civ = iv;
+                        const int xi = px + iu, yi = py + iv;
+                        const bool inside = xi >= 0 && yi >= 0 && xi + ps <= w - 1 && yi + ps <= h - 1;
 #pragma unroll
-                        for (int m = 0; m < M; ++m) {
-                            if (lane + 32 * m < n) {
-                                const float* p = base + ky[m] * pitch + kx[m];
-                                const float a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + pitch), d = __ldg(p + pitch + 1);
-                                const float top = fmaf(ax, b - a, a), bot = fmaf(ax, d - c, c);
-                                wv[m] = fmaf(ay, bot - top, top);
-                                sw += wv[m];
-                            } else {
-                                wv[m] = 0.0f;
+                        for (int m = 0; m < PPL; ++m) {
+                            const int k = gl + LPP * m;
+                            float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f;
+                            if (k < n) {
+                                const int kx = k % ps, ky = k / ps;
+                                if (inside) {
+                                    const float* p = J.S1 + (long long)(yi + ky) * pitch + (xi + kx);
+                                    a = __ldg(p);
+                                    b = __ldg(p + 1);
+                                    c = __ldg(p + pitch);
+                                    d = __ldg(p + pitch + 1);
+                                } else {
+                                    const int x0 = clampi(xi + kx, 0, w - 1), x1 = clampi(xi + kx + 1, 0, w - 1);
+                                    const float* r0 = J.S1 + (long long)clampi(yi + ky, 0, h - 1) * pitch;
+                                    const float* r1 = J.S1 + (long long)clampi(yi + ky + 1, 0, h - 1) * pitch;
+                                    a = __ldg(r0 + x0);
+                                    b = __ldg(r0 + x1);
+                                    c = __ldg(r1 + x0);
+                                    d = __ldg(r1 + x1);
+                                }
                             }
-                        }
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < M; ++m) {
-                            if (lane + 32 * m < n) {
-                                const int x0 = clampi(xi + kx[m], 0, w - 1), x1 = clampi(xi + kx[m] + 1, 0, w - 1);
-                                const int y0 = clampi(yi + ky[m], 0, h - 1), y1 = clampi(yi + ky[m] + 1, 0, h - 1);
-                                const float* r0 = J.S1 + (long long)y0 * pitch;
-                                const float* r1 = J.S1 + (long long)y1 * pitch;
-                                const float a = __ldg(r0 + x0), b = __ldg(r0 + x1), c = __ldg(r1 + x0), d = __ldg(r1 + x1);
-                                const float top = fmaf(ax, b - a, a), bot = fmaf(ax, d - c, c);
-                                wv[m] = fmaf(ay, bot - top, top);
-                                sw += wv[m];
-                            } else {
-                                wv[m] = 0.0f;
-                            }
+                            t0[m] = a;
+                            t1[m] = b - a;
+                            t2[m] = c - a;
+                            t3[m] = (d - c) - (b - a);
                         }
                     }
-                    const float mw = warp_sum(sw) * inv_n;
-                    float b0 = 0.0f, b1 = 0.0f;
+                    float S0 = 0.0f, Sx = 0.0f, Sy = 0.0f;
 #pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const float r = (lane + 32 * m < n) ? (wv[m] - mw) - T[m] : 0.0f;
-                        b0 = fmaf(gx[m], r, b0);
-                        b1 = fmaf(gy[m], r, b1);
+                    for (int m = 0; m < PPL; ++m) {
+                        if (gl + LPP * m < n) {
+                            const float wv = fmaf(ay, fmaf(ax, t3[m], t2[m]), fmaf(ax, t1[m], t0[m]));
+                            const float wd = wv - mref;
+                            const float r = wd - T[m];
+                            S0 += wd;
+                            Sx = fmaf(gx[m], r, Sx);
+                            Sy = fmaf(gy[m], r, Sy);
+                        }
                     }
-                    b0 = warp_sum(b0);
-                    b1 = warp_sum(b1);
+#pragma unroll
+                    for (int o = LPP / 2; o > 0; o >>= 1) {
+                        S0 += __shfl_xor_sync(gmask, S0, o);
+                        Sx += __shfl_xor_sync(gmask, Sx, o);
+                        Sy += __shfl_xor_sync(gmask, Sy, o);
+                    }
+                    const float dm = S0 * inv_n;
+                    const float b0 = fmaf(-dm, sgx, Sx), b1 = fmaf(-dm, sgy, Sy);
+                    mref += dm;
                     u -= (h11 * b0 - h01 * b1) * idet;
                     v -= (h00 * b1 - h01 * b0) * idet;
                 }
@@ -146,7 +182,7 @@ __global__ void __launch_bounds__(256) search_kernel(const __grid_constant__ Job
                 }
             }
         }
-        if (lane == 0) {
+        if (gl == 0) {
             J.pu[pk] = make_float2(u, v);
             if (J.pui) J.pui[pk] = ui;
             if (J.pst) J.pst[pk] = st;
@@ -155,39 +191,57 @@ __global__ void __launch_bounds__(256) search_kernel(const __grid_constant__ Job
     }
 }
 
-template <int M>
-static cudaError_t launch_m(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
-                            const LaunchCfg& lc, cudaStream_t s)
+template <int LPP, int PPL>
+static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
+                             const LaunchCfg& lc, cudaStream_t s)
 {
-    const int threads = 256, wpb = threads / 32;
-    const size_t smem = (size_t)wpb * (ps + 2) * (ps + 2) * sizeof(float);
+    const int threads = 128, wpb = threads / 32, per_block = wpb * (32 / LPP);
+    const size_t smem = (size_t)per_block * (ps + 2) * (ps + 2) * sizeof(float);
     static int occ = 0;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<M>, threads, smem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL>, threads, smem) !=
+                cudaSuccess ||
             occ < 1)
             occ = 1;
     }
-    long long blocks = (total + wpb - 1) / wpb;
+    long long blocks = (total + per_block - 1) / per_block;
     const long long cap = (long long)lc.sm_count * occ;
     if (blocks > cap) blocks = cap;
-    search_kernel<M><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
+    search_kernel<LPP, PPL><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
     return cudaGetLastError();
 }
 
+// Lanes per patch by patch size: 8 up to 8x8 (<= 8 pixels per lane), 16 up to 12x12 (<= 9),
+// 32 up to 16x16 (<= 8).
 cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
                           const LaunchCfg& lc, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
-    switch ((ps * ps + 31) / 32) {
-        case 1: return launch_m<1>(js, total, ps, stride, iters, lc, s);
-        case 2: return launch_m<2>(js, total, ps, stride, iters, lc, s);
-        case 3: return launch_m<3>(js, total, ps, stride, iters, lc, s);
-        case 4: return launch_m<4>(js, total, ps, stride, iters, lc, s);
-        case 5: return launch_m<5>(js, total, ps, stride, iters, lc, s);
-        case 6: return launch_m<6>(js, total, ps, stride, iters, lc, s);
-        case 7: return launch_m<7>(js, total, ps, stride, iters, lc, s);
-        case 8: return launch_m<8>(js, total, ps, stride, iters, lc, s);
-        default: return cudaErrorInvalidValue;
+    const int n = ps * ps;
+    if (ps <= 8) {
+        switch ((n + 7) / 8) {
+            case 1: return launch_lp<8, 1>(js, total, ps, stride, iters, lc, s);
+            case 2: return launch_lp<8, 2>(js, total, ps, stride, iters, lc, s);
+            case 3: return launch_lp<8, 3>(js, total, ps, stride, iters, lc, s);
+            case 4: return launch_lp<8, 4>(js, total, ps, stride, iters, lc, s);
+            case 5: return launch_lp<8, 5>(js, total, ps, stride, iters, lc, s);
+            case 6: return launch_lp<8, 6>(js, total, ps, stride, iters, lc, s);
+            case 7: return launch_lp<8, 7>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<8, 8>(js, total, ps, stride, iters, lc, s);
+        }
+    }
+    if (ps <= 12) {
+        switch ((n + 15) / 16) {
+            case 6: return launch_lp<16, 6>(js, total, ps, stride, iters, lc, s);
+            case 7: return launch_lp<16, 7>(js, total, ps, stride, iters, lc, s);
+            case 8: return launch_lp<16, 8>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<16, 9>(js, total, ps, stride, iters, lc, s);
+        }
+    }
+    switch ((n + 31) / 32) {
+        case 6: return launch_lp<32, 6>(js, total, ps, stride, iters, lc, s);
+        case 7: return launch_lp<32, 7>(js, total, ps, stride, iters, lc, s);
+        default: return launch_lp<32, 8>(js, total, ps, stride, iters, lc, s);
     }
 }
 
