@@ -186,6 +186,29 @@ dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, in
 dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, float* Uout, int wo, int ho,
                              void* stream);
 
+/* ---- allocation-free variant (no counterpart in the paper) ----------------------------
+ * dis_refine_level needs a handle, i.e. device memory that dis_create obtained with
+ * cudaMalloc.  Callers that cannot allocate device memory - a plugin inside a host application
+ * that owns the whole memory budget through its own pool, or a latency-critical loop that may
+ * not call cudaMalloc / cudaFree because they can synchronise the device - use this variant:
+ * same operation, arguments and result as dis_refine_level, but its scratch is a fixed device
+ * array of DIS_NOALLOC_SCRATCH_FLOATS floats (16 MiB) built into the library, which every
+ * device that loads the library holds until the process exits.  The call allocates nothing;
+ * the caller still owns I0, I1 and U.
+ *  - Size limit: (15 * channels + 8) * pitch * h must not exceed DIS_NOALLOC_SCRATCH_FLOATS
+ *    (e.g. a 512 x 256 grayscale level with pitch 512: 3,014,656 floats); larger levels are
+ *    rejected with DIS_ERR_INVALID_ARG before any work is enqueued.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device current) and caches it; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents (the call itself
+ *    zeroes what must start at zero).  Calls whose GPU work overlaps - on different streams
+ *    or host threads - race on it: serialise them (e.g. one stream).
+ *  - Errors are reported through dis_last_error_string(NULL). */
+#define DIS_NOALLOC_SCRATCH_FLOATS (1u << 22)
+dis_status dis_refine_level_noalloc(const float* I0, const float* I1, int w, int h, int64_t pitch, int channels,
+                                    float* U, int outer, int inner, float delta, float gamma, float alpha, float omega,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

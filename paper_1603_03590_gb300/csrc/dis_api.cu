@@ -789,3 +789,11 @@ dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, flo
 }
 
 }  // extern "C"
+
+namespace dis {
+
+LaunchCfg stage_launch_cfg() { return stage_lc(); }
+
+void set_thread_error(const std::string& msg) { g_err = msg; }
+
+}  // namespace dis

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace dis {
 
 // Patch / pyramid / refinement work of one frame pair at one pyramid level.
@@ -130,5 +132,10 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
 cudaError_t launch_upsample(const Jobs<UpJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
 
 LaunchCfg query_launch_cfg();
+
+// Launch configuration of the handle-less entry points (cached per host thread).
+LaunchCfg stage_launch_cfg();
+// Message returned by dis_last_error_string(NULL) for handle-less calls of this thread.
+void set_thread_error(const std::string& msg);
 
 }  // namespace dis

@@ -78,6 +78,7 @@ _SIGS = {
     "dis_densify_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _vp, _i, _i, _f, _vp, _vp]),
     "dis_refine_level": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
     "dis_upsample_flow": (_i, [_vp, _i, _i, _f, _vp, _i, _i, _vp]),
+    "dis_refine_level_noalloc": (_i, [_vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -194,3 +195,14 @@ def dis_refine_level(handle, I0, I1, w, h, pitch, channels, U, outer, inner, del
 
 def dis_upsample_flow(Uin, wi, hi, factor, Uout, wo, ho, stream=None):
     _check(_lib.dis_upsample_flow(_ptr(Uin), wi, hi, factor, _ptr(Uout), wo, ho, _stream(stream)))
+
+
+DIS_NOALLOC_SCRATCH_FLOATS = 1 << 22
+
+
+def dis_refine_level_noalloc(I0, I1, w, h, pitch, channels, U, outer, inner, delta=5.0, gamma=10.0, alpha=10.0,
+                             omega=1.6, stream=None):
+    """dis_refine_level without a handle: scratch is the library's fixed device array
+    (for callers that cannot allocate device memory; see include/dis.h)."""
+    _check(_lib.dis_refine_level_noalloc(_ptr(I0), _ptr(I1), w, h, pitch, channels, _ptr(U), outer, inner, delta,
+                                         gamma, alpha, omega, _stream(stream)))
