@@ -131,7 +131,7 @@ dis_status dis_compute_flow(dis_handle* h, const float* I0, const float* I1, int
  *  record_out  (nullable): receives those increments (0 for reset and flat patches).
  *  checkpoints (nullable): receives the densified flow U_s of every processed level,
  *              coarsest first, each level's w_s*h_s*2 floats back to back (dis_levels
- *              gives the sizes); used by dis_backward. */
+ *              gives the sizes). */
 dis_status dis_compute_flow_ex(dis_handle* h, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
                                const dis_params* p, const float* init_flow, const float* frozen_in,
                                float* record_out, float* checkpoints, float* flow_out, void* stream);
@@ -185,6 +185,46 @@ dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, in
  * clamping.  Uin: wi*hi*2, Uout: wo*ho*2. */
 dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, float* Uout, int wo, int ho,
                              void* stream);
+
+/* ---- differentiable form (not in the paper) -------------------------------------------
+ * The differentiable map F(I0, I1, init_flow) is DIS with every patch search replaced by its
+ * recorded increment (u_i = u_init,i + Delta_i, Delta_i frozen: a converged argmin does not
+ * depend on where it started), so gradients flow through the bilinear sampling of the initial
+ * displacement, the densification weights (Eq. 3), the unrolled red-black SOR of the variational
+ * refinement (Sec. 2.3) and the pyramid.  Record the increments with dis_compute_flow_ex
+ * (record_out); dis_replay_flow evaluates F and dis_backward its gradient.  Both compute in
+ * double precision: the refinement's robust weights Psi'(a^2) = 1 / (2 sqrt(a^2 + eps^2))
+ * (eps = 0.001) make the gradient depend on flow and residual differences near 1e-6, below the
+ * resolution of FP32 flow values.  Grayscale and finest_scale == 0 only (DIS_ERR_NOT_SUPPORTED
+ * otherwise).  frozen: dis_levels' total_patches x 2 floats, coarsest level first; init_flow
+ * (nullable): level theta_ss resolution, dense, 2 floats per pixel.  Nothing is allocated: the
+ * caller passes a device workspace of dis_backward_workspace_bytes bytes. */
+
+/* Photometric loss L = mean over channels and pixels of sqrt((I1(x + U(x)) - I0(x))^2 + eps^2)
+ * (Charbonnier, eps = 0.001 by default) on the [0,1] scale, and its gradient with respect to
+ * the flow (h*w*2), I0 and I1 (planar, pitch `pitch`).  loss_out: one device double.
+ * scratch: device bytes >= dis_photometric_loss_scratch_bytes(...).  Deterministic. */
+int64_t dis_photometric_loss_scratch_bytes(int width, int height, int64_t pitch, int channels);
+dis_status dis_photometric_loss(const float* I0, const float* I1, int w, int h, int64_t pitch, int channels,
+                                const float* flow, float eps, double* loss_out, float* grad_flow, float* grad_I0,
+                                float* grad_I1, void* scratch, int64_t scratch_bytes, void* stream);
+
+/* Device workspace for dis_replay_flow / dis_backward on a W x H pair under `p` (-1: invalid). */
+int64_t dis_backward_workspace_bytes(int width, int height, const dis_params* p);
+
+/* F(I0, I1, init_flow) with the recorded increments `frozen`, in FP64; flow_out: h*w*2 floats. */
+dis_status dis_replay_flow(dis_handle* h, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                           const dis_params* p, const float* init_flow, const float* frozen, float* flow_out,
+                           void* workspace, int64_t workspace_bytes, void* stream);
+
+/* Gradient of a scalar loss through F: given grad_flow = dLoss/dF (h*w*2), writes dLoss/dI0 and
+ * dLoss/dI1 (full resolution, [0,1] scale, row pitch grad_pitch) and, when grad_init_flow is
+ * not NULL (init_flow must then be given), dLoss/dinit_flow.  Image-gradient scatters accumulate
+ * in 64-bit fixed point, so the result is deterministic. */
+dis_status dis_backward(dis_handle* h, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                        const dis_params* p, const float* init_flow, const float* frozen, const float* grad_flow,
+                        float* grad_I0, float* grad_I1, int64_t grad_pitch, float* grad_init_flow, void* workspace,
+                        int64_t workspace_bytes, void* stream);
 
 /* ---- allocation-free variant (no counterpart in the paper) ----------------------------
  * dis_refine_level needs a handle, i.e. device memory that dis_create obtained with

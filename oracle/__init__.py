@@ -83,7 +83,7 @@ def _load():
             "or_upsample_flow": (None, [_D, i, i, d, _D, i, i]),
             "or_total_patches": (i, [i, i, P]),
             "or_dis_flow": (i, [_D, _D, i, i, P, _D, _D, _D, _D, u64p]),
-            "or_charbonnier_loss": (d, [_D, _D, i, i, i, _D, d]),
+            "or_charbonnier_loss": (d, [_D, _D, i, i, i, _D, d, u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -225,9 +225,14 @@ def dis_flow(I0, I1, prm, init_flow=None, frozen=None, record=False, want_hash=F
     return out[0] if len(out) == 1 else tuple(out)
 
 
-def charbonnier_loss(I0, I1, flow, eps_c=1e-3):
+def charbonnier_loss(I0, I1, flow, eps_c=1e-3, hash_seed=None):
+    """Mean Charbonnier photometric loss; with hash_seed (an int) also returns the decision
+    trace of the loss's samples continued from that seed."""
     I0, I1, flow = _f64(I0), _f64(I1), _f64(flow)
     if I0.ndim == 2:
         I0, I1 = I0[None], I1[None]
     C, H, W = I0.shape
-    return _load().or_charbonnier_loss(_p(I0), _p(I1), W, H, C, _p(flow), float(eps_c))
+    hv = ctypes.c_uint64(0 if hash_seed is None else hash_seed)
+    v = _load().or_charbonnier_loss(_p(I0), _p(I1), W, H, C, _p(flow), float(eps_c),
+                                    None if hash_seed is None else ctypes.byref(hv))
+    return v if hash_seed is None else (v, hv.value)

@@ -653,11 +653,14 @@ int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_param
 
 /* Photometric loss of the differentiable form: mean over channels and pixels of the
  * Charbonnier penalty sqrt((I1(x + U(x)) - I0(x))^2 + eps_c^2) on the [0,1] input scale.
- * [R18] eps_c is a parameter (the paper's eps = 0.001 by default). */
-double or_charbonnier_loss(const double* I0, const double* I1, int W, int H, int C, const double* flow, double eps_c)
+ * [R18] eps_c is a parameter (the paper's eps = 0.001 by default).  hash (optional): the
+ * bilinear cells and clampings of the loss's samples join the decision trace. */
+double or_charbonnier_loss(const double* I0, const double* I1, int W, int H, int C, const double* flow, double eps_c,
+                           uint64_t* hash)
 {
     size_t n = (size_t)W * H;
     double acc = 0.0;
+    t_hash = hash;
     for (int c = 0; c < C; c++)
         for (int y = 0; y < H; y++)
             for (int x = 0; x < W; x++) {
@@ -665,5 +668,6 @@ double or_charbonnier_loss(const double* I0, const double* I1, int W, int H, int
                 double r = or_bilinear(I1 + n * c, W, H, x + flow[2 * o], y + flow[2 * o + 1]) - I0[n * c + o];
                 acc += sqrt(r * r + eps_c * eps_c);
             }
+    t_hash = NULL;
     return acc / (double)(n * C);
 }

@@ -1,0 +1,108 @@
+"""torch.autograd wrappers of the differentiable form (marshalling only; the forward and the
+backward run in libdis.so's kernels).
+
+DifferentiableDIS(I0, I1, init_flow) returns the flow of the frozen-search DIS map: the
+forward records every patch's search increment (FP32 search) and evaluates the map with those
+increments frozen in FP64; the backward repeats that replay and runs the FP64 adjoint of the
+pyramid, initial displacements, densification and unrolled SOR sweeps.  photometric_loss is the mean
+Charbonnier penalty sqrt((I1(x + U(x)) - I0(x))^2 + eps^2) with its gradients.
+"""
+import torch
+
+from . import dis
+
+
+def _level_dims(w, h, s):
+    for _ in range(s):
+        w, h = (w + 1) // 2, (h + 1) // 2
+    return w, h
+
+
+class DifferentiableDIS:
+    """Grayscale DIS with gradients w.r.t. I0, I1 (H, W float32 CUDA, [0, 1]) and the initial
+    flow (level theta_ss resolution, (h_ss, w_ss, 2)).  finest_scale must be 0."""
+
+    def __init__(self, max_w, max_h, preset="default", **overrides):
+        self.params = dis.dis_default_params(preset, channels=1, **overrides)
+        self.handle = dis.dis_create(max_w, max_h, 1, 1)
+
+    def close(self):
+        if self.handle:
+            dis.dis_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coarsest_shape(self, w, h):
+        ss, _, _ = dis.dis_levels(w, h, self.params)
+        ws, hs = _level_dims(w, h, ss)
+        return hs, ws
+
+    def __call__(self, I0, I1, init_flow=None):
+        return _DISFlow.apply(I0, I1, init_flow, self)
+
+
+class _DISFlow(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, I0, I1, init_flow, owner):
+        I0c, I1c = I0.detach().contiguous(), I1.detach().contiguous()
+        H, W = I0c.shape
+        p = owner.params
+        n = dis.dis_levels(W, H, p)[2]
+        rec = torch.empty((n, 2), device=I0c.device, dtype=torch.float32)
+        tmp = torch.empty((H, W, 2), device=I0c.device, dtype=torch.float32)
+        init = None if init_flow is None else init_flow.detach().contiguous()
+        # the FP32 search records every patch's increment ...
+        dis.dis_compute_flow_ex(owner.handle, I0c, I1c, W, H, W, p, init, None, rec, None, tmp)
+        # ... and the map with those increments frozen is evaluated in FP64
+        nbytes = dis.dis_backward_workspace_bytes(W, H, p)
+        ws = torch.empty(nbytes, device=I0c.device, dtype=torch.uint8)
+        flow = torch.empty((H, W, 2), device=I0c.device, dtype=torch.float32)
+        dis.dis_replay_flow(owner.handle, I0c, I1c, W, H, W, p, init, rec, flow, ws, nbytes)
+        ctx.owner = owner
+        ctx.has_init = init is not None
+        ctx.save_for_backward(I0c, I1c, init if init is not None else torch.empty(0, device=I0c.device), rec)
+        return flow
+
+    @staticmethod
+    def backward(ctx, grad_flow):
+        I0, I1, init, rec = ctx.saved_tensors
+        owner, p = ctx.owner, ctx.owner.params
+        H, W = I0.shape
+        nbytes = dis.dis_backward_workspace_bytes(W, H, p)
+        ws = torch.empty(nbytes, device=I0.device, dtype=torch.uint8)
+        gI0, gI1 = torch.empty_like(I0), torch.empty_like(I1)
+        it = init if ctx.has_init else None
+        gInit = torch.empty_like(init) if ctx.has_init else None
+        dis.dis_backward(owner.handle, I0, I1, W, H, W, p, it, rec, grad_flow.contiguous(), gI0, gI1, W, gInit, ws,
+                         nbytes)
+        return gI0, gI1, gInit, None
+
+
+class _PhotometricLoss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, I0, I1, flow, eps):
+        I0c, I1c, fc = I0.detach().contiguous(), I1.detach().contiguous(), flow.detach().contiguous()
+        C = 1 if I0c.dim() == 2 else I0c.shape[0]
+        H, W = I0c.shape[-2:]
+        loss = torch.empty(1, device=I0c.device, dtype=torch.float64)
+        gf, g0, g1 = torch.empty_like(fc), torch.empty_like(I0c), torch.empty_like(I1c)
+        nb = dis.dis_photometric_loss_scratch_bytes(W, H, W, C)
+        scratch = torch.empty(nb, device=I0c.device, dtype=torch.uint8)
+        dis.dis_photometric_loss(I0c, I1c, W, H, W, C, fc, float(eps), loss, gf, g0, g1, scratch, nb)
+        ctx.save_for_backward(g0, g1, gf)
+        return loss[0].to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, g):
+        g0, g1, gf = ctx.saved_tensors
+        return g * g0, g * g1, g * gf, None
+
+
+def photometric_loss(I0, I1, flow, eps=1e-3):
+    """Mean Charbonnier photometric error of flow (H, W, 2) between I0 and I1."""
+    return _PhotometricLoss.apply(I0, I1, flow, eps)

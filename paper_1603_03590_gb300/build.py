@@ -36,7 +36,7 @@ def _stale(outputs, inputs):
 
 def build(force=False, verbose=False, extra_flags=()):
     """Compile every csrc/*.cu and link libdis.so; returns the library path."""
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "dis.h")]
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "dis.h")]
     srcs = sources()
     if not force and not _stale([LIB], srcs + headers + [__file__]):
         return LIB

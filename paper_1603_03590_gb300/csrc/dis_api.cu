@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/dis.h"
+#include "dis_host.h"
 #include "dis_internal.cuh"
 
 using dis::Jobs;
@@ -113,31 +114,6 @@ dis_status resolve_levels(int W, int H, const dis_params& p, int& ss, int& sf, s
 int grid_n(int L, int ps, int stride) { return L < ps ? 0 : (L - ps + stride - 1) / stride + 1; }
 
 }  // namespace
-
-// ---- handle and arena -------------------------------------------------------------------
-struct dis_handle {
-    int max_w = 0, max_h = 0, max_batch = 0, C = 1, levels = 0, device = 0;
-    char* arena = nullptr;
-    size_t arena_bytes = 0, slot_bytes = 0;
-    std::vector<size_t> off_img, off_U, off_pu, off_pui, off_pst;  // per level, within a slot
-    size_t off_rs = 0;
-    size_t rs_floats = 0;  // capacity of the refinement scratch (floats)
-    char* jobs_dev = nullptr;
-    size_t jobs_bytes = 0;
-    char* jobs_pinned = nullptr;
-    cudaEvent_t jobs_ev = nullptr;
-    bool jobs_valid = false;
-    std::vector<char> jobs_last;
-    cudaStream_t cap_stream = nullptr;
-    struct Graph {
-        std::vector<int64_t> key;
-        cudaGraphExec_t exec;
-    };
-    std::vector<Graph> graphs;
-    dis::LaunchCfg lc{};
-    bool use_graphs = true;
-    std::string err = "no error";
-};
 
 namespace {
 
@@ -797,3 +773,20 @@ LaunchCfg stage_launch_cfg() { return stage_lc(); }
 void set_thread_error(const std::string& msg) { g_err = msg; }
 
 }  // namespace dis
+
+// ---- host helpers shared with the backward pass (dis_backward.cu) ------------------------
+namespace dis_host {
+
+int pitch_of_w(int w) { return pitch_of(w); }
+int level_dim_of(int d, int s) { return level_dim(d, s); }
+int stride_of_params(const dis_params& p) { return stride_of(p); }
+int grid_count(int L, int ps, int stride) { return grid_n(L, ps, stride); }
+dis_status validate_params(const dis_params* p, std::string& err) { return validate(p, err); }
+dis_status levels_of(int W, int H, const dis_params& p, int& ss, int& sf, std::string& err)
+{
+    return resolve_levels(W, H, p, ss, sf, err);
+}
+dis_status set_fail(dis_handle* h, dis_status st, const std::string& msg) { return fail(h, st, msg); }
+dis_status set_cuda_fail(dis_handle* h, cudaError_t e, const char* what) { return cuda_fail(h, e, what); }
+
+}  // namespace dis_host

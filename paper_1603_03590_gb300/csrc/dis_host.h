@@ -1,0 +1,50 @@
+// Private host-side declarations of the DIS library: the handle and helpers shared by the
+// forward (dis_api.cu) and backward (dis_backward.cu) translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dis.h"
+#include "dis_internal.cuh"
+
+// The handle: one device arena (max_batch slots of per-level planes, a refinement scratch,
+// a job-table region), the job upload state and the CUDA-graph cache.
+struct dis_handle {
+    int max_w = 0, max_h = 0, max_batch = 0, C = 1, levels = 0, device = 0;
+    char* arena = nullptr;
+    size_t arena_bytes = 0, slot_bytes = 0;
+    std::vector<size_t> off_img, off_U, off_pu, off_pui, off_pst;  // per level, within a slot
+    size_t off_rs = 0;
+    size_t rs_floats = 0;  // capacity of the refinement scratch (floats)
+    char* jobs_dev = nullptr;
+    size_t jobs_bytes = 0;
+    char* jobs_pinned = nullptr;
+    cudaEvent_t jobs_ev = nullptr;
+    bool jobs_valid = false;
+    std::vector<char> jobs_last;
+    cudaStream_t cap_stream = nullptr;
+    struct Graph {
+        std::vector<int64_t> key;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    dis::LaunchCfg lc{};
+    bool use_graphs = true;
+    std::string err = "no error";
+};
+
+
+namespace dis_host {
+int pitch_of_w(int w);
+int level_dim_of(int d, int s);
+int stride_of_params(const dis_params& p);
+int grid_count(int L, int ps, int stride);
+dis_status validate_params(const dis_params* p, std::string& err);
+dis_status levels_of(int W, int H, const dis_params& p, int& ss, int& sf, std::string& err);
+dis_status set_fail(dis_handle* h, dis_status st, const std::string& msg);
+dis_status set_cuda_fail(dis_handle* h, cudaError_t e, const char* what);
+}  // namespace dis_host

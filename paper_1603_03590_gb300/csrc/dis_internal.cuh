@@ -129,9 +129,76 @@ struct RefineArgs {
 };
 cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, const RefineArgs& a,
                           const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_refine_prepare(const Jobs<LevelJob>& js, long long total_pix, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_refine_weights(const Jobs<LevelJob>& js, long long total_pix, const RefineArgs& a,
+                                  const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_refine_half_sweep(const Jobs<LevelJob>& js, long long total_half, int colour, float omega,
+                                     const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_upsample(const Jobs<UpJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
 
 LaunchCfg query_launch_cfg();
+
+// ---- differentiable form: FP64 replay and adjoint of one level of one pair ---------------
+// Adjoint planes (level pitch x height each): gD[9] gsys[6] gdU[2] gmid[8] tmp[4] gIx gIy gI1w.
+enum { ADJ_GD = 0, ADJ_GSYS = 9, ADJ_GDU = 15, ADJ_GM = 17, ADJ_GT = 25, ADJ_GIX = 29, ADJ_GIY = 30,
+       ADJ_GI1W = 31, ADJ_PLANES = 32 };
+
+struct Lvl64 {
+    const double* S0;         // level images (0..255 scale), row pitch `pitch`
+    const double* S1;
+    const double2* U;         // refinement input: the densified flow (dense w*h)
+    double* rs;               // refinement scratch ((15 + 8) planes, C = 1 layout of rs_*)
+    double* ga;               // adjoint planes, ADJ_PLANES x plane
+    double* gS0;              // gradient of S0 (accumulated, pitch)
+    unsigned long long* gS1;  // gradient of S1 in 2^-40 fixed point (accumulated, pitch)
+    double2* gU;              // gradient of the densified flow (accumulated, dense)
+    long long plane;
+    int w, h, pitch;
+    double delta, gamma, alpha, omega;
+};
+
+struct Dens64 {
+    const double2* pu;   // patch flows u_i = u_init,i + Delta_i
+    double2* gpu;        // gradient of the patch flows
+    const double2* gUd;  // gradient of the densified flow (dense)
+    int nx, ny, ps, stride;
+};
+
+cudaError_t launch_prep64(const float* I, int w, int h, int in_pitch, double scale, double* S, int pitch,
+                          const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_pyr64(const double* in, int win, int hin, int pin, double* out, int wout, int hout, int pout,
+                         const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_uinit64(const Dens64& A, int w, int h, const double2* Uc, int wc, int hc, double cs,
+                           const float2* frozen, double2* pu, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_densify64(const double* S0, const double* S1, int w, int h, int pitch, const Dens64& A,
+                             const double2* Uc, int wc, int hc, double cs, double2* Ud, const LaunchCfg& lc,
+                             cudaStream_t s);
+cudaError_t launch_ref64_prepare(const Lvl64& L, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_ref64_weights(const Lvl64& L, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_ref64_sor(const Lvl64& L, int colour, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_ref64_apply(const Lvl64& L, double2* Uout, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_loss(const float* I0, const float* I1, int w, int h, int pitch, int C, const float2* flow, float eps,
+                        double* partials, int max_partials, double* loss_out, float2* gflow, float* gI0,
+                        unsigned long long* gI1acc, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_fx_to_float(const unsigned long long* acc, int apitch, float* out, int opitch, int w, int h,
+                               double scale, bool accumulate, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_fx_to_double(const unsigned long long* acc, int apitch, double* out, int opitch, int w, int h,
+                                double scale, bool accumulate, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_sor_bwd(const Lvl64& L, const double* st_du, const double* st_dv, int colour, const LaunchCfg& lc,
+                           cudaStream_t s);
+cudaError_t launch_weights_bwd(const Lvl64& L, const double* st_du, const double* st_dv, const LaunchCfg& lc,
+                               cudaStream_t s);
+cudaError_t launch_deriv_warp_bwd(const Lvl64& L, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_start_flow(const Lvl64& L, const double2* g, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_dens_bwd(const Lvl64& L, const Dens64& A, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_uinit_bwd(const Dens64& A, int w, int h, unsigned long long* gUc, int wc, int hc, double cs,
+                             const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_pyr_bwd(const double* gc, int wc, int hc, int pc, double* gf, int wf, int hf, int pf,
+                           const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_f2_to_d2(const float2* in, double2* out, long long n, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_d2_to_f2(const double2* in, float2* out, long long n, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_scale_out(const double* in, int ipitch, float* out, int opitch, int w, int h, double scale,
+                             const LaunchCfg& lc, cudaStream_t s);
 
 // Launch configuration of the handle-less entry points (cached per host thread).
 LaunchCfg stage_launch_cfg();

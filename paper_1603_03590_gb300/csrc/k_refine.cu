@@ -241,4 +241,31 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
     return cudaGetLastError();
 }
 
+// Single phases of the refinement, for the backward pass, which recomputes the forward states
+// (derivatives, lagged weights, the increment before every half-sweep) level by level.
+cudaError_t launch_refine_prepare(const Jobs<LevelJob>& js, long long total_pix, const LaunchCfg& lc, cudaStream_t s)
+{
+    const int gp = (int)std::min<long long>((total_pix + 255) / 256, (long long)lc.sm_count * lc.max_blocks_256);
+    refine_warp_kernel<<<gp, 256, 0, s>>>(js, total_pix);
+    refine_deriv1_kernel<<<gp, 256, 0, s>>>(js, total_pix);
+    refine_deriv2_kernel<<<gp, 256, 0, s>>>(js, total_pix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_weights(const Jobs<LevelJob>& js, long long total_pix, const RefineArgs& a,
+                                  const LaunchCfg& lc, cudaStream_t s)
+{
+    const int gp = (int)std::min<long long>((total_pix + 255) / 256, (long long)lc.sm_count * lc.max_blocks_256);
+    refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_half_sweep(const Jobs<LevelJob>& js, long long total_half, int colour, float omega,
+                                     const LaunchCfg& lc, cudaStream_t s)
+{
+    const int gh = (int)std::min<long long>((total_half + 255) / 256, (long long)lc.sm_count * lc.max_blocks_256);
+    refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, colour, omega);
+    return cudaGetLastError();
+}
+
 }  // namespace dis

@@ -79,6 +79,11 @@ _SIGS = {
     "dis_refine_level": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
     "dis_upsample_flow": (_i, [_vp, _i, _i, _f, _vp, _i, _i, _vp]),
     "dis_refine_level_noalloc": (_i, [_vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
+    "dis_photometric_loss_scratch_bytes": (_i64, [_i, _i, _i64, _i]),
+    "dis_photometric_loss": (_i, [_vp, _vp, _i, _i, _i64, _i, _vp, _f, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "dis_backward_workspace_bytes": (_i64, [_i, _i, _P]),
+    "dis_replay_flow": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "dis_backward": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -206,3 +211,31 @@ def dis_refine_level_noalloc(I0, I1, w, h, pitch, channels, U, outer, inner, del
     (for callers that cannot allocate device memory; see include/dis.h)."""
     _check(_lib.dis_refine_level_noalloc(_ptr(I0), _ptr(I1), w, h, pitch, channels, _ptr(U), outer, inner, delta,
                                          gamma, alpha, omega, _stream(stream)))
+
+
+def dis_photometric_loss_scratch_bytes(w, h, pitch, channels=1):
+    return _lib.dis_photometric_loss_scratch_bytes(w, h, pitch, channels)
+
+
+def dis_photometric_loss(I0, I1, w, h, pitch, channels, flow, eps, loss_out, grad_flow, grad_I0, grad_I1, scratch,
+                         scratch_bytes, stream=None):
+    _check(_lib.dis_photometric_loss(_ptr(I0), _ptr(I1), w, h, pitch, channels, _ptr(flow), eps, _ptr(loss_out),
+                                     _ptr(grad_flow), _ptr(grad_I0), _ptr(grad_I1), _ptr(scratch), scratch_bytes,
+                                     _stream(stream)))
+
+
+def dis_backward_workspace_bytes(w, h, params):
+    return _lib.dis_backward_workspace_bytes(w, h, ctypes.byref(params))
+
+
+def dis_replay_flow(handle, I0, I1, w, h, pitch, params, init_flow, frozen, flow_out, workspace, workspace_bytes,
+                    stream=None):
+    _check(_lib.dis_replay_flow(handle, _ptr(I0), _ptr(I1), w, h, pitch, ctypes.byref(params), _ptr(init_flow),
+                                _ptr(frozen), _ptr(flow_out), _ptr(workspace), workspace_bytes, _stream(stream)), handle)
+
+
+def dis_backward(handle, I0, I1, w, h, pitch, params, init_flow, frozen, grad_flow, grad_I0, grad_I1, grad_pitch,
+                 grad_init_flow, workspace, workspace_bytes, stream=None):
+    _check(_lib.dis_backward(handle, _ptr(I0), _ptr(I1), w, h, pitch, ctypes.byref(params), _ptr(init_flow),
+                             _ptr(frozen), _ptr(grad_flow), _ptr(grad_I0), _ptr(grad_I1), grad_pitch,
+                             _ptr(grad_init_flow), _ptr(workspace), workspace_bytes, _stream(stream)), handle)

@@ -1,0 +1,195 @@
+"""Adjoint of the differentiable DIS map against FP64 central finite differences.
+
+The map replays every patch's recorded search increment (u_i = u_init,i + Delta_i, Delta_i
+frozen) and differentiates through the initial-displacement sampling, densification (Eq. 3),
+ten unrolled red-black SOR sweeps per level (Sec. 2.3) and the pyramid, into the mean
+Charbonnier photometric loss.  The GPU's analytic gradient (the FP64 replay and adjoint of
+dis_backward, through torch.autograd) is compared with central differences (step 1e-4) of the FP64 oracle run with
+the same frozen increments, at 200 seeded coordinates of I0, I1 and the initial flow.  The
+map is not smooth at the scale of that step everywhere: the robust weights Psi'(a^2) =
+1 / (2 sqrt(a^2 + eps^2)), eps = 0.001, bend sharply where residuals are near eps, and bilinear
+cells and the max(1, |d|) branch give kinks.  A coordinate is therefore compared only when its
+central difference has converged at step h (halving the step changes it by less than 0.3 of
+the tolerance) and no discrete decision (the oracle's decision trace) flips within h/2 of the
+point; the others are counted and reported.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_03590_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-3
+H_STEP = 1e-4
+PARAMS = dict(patch_size=8, overlap=0.5, grad_iters=16, coarsest_scale=3, var_outer=1, var_inner=10)
+
+_W = {}
+
+
+def _init_worker(I0, I1, rec, init, kw):
+    _W.update(I0=I0, I1=I1, rec=rec, init=init, q=oracle.params(**kw))
+
+
+def _fd_task(task):
+    kind, idx, step = task
+    I0, I1, init = _W["I0"].copy(), _W["I1"].copy(), _W["init"].copy()
+    arr = {"I0": I0, "I1": I1, "init": init}[kind]
+    arr.reshape(-1)[idx] += step
+    flow, hv = oracle.dis_flow(I0, I1, _W["q"], init_flow=init, frozen=_W["rec"], want_hash=True)
+    loss, hv2 = oracle.charbonnier_loss(I0, I1, flow, 1e-3, hash_seed=hv)
+    return loss, hv2
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_03590_gb300 import build
+    build.build()
+    from paper_1603_03590_gb300 import autograd, dis
+    return torch, dis, autograd, torch.device("cuda:0")
+
+
+def _pair(seed):
+    I0, I1, _ = synth.layered_pair(seed, width=512, height=256, max_disp=20.0)
+    return I0, I1
+
+
+def test_photometric_loss_gradient_matches_fd(env):
+    torch, dis, ag, dev = env
+    g = np.random.default_rng(0)
+    I0, I1 = _pair(3001)
+    flow = (g.normal(0, 1.0, (256, 512, 2)) + np.array([3.3, -1.2])).astype(np.float32)
+    a = torch.tensor(I0, device=dev, requires_grad=True)
+    b = torch.tensor(I1, device=dev, requires_grad=True)
+    f = torch.tensor(flow, device=dev, requires_grad=True)
+    loss = ag.photometric_loss(a, b, f)
+    loss.backward()
+    ref = oracle.charbonnier_loss(I0, I1, flow)
+    assert abs(float(loss) - ref) <= 1e-6 * max(1.0, abs(ref))
+    ga, gb, gf = a.grad.cpu().numpy(), b.grad.cpu().numpy(), f.grad.cpu().numpy()
+    for _ in range(30):
+        k = int(g.integers(0, 3))
+        arr, grad = [(I0, ga), (I1, gb), (flow, gf)][k]
+        idx = int(g.integers(0, arr.size))
+        vals, hs = [], []
+        for sgn in (1, -1):
+            c = [x.astype(np.float64).copy() for x in (I0, I1, flow)]
+            c[k].reshape(-1)[idx] += sgn * H_STEP
+            v, hv = oracle.charbonnier_loss(c[0], c[1], c[2], 1e-3, hash_seed=0)
+            vals.append(v)
+            hs.append(hv)
+        if hs[0] != hs[1]:
+            continue
+        fd = (vals[0] - vals[1]) / (2 * H_STEP)
+        an = float(grad.reshape(-1)[idx])
+        assert abs(an - fd) <= REL_TOL * max(abs(fd), 1e-7) + 1e-9, (k, idx, an, fd)
+
+
+def test_adjoint_matches_fp64_finite_differences(env):
+    torch, dis, ag, dev = env
+    W, H = 512, 256
+    I0, I1 = _pair(3000)
+    dd = ag.DifferentiableDIS(W, H, **PARAMS)
+    try:
+        hs, ws = dd.coarsest_shape(W, H)
+        from scipy import ndimage
+        g = np.random.default_rng(7)
+        init = np.stack([ndimage.gaussian_filter(g.normal(0, 1.0, (hs, ws)), 2.0) for _ in range(2)], -1)
+        init = init.astype(np.float32)
+        a = torch.tensor(I0, device=dev, requires_grad=True)
+        b = torch.tensor(I1, device=dev, requires_grad=True)
+        it = torch.tensor(init, device=dev, requires_grad=True)
+        flow = dd(a, b, it)
+        loss = ag.photometric_loss(a, b, flow)
+        loss.backward()
+        grads = {"I0": a.grad.cpu().numpy().astype(np.float64), "I1": b.grad.cpu().numpy().astype(np.float64),
+                 "init": it.grad.cpu().numpy().astype(np.float64)}
+        # the increments the forward recorded (the FP32 search is deterministic: record them
+        # again) reproduce the forward's FP64 replay exactly
+        n = dis.dis_levels(W, H, dd.params)[2]
+        rec = torch.empty((n, 2), device=dev)
+        tmp = torch.empty((H, W, 2), device=dev)
+        dis.dis_compute_flow_ex(dd.handle, a.detach(), b.detach(), W, H, W, dd.params, it.detach(), None, rec, None,
+                                tmp)
+        nb = dis.dis_backward_workspace_bytes(W, H, dd.params)
+        ws = torch.empty(nb, device=dev, dtype=torch.uint8)
+        fl2 = torch.empty((H, W, 2), device=dev)
+        dis.dis_replay_flow(dd.handle, a.detach(), b.detach(), W, H, W, dd.params, it.detach(), rec, fl2, ws, nb)
+        torch.cuda.synchronize()
+        assert torch.equal(fl2, flow.detach())
+        # the FP64 replay agrees with the FP32 flow to the end-to-end bar
+        dflow = (tmp - flow.detach()).abs()
+        assert float(dflow.mean()) <= 0.01 and float(torch.quantile(dflow.flatten(), 0.999)) <= 0.05
+        rec = rec.cpu().numpy().astype(np.float64)
+        # a second backward is bit-identical (fixed-point scatters)
+        a2 = a.detach().clone().requires_grad_(True)
+        b2 = b.detach().clone().requires_grad_(True)
+        it2 = it.detach().clone().requires_grad_(True)
+        ag.photometric_loss(a2, b2, dd(a2, b2, it2)).backward()
+        assert torch.equal(a2.grad, a.grad) and torch.equal(b2.grad, b.grad) and torch.equal(it2.grad, it.grad)
+    finally:
+        dd.close()
+    rng = np.random.default_rng(1234)
+    coords = ([("I0", int(i)) for i in rng.integers(0, I0.size, 80)] +
+              [("I1", int(i)) for i in rng.integers(0, I1.size, 80)] +
+              [("init", int(i)) for i in rng.integers(0, init.size, 40)])
+    steps = (H_STEP, -H_STEP, 0.5 * H_STEP, -0.5 * H_STEP)
+    tasks = [(k, i, st) for k, i in coords for st in steps] + [("I0", 0, 0.0)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1), initializer=_init_worker,
+                  initargs=(I0.astype(np.float64), I1.astype(np.float64), rec, init.astype(np.float64),
+                            PARAMS)) as pool:
+        res = pool.map(_fd_task, tasks, chunksize=4)
+    h0 = res[-1][1]
+    flips, unconverged, errs = 0, 0, []
+    for c, (k, i) in enumerate(coords):
+        (lp, hp), (lm, hm), (lp2, hp2), (lm2, hm2) = res[4 * c:4 * c + 4]
+        # a decision boundary within h/2 of the point makes every central difference return the
+        # mean of the two one-sided slopes, whatever the step: not comparable
+        if hp2 != h0 or hm2 != h0:
+            flips += 1
+            continue
+        fd = (lp - lm) / (2 * H_STEP)
+        fd2 = (lp2 - lm2) / H_STEP
+        an = grads[k].reshape(-1)[i]
+        # the central difference at step h has converged when halving the step changes it by
+        # less than 0.3 tol (its own error is then 4/3 of that): the map is smooth at scale h
+        if abs(fd - fd2) > 0.3 * REL_TOL * max(abs(fd), 1e-12):
+            unconverged += 1
+            continue
+        errs.append((abs(an - fd) / max(abs(fd), 1e-12), k, i, an, fd))
+    errs.sort(reverse=True)
+    print("adjoint vs FD (step %g): %d coordinates compared; excluded: %d with a decision flip within h/2, "
+          "%d whose FD has not converged at that step; worst: %s" % (H_STEP, len(errs), flips, unconverged, errs[:5]))
+    assert len(errs) >= 60
+    mags = np.array([abs(e[4]) for e in errs])
+    floor = 1e-3 * np.median(mags)  # gradients below this are compared absolutely
+    bad = [e for e in errs if abs(e[3] - e[4]) > REL_TOL * max(abs(e[4]), floor)]
+    assert not bad, bad[:10]
+
+
+def test_batch_of_eight_pairs(env):
+    torch, dis, ag, dev = env
+    W, H = 512, 256
+    dd = ag.DifferentiableDIS(W, H, **PARAMS)
+    try:
+        total = 0.0
+        for k in range(8):
+            I0, I1 = _pair(3000 + k)
+            a = torch.tensor(I0, device=dev, requires_grad=True)
+            b = torch.tensor(I1, device=dev, requires_grad=True)
+            loss = ag.photometric_loss(a, b, dd(a, b))
+            loss.backward()
+            assert torch.isfinite(a.grad).all() and torch.isfinite(b.grad).all()
+            assert float(a.grad.abs().sum()) > 0 and float(b.grad.abs().sum()) > 0
+            total += float(loss)
+        assert np.isfinite(total)
+    finally:
+        dd.close()
