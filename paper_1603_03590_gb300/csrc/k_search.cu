@@ -4,17 +4,18 @@
 // A group of LPP lanes (8, 16 or 32 by patch size) owns one patch; lane l of the group owns
 // patch pixels l, l + LPP, ... (PPL of them).  The prologue stages the (ps+2)^2 window of I0
 // around the patch in shared memory and computes, in registers, the Sobel/8 gradients
-// S' = grad T, the mean-normalised template T and the 2x2 Hessian H' = sum S'^T S' (group
-// shuffle reductions).
+// S' = grad T of the mean-normalised template T and the 2x2 Hessian H' = sum S'^T S' (group
+// shuffle reductions); sum T and sum S' are kept for the update below.
 //
 // Iterations.  u is shared by the whole patch, so every pixel samples I1 with the same
-// fractional weights (ax, ay): I1(x + u) = t0 + ax t1 + ay (t2 + ax t3) with the pixel's four
-// taps folded into t0..t3.  The taps stay in registers and are re-read only when the integer
-// part of u changes (the clamped taps also encode the image border), so a converged patch
-// iterates from registers alone: 3 FMA per sample.  The mean-normalised residual is reduced in
-// one pass relative to the previous iteration's mean m:
-//   S0 = sum (w - m),  Sg = sum S' (w - m - T),  b = Sg - (S0 / n) sum S'  ( = sum S'^T (w - mean w - T) )
-// which keeps the three group sums independent and their terms small.  u <- u - H'^-1 b.
+// fractional weights (ax, ay).  Each pixel keeps its four bilinear taps folded into
+// t0..t3 with t0 = I1(tap) - T - m, m a reference intensity fixed at the last re-read, so that
+//   w'' = t0 + ax t1 + ay (t2 + ax t3) = I1(x + u) - T(x) - m.
+// The taps stay in registers and are re-read only when the integer part of u changes (the
+// clamped taps also encode the image border); a converged patch iterates from registers:
+// 3 FMA per sample.  With A0 = sum w'', A = sum S' w'' and e = (A0 + sum T) / n (= mean w - m):
+//   b = sum S'^T (w - mean w - T) = A - e sum S',   u <- u - H'^-1 b,
+// all terms being residual-sized, which keeps the FP32 sums accurate.
 #include <climits>
 
 #include "dis_device.cuh"
@@ -29,12 +30,14 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask)
     return v;
 }
 
-template <int LPP, int PPL>
-__global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total, int ps,
-                                                     int stride, int iters)
+// PSC: compile-time patch size (0: the runtime `ps_rt`).
+template <int LPP, int PPL, int PSC>
+__global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
+                                                     int ps_rt, int stride, int iters)
 {
     extern __shared__ float smem[];
     constexpr int GPW = 32 / LPP;  // patches per warp
+    const int ps = PSC ? PSC : ps_rt;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int grp = lane / LPP, gl = lane % LPP;
     const unsigned gmask = (LPP == 32) ? 0xffffffffu : (((1u << LPP) - 1u) << (grp * LPP));
@@ -57,47 +60,49 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
             u += f.x;
             v += f.y;
         } else {
-            // ---- template window, gradients, template, Hessian (once per patch)
+            // ---- template window, gradients, Hessian (once per patch)
             for (int t = gl; t < ws * ws; t += LPP) {
                 const int a = t % ws, b = t / ws;
                 win[t] = __ldg(J.S0 + (long long)clampi(py - 1 + b, 0, h - 1) * pitch + clampi(px - 1 + a, 0, w - 1));
             }
             __syncwarp(gmask);
-            float T[PPL], gx[PPL], gy[PPL];
+            float gx[PPL], gy[PPL];
             float s0 = 0.0f;
 #pragma unroll
             for (int m = 0; m < PPL; ++m) {
                 const int k = gl + LPP * m;
+                gx[m] = gy[m] = 0.0f;
                 if (k < n) {
                     const int kx = k % ps, ky = k / ps;
                     const float* c0 = win + ky * ws + kx;  // (x-1, y-1)
                     const float* c1 = c0 + ws;
                     const float* c2 = c1 + ws;
-                    T[m] = c1[1];
                     s0 += c1[1];
                     gx[m] = 0.125f * ((c0[2] - c0[0]) + 2.0f * (c1[2] - c1[0]) + (c2[2] - c2[0]));
                     gy[m] = 0.125f * ((c2[0] - c0[0]) + 2.0f * (c2[1] - c0[1]) + (c2[2] - c0[2]));
-                } else {
-                    T[m] = gx[m] = gy[m] = 0.0f;
                 }
             }
-            __syncwarp(gmask);
             const float mean0 = group_sum<LPP>(s0, gmask) * inv_n;
-            float h00 = 0.0f, h01 = 0.0f, h11 = 0.0f, sgx = 0.0f, sgy = 0.0f;
+            float h00 = 0.0f, h01 = 0.0f, h11 = 0.0f, sgx = 0.0f, sgy = 0.0f, sT = 0.0f;
 #pragma unroll
             for (int m = 0; m < PPL; ++m) {
-                if (gl + LPP * m < n) T[m] -= mean0;
+                const int k = gl + LPP * m;
+                if (k < n) sT += win[(k / ps + 1) * ws + k % ps + 1] - mean0;
                 h00 = fmaf(gx[m], gx[m], h00);
                 h01 = fmaf(gx[m], gy[m], h01);
                 h11 = fmaf(gy[m], gy[m], h11);
                 sgx += gx[m];
                 sgy += gy[m];
             }
-            h00 = group_sum<LPP>(h00, gmask);
-            h01 = group_sum<LPP>(h01, gmask);
-            h11 = group_sum<LPP>(h11, gmask);
-            sgx = group_sum<LPP>(sgx, gmask);
-            sgy = group_sum<LPP>(sgy, gmask);
+#pragma unroll
+            for (int o = LPP / 2; o > 0; o >>= 1) {
+                h00 += __shfl_xor_sync(gmask, h00, o);
+                h01 += __shfl_xor_sync(gmask, h01, o);
+                h11 += __shfl_xor_sync(gmask, h11, o);
+                sgx += __shfl_xor_sync(gmask, sgx, o);
+                sgy += __shfl_xor_sync(gmask, sgy, o);
+                sT += __shfl_xor_sync(gmask, sT, o);
+            }
             // 2x2 determinant with the product h01^2 split exactly (Kahan)
             const float p2 = h01 * h01;
             const float e2 = fmaf(h01, h01, -p2);
@@ -107,9 +112,11 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
                 st = 2;
             } else {
                 const float idet = 1.0f / det;
+                const float k00 = h11 * idet, k01 = -h01 * idet, k11 = h00 * idet;  // H'^-1
                 float t0[PPL], t1[PPL], t2[PPL], t3[PPL];
                 int ciu = INT_MIN, civ = INT_MIN;
-                float mref = mean0;
+                float mref = mean0;  // reference intensity of the folded taps
+                float mcur = mean0;  // latest estimate of the window mean
                 for (int it = 0; it < iters; ++it) {
                     const float uc = fminf(fmaxf(u, -1.0e7f), 1.0e7f);
                     const float vc = fminf(fmaxf(v, -1.0e7f), 1.0e7f);
@@ -120,14 +127,16 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
                         // the integer displacement moved: re-read the taps (clamped at the border)
                         ciu = iu;
                         civ = iv;
+                        mref = mcur;
                         const int xi = px + iu, yi = py + iv;
                         const bool inside = xi >= 0 && yi >= 0 && xi + ps <= w - 1 && yi + ps <= h - 1;
 #pragma unroll
                         for (int m = 0; m < PPL; ++m) {
                             const int k = gl + LPP * m;
-                            float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f;
+                            float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f, T = 0.0f;
                             if (k < n) {
                                 const int kx = k % ps, ky = k / ps;
+                                T = win[(ky + 1) * ws + kx + 1] - mean0;
                                 if (inside) {
                                     const float* p = J.S1 + (long long)(yi + ky) * pitch + (xi + kx);
                                     a = __ldg(p);
@@ -143,36 +152,44 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
                                     c = __ldg(r1 + x0);
                                     d = __ldg(r1 + x1);
                                 }
+                                t0[m] = (a - T) - mref;
+                            } else {
+                                t0[m] = 0.0f;
                             }
-                            t0[m] = a;
                             t1[m] = b - a;
                             t2[m] = c - a;
                             t3[m] = (d - c) - (b - a);
                         }
                     }
-                    float S0 = 0.0f, Sx = 0.0f, Sy = 0.0f;
+                    // two partial sums per quantity halve the dependency chains
+                    float A0a = 0.0f, A0b = 0.0f, Axa = 0.0f, Axb = 0.0f, Aya = 0.0f, Ayb = 0.0f;
 #pragma unroll
                     for (int m = 0; m < PPL; ++m) {
                         if (gl + LPP * m < n) {
                             const float wv = fmaf(ay, fmaf(ax, t3[m], t2[m]), fmaf(ax, t1[m], t0[m]));
-                            const float wd = wv - mref;
-                            const float r = wd - T[m];
-                            S0 += wd;
-                            Sx = fmaf(gx[m], r, Sx);
-                            Sy = fmaf(gy[m], r, Sy);
+                            if (m & 1) {
+                                A0b += wv;
+                                Axb = fmaf(gx[m], wv, Axb);
+                                Ayb = fmaf(gy[m], wv, Ayb);
+                            } else {
+                                A0a += wv;
+                                Axa = fmaf(gx[m], wv, Axa);
+                                Aya = fmaf(gy[m], wv, Aya);
+                            }
                         }
                     }
+                    float A0 = A0a + A0b, Ax = Axa + Axb, Ay = Aya + Ayb;
 #pragma unroll
                     for (int o = LPP / 2; o > 0; o >>= 1) {
-                        S0 += __shfl_xor_sync(gmask, S0, o);
-                        Sx += __shfl_xor_sync(gmask, Sx, o);
-                        Sy += __shfl_xor_sync(gmask, Sy, o);
+                        A0 += __shfl_xor_sync(gmask, A0, o);
+                        Ax += __shfl_xor_sync(gmask, Ax, o);
+                        Ay += __shfl_xor_sync(gmask, Ay, o);
                     }
-                    const float dm = S0 * inv_n;
-                    const float b0 = fmaf(-dm, sgx, Sx), b1 = fmaf(-dm, sgy, Sy);
-                    mref += dm;
-                    u -= (h11 * b0 - h01 * b1) * idet;
-                    v -= (h00 * b1 - h01 * b0) * idet;
+                    const float e = (A0 + sT) * inv_n;  // mean of the window minus mref
+                    const float b0 = fmaf(-e, sgx, Ax), b1 = fmaf(-e, sgy, Ay);
+                    mcur = mref + e;
+                    u -= fmaf(k00, b0, k01 * b1);
+                    v -= fmaf(k01, b0, k11 * b1);
                 }
                 const float ex = u - ui.x, ey = v - ui.y;
                 if (ex * ex + ey * ey > (float)(ps * ps)) {
@@ -181,6 +198,7 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
                     v = ui.y;
                 }
             }
+            __syncwarp(gmask);  // the window is rewritten by the next patch of this group
         }
         if (gl == 0) {
             J.pu[pk] = make_float2(u, v);
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
     }
 }
 
-template <int LPP, int PPL>
+template <int LPP, int PPL, int PSC>
 static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
                              const LaunchCfg& lc, cudaStream_t s)
 {
@@ -199,7 +217,7 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     const size_t smem = (size_t)per_block * (ps + 2) * (ps + 2) * sizeof(float);
     static int occ = 0;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL>, threads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC>, threads, smem) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
@@ -207,41 +225,40 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     long long blocks = (total + per_block - 1) / per_block;
     const long long cap = (long long)lc.sm_count * occ;
     if (blocks > cap) blocks = cap;
-    search_kernel<LPP, PPL><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
+    search_kernel<LPP, PPL, PSC><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
     return cudaGetLastError();
 }
 
 // Lanes per patch by patch size: 8 up to 8x8 (<= 8 pixels per lane), 16 up to 12x12 (<= 9),
-// 32 up to 16x16 (<= 8).
+// 32 up to 16x16 (<= 8); the 8x8 and 12x12 patches of the presets get compile-time sizes.
 cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
                           const LaunchCfg& lc, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
     const int n = ps * ps;
-    if (ps <= 8) {
+    if (ps == 8) return launch_lp<8, 8, 8>(js, total, ps, stride, iters, lc, s);
+    if (ps == 12) return launch_lp<16, 9, 12>(js, total, ps, stride, iters, lc, s);
+    if (ps < 8) {
         switch ((n + 7) / 8) {
-            case 1: return launch_lp<8, 1>(js, total, ps, stride, iters, lc, s);
-            case 2: return launch_lp<8, 2>(js, total, ps, stride, iters, lc, s);
-            case 3: return launch_lp<8, 3>(js, total, ps, stride, iters, lc, s);
-            case 4: return launch_lp<8, 4>(js, total, ps, stride, iters, lc, s);
-            case 5: return launch_lp<8, 5>(js, total, ps, stride, iters, lc, s);
-            case 6: return launch_lp<8, 6>(js, total, ps, stride, iters, lc, s);
-            case 7: return launch_lp<8, 7>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<8, 8>(js, total, ps, stride, iters, lc, s);
+            case 1: return launch_lp<8, 1, 0>(js, total, ps, stride, iters, lc, s);
+            case 2: return launch_lp<8, 2, 0>(js, total, ps, stride, iters, lc, s);
+            case 3: return launch_lp<8, 3, 0>(js, total, ps, stride, iters, lc, s);
+            case 4: return launch_lp<8, 4, 0>(js, total, ps, stride, iters, lc, s);
+            case 5: return launch_lp<8, 5, 0>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<8, 7, 0>(js, total, ps, stride, iters, lc, s);
         }
     }
-    if (ps <= 12) {
+    if (ps < 12) {
         switch ((n + 15) / 16) {
-            case 6: return launch_lp<16, 6>(js, total, ps, stride, iters, lc, s);
-            case 7: return launch_lp<16, 7>(js, total, ps, stride, iters, lc, s);
-            case 8: return launch_lp<16, 8>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<16, 9>(js, total, ps, stride, iters, lc, s);
+            case 6: return launch_lp<16, 6, 0>(js, total, ps, stride, iters, lc, s);
+            case 7: return launch_lp<16, 7, 0>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<16, 8, 0>(js, total, ps, stride, iters, lc, s);
         }
     }
     switch ((n + 31) / 32) {
-        case 6: return launch_lp<32, 6>(js, total, ps, stride, iters, lc, s);
-        case 7: return launch_lp<32, 7>(js, total, ps, stride, iters, lc, s);
-        default: return launch_lp<32, 8>(js, total, ps, stride, iters, lc, s);
+        case 6: return launch_lp<32, 6, 0>(js, total, ps, stride, iters, lc, s);
+        case 7: return launch_lp<32, 7, 0>(js, total, ps, stride, iters, lc, s);
+        default: return launch_lp<32, 8, 0>(js, total, ps, stride, iters, lc, s);
     }
 }
 
