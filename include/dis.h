@@ -143,6 +143,14 @@ dis_status dis_compute_flow_ex(dis_handle* h, const float* I0, const float* I1, 
  * repeat. */
 dis_status dis_compute_flow_batched(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream);
 
+/* Autotuner (not in the paper): time the variants the library offers for this workload - the
+ * number of lanes that share one patch in the inverse-search kernel - on the caller's pairs
+ * (the batched call, 4 runs per variant, synchronising `stream`) and keep the fastest in the
+ * handle for later calls with the same patch size.  The runs write the pairs' flow_out.
+ * *chosen_lanes (nullable) receives the choice. */
+dis_status dis_autotune(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream,
+                        int* chosen_lanes);
+
 /* ---- per-stage entry points (one pyramid level; used for per-stage parity tests and by
  * callers that drive the level loop themselves).  No allocation; caller-owned buffers. */
 

@@ -201,6 +201,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     plan.key.push_back(n);
     const int32_t* pw = reinterpret_cast<const int32_t*>(&p);
     for (size_t i = 0; i < sizeof(dis_params) / 4; ++i) plan.key.push_back(pw[i]);
+    plan.key.push_back(hd->search_lanes[p.patch_size]);
 
     auto slot = [&](int i) { return hd->arena + (size_t)i * hd->slot_bytes; };
     auto img = [&](int i, int s) { return reinterpret_cast<float*>(slot(i) + hd->off_img[s]); };
@@ -364,7 +365,7 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                 break;
             case Phase::LEVEL: {
                 auto js = dis::device_jobs(reinterpret_cast<const LevelJob*>(tab), ph.n);
-                e = dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s);
+                e = dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s, hd->search_lanes[ps]);
                 if (e == cudaSuccess) e = dis::launch_densify(js, ph.total2, ps, stride, hd->lc, s);
                 for (const auto& c : plan.copies)
                     if (e == cudaSuccess && c.s == ph.s) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s);
@@ -773,6 +774,53 @@ LaunchCfg stage_launch_cfg() { return stage_lc(); }
 void set_thread_error(const std::string& msg) { g_err = msg; }
 
 }  // namespace dis
+
+// ---- autotuner ---------------------------------------------------------------------------
+extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n, const dis_params* p, void* stream,
+                                   int* chosen_lanes)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    std::string verr;
+    dis_status vst = validate(p, verr);
+    if (vst != DIS_OK) return fail(hd, vst, verr);
+    int opts[8];
+    const int nopt = dis::search_lane_options(p->patch_size, opts);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(hd, DIS_ERR_CUDA, "dis_autotune: event creation failed");
+    }
+    const int ps = p->patch_size;
+    const int keep = hd->search_lanes[ps];
+    float best_ms = 1e30f;
+    int best = keep;
+    dis_status st = DIS_OK;
+    for (int k = 0; k < nopt && st == DIS_OK; ++k) {
+        hd->search_lanes[ps] = opts[k];
+        st = dis_compute_flow_batched(hd, pairs, n, p, stream);  // warm-up, builds the graph
+        if (st != DIS_OK) break;
+        float tot = 0.0f;
+        for (int r = 0; r < 3 && st == DIS_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = dis_compute_flow_batched(hd, pairs, n, p, stream);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(hd, cudaGetLastError(), "dis_autotune");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
+        }
+        if (st == DIS_OK && tot < best_ms) {
+            best_ms = tot;
+            best = opts[k];
+        }
+    }
+    hd->search_lanes[ps] = (st == DIS_OK) ? best : keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (chosen_lanes) *chosen_lanes = hd->search_lanes[ps];
+    return st;
+}
 
 // ---- host helpers shared with the backward pass (dis_backward.cu) ------------------------
 namespace dis_host {

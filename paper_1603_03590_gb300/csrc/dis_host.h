@@ -34,6 +34,7 @@ struct dis_handle {
     std::vector<Graph> graphs;
     dis::LaunchCfg lc{};
     bool use_graphs = true;
+    int search_lanes[17] = {};  // autotuned lanes per patch by patch size (0 = default)
     std::string err = "no error";
 };
 

@@ -119,8 +119,11 @@ cudaError_t launch_prep(const Jobs<PrepJob>& js, long long total, const LaunchCf
 cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_sobel(const float* in, int w, int h, int pitch, float* gx, float* gy, int out_pitch,
                          const LaunchCfg& lc, cudaStream_t s);
+// lanes: lanes per patch (0 = default for the patch size; see search_lane_options).
 cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
-                          const LaunchCfg& lc, cudaStream_t s);
+                          const LaunchCfg& lc, cudaStream_t s, int lanes = 0);
+// Group widths the search kernel offers for patch size ps (first = default); returns the count.
+int search_lane_options(int ps, int* out);
 cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, int stride, const LaunchCfg& lc,
                            cudaStream_t s);
 struct RefineArgs {

@@ -230,14 +230,28 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
 }
 
 // Lanes per patch by patch size: 8 up to 8x8 (<= 8 pixels per lane), 16 up to 12x12 (<= 9),
-// 32 up to 16x16 (<= 8); the 8x8 and 12x12 patches of the presets get compile-time sizes.
+// 32 up to 16x16 (<= 8); the 8x8 and 12x12 patches of the presets get compile-time sizes and
+// alternative group widths `lanes` (0 = the default) for the autotuner.
 cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
-                          const LaunchCfg& lc, cudaStream_t s)
+                          const LaunchCfg& lc, cudaStream_t s, int lanes)
 {
     if (total <= 0) return cudaSuccess;
     const int n = ps * ps;
-    if (ps == 8) return launch_lp<8, 8, 8>(js, total, ps, stride, iters, lc, s);
-    if (ps == 12) return launch_lp<16, 9, 12>(js, total, ps, stride, iters, lc, s);
+    if (ps == 8) {
+        switch (lanes) {
+            case 4: return launch_lp<4, 16, 8>(js, total, ps, stride, iters, lc, s);
+            case 16: return launch_lp<16, 4, 8>(js, total, ps, stride, iters, lc, s);
+            case 32: return launch_lp<32, 2, 8>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<8, 8, 8>(js, total, ps, stride, iters, lc, s);
+        }
+    }
+    if (ps == 12) {
+        switch (lanes) {
+            case 8: return launch_lp<8, 18, 12>(js, total, ps, stride, iters, lc, s);
+            case 32: return launch_lp<32, 5, 12>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<16, 9, 12>(js, total, ps, stride, iters, lc, s);
+        }
+    }
     if (ps < 8) {
         switch ((n + 7) / 8) {
             case 1: return launch_lp<8, 1, 0>(js, total, ps, stride, iters, lc, s);
@@ -260,6 +274,20 @@ cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int
         case 7: return launch_lp<32, 7, 0>(js, total, ps, stride, iters, lc, s);
         default: return launch_lp<32, 8, 0>(js, total, ps, stride, iters, lc, s);
     }
+}
+
+int search_lane_options(int ps, int* out)
+{
+    if (ps == 8) {
+        out[0] = 8, out[1] = 4, out[2] = 16, out[3] = 32;
+        return 4;
+    }
+    if (ps == 12) {
+        out[0] = 16, out[1] = 8, out[2] = 32;
+        return 3;
+    }
+    out[0] = 0;
+    return 1;
 }
 
 }  // namespace dis

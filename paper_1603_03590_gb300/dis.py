@@ -72,6 +72,7 @@ _SIGS = {
     "dis_compute_flow": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp]),
     "dis_compute_flow_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dis_compute_flow_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp]),
+    "dis_autotune": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, ctypes.POINTER(_i)]),
     "dis_pyr_down": (_i, [_vp, _i, _i, _i64, _vp, _i64, _vp]),
     "dis_sobel": (_i, [_vp, _i, _i, _i64, _vp, _vp, _i64, _vp]),
     "dis_search_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _vp, _vp, _vp, _vp]),
@@ -171,6 +172,13 @@ def make_pairs(items):
 
 def dis_compute_flow_batched(handle, pairs, n, params, stream=None):
     _check(_lib.dis_compute_flow_batched(handle, pairs, n, ctypes.byref(params), _stream(stream)), handle)
+
+
+def dis_autotune(handle, pairs, n, params, stream=None):
+    """Time the search-kernel variants on these pairs, keep the fastest; returns its lanes."""
+    lanes = _i()
+    _check(_lib.dis_autotune(handle, pairs, n, ctypes.byref(params), _stream(stream), ctypes.byref(lanes)), handle)
+    return lanes.value
 
 
 def dis_pyr_down(inp, w, h, in_pitch, out, out_pitch, stream=None):

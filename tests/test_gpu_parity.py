@@ -404,3 +404,28 @@ def test_batched_matches_plain_bit_exact(env):
             dis.dis_destroy(h)
         for k, f in enumerate(flows):
             assert np.array_equal(host(f), plain[k]), (preset, sizes[k])
+
+
+@pytest.mark.parametrize("preset", ["fast", "dense"])
+def test_autotuned_search_variant_keeps_parity(env, preset):
+    torch, dis, dev = env
+    pairs = [synth.layered_pair(60 + k, width=320, height=240, n_ellipses=6, max_disp=12.0) for k in range(3)]
+    p = dis.dis_default_params(preset)
+    h = dis.dis_create(320, 240, len(pairs), 1)
+    try:
+        dev_pairs = [(to_dev(torch, a, dev), to_dev(torch, b, dev)) for a, b, _ in pairs]
+        flows = [torch.zeros((240, 320, 2), device=dev) for _ in pairs]
+        arr = dis.make_pairs([(a, b, 320, 240, 320, f) for (a, b), f in zip(dev_pairs, flows)])
+        dis.dis_compute_flow_batched(h, arr, len(pairs), p)
+        torch.cuda.synchronize()
+        default = [host(f) for f in flows]
+        lanes = dis.dis_autotune(h, arr, len(pairs), p)
+        assert lanes in ((8, 4, 16, 32) if p.patch_size == 8 else (16, 8, 32))
+        dis.dis_compute_flow_batched(h, arr, len(pairs), p)
+        torch.cuda.synchronize()
+    finally:
+        dis.dis_destroy(h)
+    for k, f in enumerate(flows):
+        d = np.abs(host(f) - default[k])
+        print("autotuned lanes %d vs default: mean %.2e p99.9 %.2e" % (lanes, d.mean(), np.quantile(d, 0.999)))
+        assert d.mean() <= E2E_MEAN and np.quantile(d, 0.999) <= E2E_P999
