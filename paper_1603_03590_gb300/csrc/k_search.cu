@@ -1,21 +1,25 @@
 // Inverse-compositional patch search of DIS (Sec. 2.1; supplementary Sec. A, Eq. solvereqinv;
 // Alg. 1 steps 1-3 and the outlier reset of step 4).
 //
-// A group of LPP lanes (8, 16 or 32 by patch size) owns one patch; lane l of the group owns
-// patch pixels l, l + LPP, ... (PPL of them).  The prologue stages the (ps+2)^2 window of I0
-// around the patch in shared memory and computes, in registers, the Sobel/8 gradients
-// S' = grad T of the mean-normalised template T and the 2x2 Hessian H' = sum S'^T S' (group
-// shuffle reductions); sum T and sum S' are kept for the update below.
+// A group of LPP lanes (4, 8, 16 or 32) owns one patch; lane l of the group owns patch pixels
+// l, l + LPP, ... (PPL of them).  The prologue stages the (ps+2)^2 window of I0 around the
+// patch in shared memory and computes the Sobel/8 gradients S' = grad T of the mean-normalised
+// template T (kept in registers) and, by group shuffle reductions, the 2x2 Hessian
+// H' = sum S'^T S', sum S' and sum T.
 //
-// Iterations.  u is shared by the whole patch, so every pixel samples I1 with the same
-// fractional weights (ax, ay).  Each pixel keeps its four bilinear taps folded into
-// t0..t3 with t0 = I1(tap) - T - m, m a reference intensity fixed at the last re-read, so that
-//   w'' = t0 + ax t1 + ay (t2 + ax t3) = I1(x + u) - T(x) - m.
-// The taps stay in registers and are re-read only when the integer part of u changes (the
-// clamped taps also encode the image border); a converged patch iterates from registers:
-// 3 FMA per sample.  With A0 = sum w'', A = sum S' w'' and e = (A0 + sum T) / n (= mean w - m):
-//   b = sum S'^T (w - mean w - T) = A - e sum S',   u <- u - H'^-1 b,
-// all terms being residual-sized, which keeps the FP32 sums accurate.
+// Iterations.  u is shared by the whole patch, so while the integer part of u stays in one cell
+// every pixel samples I1 with the same fractional weights (ax, ay):
+//   w''(x) = I1(x + u) - T(x) - m = t0 + ax t1 + ay (t2 + ax t3),
+// t0 = a - T - m, t1 = b - a, t2 = c - a, t3 = d - c - b + a from the pixel's four taps a..d and a
+// reference intensity m.  The patch sums the update needs therefore factor into twelve sums
+// that depend on the cell only,
+//   sum w'' = T0 + ax T1 + ay (T2 + ax T3),   T_k = sum t_k,
+//   sum S' w'' = G0 + ax G1 + ay (G2 + ax G3), G_k = sum S' t_k,
+// which are rebuilt (taps read, clamped at the border, and reduced over the group) only when
+// the integer part of u changes.  Every other iteration costs a few scalar FMAs:
+//   e = (sum w'' + sum T) / n (mean of the window minus m),  b = sum S' w'' - e sum S',
+//   u <- u - H'^-1 b  (= sum S'^T (w - mean w - T), Eq. solvereqinv with mean-normalisation).
+// m follows the window mean at every rebuild, so all sums are residual-sized.
 #include <climits>
 
 #include "dis_device.cuh"
@@ -113,10 +117,9 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
             } else {
                 const float idet = 1.0f / det;
                 const float k00 = h11 * idet, k01 = -h01 * idet, k11 = h00 * idet;  // H'^-1
-                float t0[PPL], t1[PPL], t2[PPL], t3[PPL];
+                float Q[12];  // T0..T3, Gx0..Gx3, Gy0..Gy3 of the current cell
                 int ciu = INT_MIN, civ = INT_MIN;
-                float mref = mean0;  // reference intensity of the folded taps
-                float mcur = mean0;  // latest estimate of the window mean
+                float mref = mean0, mcur = mean0;
                 for (int it = 0; it < iters; ++it) {
                     const float uc = fminf(fmaxf(u, -1.0e7f), 1.0e7f);
                     const float vc = fminf(fmaxf(v, -1.0e7f), 1.0e7f);
@@ -124,19 +127,21 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
                     const float ax = uc - fu, ay = vc - fv;
                     const int iu = (int)fu, iv = (int)fv;
                     if (iu != ciu || iv != civ) {
-                        // the integer displacement moved: re-read the taps (clamped at the border)
+                        // the integer displacement moved: rebuild the cell sums from the taps
                         ciu = iu;
                         civ = iv;
                         mref = mcur;
                         const int xi = px + iu, yi = py + iv;
                         const bool inside = xi >= 0 && yi >= 0 && xi + ps <= w - 1 && yi + ps <= h - 1;
 #pragma unroll
+                        for (int q = 0; q < 12; ++q) Q[q] = 0.0f;
+#pragma unroll
                         for (int m = 0; m < PPL; ++m) {
                             const int k = gl + LPP * m;
-                            float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f, T = 0.0f;
                             if (k < n) {
                                 const int kx = k % ps, ky = k / ps;
-                                T = win[(ky + 1) * ws + kx + 1] - mean0;
+                                const float T = win[(ky + 1) * ws + kx + 1] - mean0;
+                                float a, b, c, d;
                                 if (inside) {
                                     const float* p = J.S1 + (long long)(yi + ky) * pitch + (xi + kx);
                                     a = __ldg(p);
@@ -152,39 +157,23 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
                                     c = __ldg(r1 + x0);
                                     d = __ldg(r1 + x1);
                                 }
-                                t0[m] = (a - T) - mref;
-                            } else {
-                                t0[m] = 0.0f;
-                            }
-                            t1[m] = b - a;
-                            t2[m] = c - a;
-                            t3[m] = (d - c) - (b - a);
-                        }
-                    }
-                    // two partial sums per quantity halve the dependency chains
-                    float A0a = 0.0f, A0b = 0.0f, Axa = 0.0f, Axb = 0.0f, Aya = 0.0f, Ayb = 0.0f;
+                                const float t[4] = {(a - T) - mref, b - a, c - a, (d - c) - (b - a)};
 #pragma unroll
-                    for (int m = 0; m < PPL; ++m) {
-                        if (gl + LPP * m < n) {
-                            const float wv = fmaf(ay, fmaf(ax, t3[m], t2[m]), fmaf(ax, t1[m], t0[m]));
-                            if (m & 1) {
-                                A0b += wv;
-                                Axb = fmaf(gx[m], wv, Axb);
-                                Ayb = fmaf(gy[m], wv, Ayb);
-                            } else {
-                                A0a += wv;
-                                Axa = fmaf(gx[m], wv, Axa);
-                                Aya = fmaf(gy[m], wv, Aya);
+                                for (int q = 0; q < 4; ++q) {
+                                    Q[q] += t[q];
+                                    Q[4 + q] = fmaf(gx[m], t[q], Q[4 + q]);
+                                    Q[8 + q] = fmaf(gy[m], t[q], Q[8 + q]);
+                                }
                             }
                         }
-                    }
-                    float A0 = A0a + A0b, Ax = Axa + Axb, Ay = Aya + Ayb;
 #pragma unroll
-                    for (int o = LPP / 2; o > 0; o >>= 1) {
-                        A0 += __shfl_xor_sync(gmask, A0, o);
-                        Ax += __shfl_xor_sync(gmask, Ax, o);
-                        Ay += __shfl_xor_sync(gmask, Ay, o);
+                        for (int o = LPP / 2; o > 0; o >>= 1)
+#pragma unroll
+                            for (int q = 0; q < 12; ++q) Q[q] += __shfl_xor_sync(gmask, Q[q], o);
                     }
+                    const float A0 = fmaf(ay, fmaf(ax, Q[3], Q[2]), fmaf(ax, Q[1], Q[0]));
+                    const float Ax = fmaf(ay, fmaf(ax, Q[7], Q[6]), fmaf(ax, Q[5], Q[4]));
+                    const float Ay = fmaf(ay, fmaf(ax, Q[11], Q[10]), fmaf(ax, Q[9], Q[8]));
                     const float e = (A0 + sT) * inv_n;  // mean of the window minus mref
                     const float b0 = fmaf(-e, sgx, Ax), b1 = fmaf(-e, sgy, Ay);
                     mcur = mref + e;
@@ -229,9 +218,9 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     return cudaGetLastError();
 }
 
-// Lanes per patch by patch size: 8 up to 8x8 (<= 8 pixels per lane), 16 up to 12x12 (<= 9),
-// 32 up to 16x16 (<= 8); the 8x8 and 12x12 patches of the presets get compile-time sizes and
-// alternative group widths `lanes` (0 = the default) for the autotuner.
+// Lanes per patch: 8 by default up to 8x8 patches, 16 up to 16x16 (at most 16 pixels per lane);
+// the 8x8 and 12x12 patches of the presets get compile-time sizes and alternative group widths
+// `lanes` (0 = the default) for the autotuner.
 cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
                           const LaunchCfg& lc, cudaStream_t s, int lanes)
 {
@@ -241,7 +230,6 @@ cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int
         switch (lanes) {
             case 4: return launch_lp<4, 16, 8>(js, total, ps, stride, iters, lc, s);
             case 16: return launch_lp<16, 4, 8>(js, total, ps, stride, iters, lc, s);
-            case 32: return launch_lp<32, 2, 8>(js, total, ps, stride, iters, lc, s);
             default: return launch_lp<8, 8, 8>(js, total, ps, stride, iters, lc, s);
         }
     }
@@ -256,31 +244,19 @@ cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int
         switch ((n + 7) / 8) {
             case 1: return launch_lp<8, 1, 0>(js, total, ps, stride, iters, lc, s);
             case 2: return launch_lp<8, 2, 0>(js, total, ps, stride, iters, lc, s);
-            case 3: return launch_lp<8, 3, 0>(js, total, ps, stride, iters, lc, s);
             case 4: return launch_lp<8, 4, 0>(js, total, ps, stride, iters, lc, s);
             case 5: return launch_lp<8, 5, 0>(js, total, ps, stride, iters, lc, s);
             default: return launch_lp<8, 7, 0>(js, total, ps, stride, iters, lc, s);
         }
     }
-    if (ps < 12) {
-        switch ((n + 15) / 16) {
-            case 6: return launch_lp<16, 6, 0>(js, total, ps, stride, iters, lc, s);
-            case 7: return launch_lp<16, 7, 0>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<16, 8, 0>(js, total, ps, stride, iters, lc, s);
-        }
-    }
-    switch ((n + 31) / 32) {
-        case 6: return launch_lp<32, 6, 0>(js, total, ps, stride, iters, lc, s);
-        case 7: return launch_lp<32, 7, 0>(js, total, ps, stride, iters, lc, s);
-        default: return launch_lp<32, 8, 0>(js, total, ps, stride, iters, lc, s);
-    }
+    return launch_lp<16, 16, 0>(js, total, ps, stride, iters, lc, s);
 }
 
 int search_lane_options(int ps, int* out)
 {
     if (ps == 8) {
-        out[0] = 8, out[1] = 4, out[2] = 16, out[3] = 32;
-        return 4;
+        out[0] = 8, out[1] = 4, out[2] = 16;
+        return 3;
     }
     if (ps == 12) {
         out[0] = 16, out[1] = 8, out[2] = 32;
