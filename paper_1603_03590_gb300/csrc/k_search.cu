@@ -34,9 +34,10 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask)
     return v;
 }
 
-// PSC: compile-time patch size (0: the runtime `ps_rt`).
-template <int LPP, int PPL, int PSC>
-__global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
+// PSC: compile-time patch size (0: the runtime `ps_rt`).  MINB: resident blocks per SM the
+// register allocation must allow (chosen per variant so that nothing spills).
+template <int LPP, int PPL, int PSC, int MINB>
+__global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
                                                      int ps_rt, int stride, int iters)
 {
     extern __shared__ float smem[];
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(128) search_kernel(const __grid_constant__ Job
     }
 }
 
-template <int LPP, int PPL, int PSC>
+template <int LPP, int PPL, int PSC, int MINB = 1>
 static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
                              const LaunchCfg& lc, cudaStream_t s)
 {
@@ -206,7 +207,7 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     const size_t smem = (size_t)per_block * (ps + 2) * (ps + 2) * sizeof(float);
     static int occ = 0;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC>, threads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC, MINB>, threads, smem) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
@@ -214,7 +215,7 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     long long blocks = (total + per_block - 1) / per_block;
     const long long cap = (long long)lc.sm_count * occ;
     if (blocks > cap) blocks = cap;
-    search_kernel<LPP, PPL, PSC><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
+    search_kernel<LPP, PPL, PSC, MINB><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
     return cudaGetLastError();
 }
 
@@ -228,16 +229,16 @@ cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int
     const int n = ps * ps;
     if (ps == 8) {
         switch (lanes) {
-            case 4: return launch_lp<4, 16, 8>(js, total, ps, stride, iters, lc, s);
+            case 4: return launch_lp<4, 16, 8, 5>(js, total, ps, stride, iters, lc, s);
             case 16: return launch_lp<16, 4, 8>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<8, 8, 8>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<8, 8, 8, 6>(js, total, ps, stride, iters, lc, s);
         }
     }
     if (ps == 12) {
         switch (lanes) {
             case 8: return launch_lp<8, 18, 12>(js, total, ps, stride, iters, lc, s);
             case 32: return launch_lp<32, 5, 12>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<16, 9, 12>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<16, 9, 12, 5>(js, total, ps, stride, iters, lc, s);
         }
     }
     if (ps < 8) {
