@@ -39,13 +39,14 @@ def preset_params(dis, name):
     return dis.dis_default_params(name, coarsest_scale=4)
 
 
-def launches_per_call(dis, p, width, height):
-    """Kernels one call launches (mirrors the host plan: prep, pyramid, per level search +
-    densify (+ refinement: 3 setup, outer x (weights + 2 x inner), apply), final up-scaling)."""
+def launches_per_call(dis, p, width, height, lanes):
+    """Kernels one call launches (mirrors the host plan: prep, pyramid, per level search planes
+    (lane-per-patch search variant only) + search + densify (+ refinement: 3 setup, outer x
+    (weights + 2 x inner), apply), final up-scaling)."""
     ss, sf, _ = dis.dis_levels(width, height, p)
     n = 1 + ss
     for s in range(ss, sf - 1, -1):
-        n += 2
+        n += 2 + (1 if lanes == 1 else 0)
         if p.refine:
             outer = s + 1 if p.var_outer < 0 else p.var_outer
             n += 3 + outer * (1 + 2 * p.var_inner) + 1
@@ -206,7 +207,7 @@ def main():
         for k in range(B):
             dis.dis_compute_flow(h, I0d[k], I1d[k], W, H, W, p, flows[k], stream)
 
-    def timed(fn, steps, warmup, sample_clocks=False):
+    def timed(fn, steps, warmup, sample_clocks=False, probe=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
@@ -221,13 +222,21 @@ def main():
             fn()
             e1.record(stream)
             evs.append((e0, e1))
+            if probe is not None:
+                probe.append(dis.dis_probe_ms(h))  # waits for the probed launch of this step only
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - t0
         ms = sum(a.elapsed_time(b) for a, b in evs)
         return ms, wall, (clk.stop() if clk else None)
 
-    ms_b, wall_b, clocks = timed(step_batched, args.steps, args.warmup, sample_clocks=True)
+    # the dominant kernel (the inverse search of the finest level, over the whole batch) is timed
+    # inside every timed step by events the library records around that launch in its graph
+    ss, sf, _ = dis.dis_levels(W, H, p)
+    dis.dis_set_probe(h, "search", sf)
+    probe = []
+    ms_b, wall_b, clocks = timed(step_batched, args.steps, args.warmup, sample_clocks=True, probe=probe)
+    dis.dis_set_probe(h, -1)
     plain_steps = max(3, args.steps // 4)
     ms_p, _, _ = timed(step_plain, plain_steps, 3)
 
@@ -249,43 +258,12 @@ def main():
     h2d = B * 2 * W * H * 4
     d2h = B * W * H * 2 * 4
 
-    # dominant kernel, timed alone on its launch stream: the inverse search of level 0, with the
-    # inputs the pipeline gives it (level-0 images, the refined level-1 flow as initialisation)
+    k_ms = statistics.mean(probe)
     flops, (lw, lh), npatch = search_flops(dis, p, W, H)
-    ps = p.patch_size
-    stride = p.stride_override or max(1, ps - int(np.floor(p.overlap * ps + 1e-4)))
-    S0 = (I0d[0] * p.intensity_scale).contiguous()
-    S1 = (I1d[0] * p.intensity_scale).contiguous()
-    ss, _, _ = dis.dis_levels(W, H, p)
-    dims = [(W, H)]
-    for _ in range(ss):
-        dims.append(((dims[-1][0] + 1) // 2, (dims[-1][1] + 1) // 2))
-    ck = torch.empty(sum(a * b for a, b in dims) * 2, device=dev)
-    tmp = torch.empty((H, W, 2), device=dev)
-    dis.dis_compute_flow_ex(h, I0d[0], I1d[0], W, H, W, p, None, None, None, ck, tmp, stream)
-    w1, h1 = dims[1]
-    off1 = sum(a * b for a, b in dims[2:]) * 2
-    U1 = ck[off1:off1 + w1 * h1 * 2].clone()
-    T0 = torch.empty((h1, w1), device=dev)
-    T1 = torch.empty((h1, w1), device=dev)
-    dis.dis_pyr_down(S0, W, H, W, T0, w1, stream)
-    dis.dis_pyr_down(S1, W, H, W, T1, w1, stream)
-    if p.refine:
-        outer1 = 2 if p.var_outer < 0 else p.var_outer
-        dis.dis_refine_level(h, T0, T1, w1, h1, w1, 1, U1, outer1, p.var_inner, p.delta, p.gamma, p.alpha,
-                             p.sor_omega, stream)
-    u = torch.empty((npatch, 2), device=dev)
-    for _ in range(3):
-        dis.dis_search_level(S0, S1, lw, lh, lw, U1, w1, h1, 2.0, ps, stride, p.grad_iters, u, stream=stream)
-    torch.cuda.synchronize()
-    reps = 20
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        dis.dis_search_level(S0, S1, lw, lh, lw, U1, w1, h1, 2.0, ps, stride, p.grad_iters, u, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    k_ms = e0.elapsed_time(e1) / reps
+    # one traced call: device time per launch group (stage shares of the batched step)
+    stages = {}
+    for kind, lev, ms in dis.dis_trace_batched(h, arr, B, p, stream):
+        stages[kind] = stages.get(kind, 0.0) + ms
 
     # max over ranks
     t = torch.tensor([ms_b, ms_p, ms_e], device=dev, dtype=torch.float64)
@@ -308,7 +286,7 @@ def main():
     plain = world * B * plain_steps / (ms_p / 1000.0)
     e2e = world * B * e2e_steps / (ms_e / 1000.0)
     abytes = algorithmic_bytes(dis, p, W, H)
-    achieved = flops / (k_ms / 1000.0) / 1e12
+    achieved = flops * B / (k_ms / 1000.0) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -316,19 +294,21 @@ def main():
         "config": {"workload": "layered 1024x436, %s preset, 5 levels, batch %d per GPU" % (args.preset, B),
                    "batch_per_gpu": B, "preset": args.preset, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-                   "autotuned": {"search_lanes_per_patch": lanes}},
+                   "autotuned": {"search_variant": lanes}},
         "plain": {"value": plain, "unit": UNIT, "ms_per_pair": ms_p / (B * plain_steps)},
         "hbm_roofline": {"algorithmic_bytes_per_pair": abytes,
                          "achieved_gbs": abytes * value / world / 1e9, "peak_gbs": hbm,
                          "frac": abytes * value / world / 1e9 / hbm},
-        "roofline": {"kernel": "search_kernel (level 0, %d patches x %d iterations, initialised from the "
-                               "refined level-1 flow as in the pipeline)" % (npatch, p.grad_iters),
-                     "ms_per_launch": k_ms,
+        "roofline": {"kernel": "inverse search of level %d over the batch (%d pairs x %d patches x %d iterations, "
+                               "search variant %d), timed inside the timed steps" % (sf, B, npatch, p.grad_iters, lanes),
+                     "ms_per_launch": k_ms, "launches_timed": len(probe),
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
+                     "algorithmic_flops_per_launch": flops * B,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max},
+        "stages_ms_per_step": {k: round(v, 4) for k, v in stages.items()},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_call(dis, p, W, H) * args.steps,
+        "gpu_launches": launches_per_call(dis, p, W, H, lanes) * args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -143,13 +143,61 @@ dis_status dis_compute_flow_ex(dis_handle* h, const float* I0, const float* I1, 
  * repeat. */
 dis_status dis_compute_flow_batched(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream);
 
-/* Autotuner (not in the paper): time the variants the library offers for this workload - the
- * number of lanes that share one patch in the inverse-search kernel - on the caller's pairs
- * (the batched call, 4 runs per variant, synchronising `stream`) and keep the fastest in the
- * handle for later calls with the same patch size.  The runs write the pairs' flow_out.
- * *chosen_lanes (nullable) receives the choice. */
+/* Tracing (not in the paper): runs the batched call once without a CUDA graph, with events on
+ * `stream` on both sides of every launch group of the plan, synchronises `stream` and writes one
+ * record per group (up to `cap`; *count receives the total): the kind below, the pyramid level
+ * (0 = finest) and the group's device time in milliseconds.  A group is one kernel launch,
+ * except DIS_LAUNCH_REFINE, which covers all launches of one level's refinement.  Writes the
+ * pairs' flow_out like dis_compute_flow_batched. */
+enum {
+    DIS_LAUNCH_PREP = 0,          /* level-0 scaling / channel mean */
+    DIS_LAUNCH_PYRAMID = 1,       /* one pyramid step */
+    DIS_LAUNCH_SEARCH_PLANES = 2, /* per-pixel search data of one level */
+    DIS_LAUNCH_SEARCH = 3,        /* inverse search of one level */
+    DIS_LAUNCH_DENSIFY = 4,       /* densification of one level */
+    DIS_LAUNCH_REFINE = 5,        /* variational refinement of one level */
+    DIS_LAUNCH_UPSAMPLE = 6       /* final up-scaling */
+};
+typedef struct dis_launch_record {
+    int kind;
+    int level;
+    float ms;
+} dis_launch_record;
+dis_status dis_trace_batched(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream,
+                             dis_launch_record* out, int cap, int* count);
+
+/* Probe (not in the paper): from now on every call of handle h records two events of its own
+ * around the launch group (kind, level) - inside the CUDA graph when the call replays one - so
+ * that the group's device time in a normal call can be read with dis_probe_ms.  kind < 0
+ * removes the probe.  Calls with and without a probe use different cached graphs. */
+dis_status dis_set_probe(dis_handle* h, int kind, int level);
+
+/* Device time in ms of the probed launch group in the most recent call that ran it (waits for
+ * that group to finish).  DIS_ERR_INVALID_ARG when no such call has been issued. */
+dis_status dis_probe_ms(dis_handle* h, float* ms);
+
+/* Autotuner (not in the paper): time the inverse-search variants the library offers for this
+ * workload on the caller's pairs (the batched call, 4 runs per variant, synchronising
+ * `stream`) and keep the fastest in the handle for later calls with the same patch size.  The
+ * runs write the pairs' flow_out.  *chosen_lanes (nullable) receives the chosen variant code:
+ *   4, 8, 16, 32   grouped: that many lanes share one patch (every group runs its own updates
+ *                  and rebuilds its cell sums alone);
+ *   1              lane per patch: one lane runs a patch's updates, the warp rebuilds the cell
+ *                  sums of each patch that needs it together (reads two per-pixel planes);
+ *   100 + G        warp-cooperative: G patches per warp, 32/G lanes per patch for the updates,
+ *                  the whole warp for every rebuild (templates in shared memory).
+ * All variants compute the same method; they differ in rounding order only. */
 dis_status dis_autotune(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream,
                         int* chosen_lanes);
+
+/* Search variants offered for patch size ps (codes as for dis_autotune, the default first):
+ * writes up to `cap` of them to out (nullable when cap is 0) and returns their count, or 0 for
+ * a patch size outside [2, 16]. */
+int dis_search_variants(int patch_size, int* out, int cap);
+
+/* Pins the search variant of handle h for patch size ps to `lanes` (one of
+ * dis_search_variants(ps)), as dis_autotune would; DIS_ERR_INVALID_ARG otherwise. */
+dis_status dis_set_search_variant(dis_handle* h, int patch_size, int lanes);
 
 /* ---- per-stage entry points (one pyramid level; used for per-stage parity tests and by
  * callers that drive the level loop themselves).  No allocation; caller-owned buffers. */
@@ -174,6 +222,13 @@ dis_status dis_sobel(const float* in, int w, int h, int64_t pitch, float* gx, fl
 dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
                             int hc, float cscale, int ps, int stride, int iters, float* u_out, float* uinit_out,
                             int* status_out, void* stream);
+
+/* dis_search_level with an explicit search variant (0 = the default, else one of
+ * dis_search_variants(ps)); the lane-per-patch variant reads the images here, not the
+ * per-pixel planes of the handle path, with the same result bit for bit. */
+dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
+                               int hc, float cscale, int ps, int stride, int iters, int variant, float* u_out,
+                               float* uinit_out, int* status_out, void* stream);
 
 /* Step 4 of Alg. 1 (Eq. 3): U(x) = sum_i w_i(x) u_i / sum_i w_i(x) over the patches covering
  * x, w_i(x) = 1 / max(1, |I1(x + u_i) - I0(x)|).  u: nx*ny*2 patch flows; U_out: w*h*2.

@@ -202,6 +202,8 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     const int32_t* pw = reinterpret_cast<const int32_t*>(&p);
     for (size_t i = 0; i < sizeof(dis_params) / 4; ++i) plan.key.push_back(pw[i]);
     plan.key.push_back(hd->search_lanes[p.patch_size]);
+    plan.key.push_back(hd->probe_kind);
+    plan.key.push_back(hd->probe_level);
 
     auto slot = [&](int i) { return hd->arena + (size_t)i * hd->slot_bytes; };
     auto img = [&](int i, int s) { return reinterpret_cast<float*>(slot(i) + hd->off_img[s]); };
@@ -310,6 +312,10 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.frozen = pairs[i].frozen ? reinterpret_cast<const float2*>(pairs[i].frozen) + before : nullptr;
             J.record = pairs[i].record ? reinterpret_cast<float2*>(pairs[i].record) + before : nullptr;
             J.rs = reinterpret_cast<float*>(slot(i) + hd->off_rs);
+            // the search planes live in the refinement scratch, which the level's refinement
+            // overwrites only after its search (8 of its 15 C + 8 planes)
+            J.tpl = reinterpret_cast<const float4*>(J.rs);
+            J.tap = J.tpl + J.plane;
             J.patch_base = pb;
             J.pix_base = xb;
             J.half_base = hb;
@@ -349,24 +355,65 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     return DIS_OK;
 }
 
-cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaStream_t s)
+// One traced launcher call: events on both sides of it on the launching stream.
+struct TraceRec {
+    int kind, level;
+    cudaEvent_t a, b;
+};
+
+cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaStream_t s,
+                        std::vector<TraceRec>* tr = nullptr)
 {
     const int ps = p.patch_size, stride = stride_of(p);
     cudaError_t e = cudaSuccess;
+    // runs one launcher call, bracketed by events when tracing
+    auto traced = [&](int kind, int level, auto&& launch) -> cudaError_t {
+        if (!tr && kind == hd->probe_kind && level == hd->probe_level) {
+            // external event nodes when captured into a graph, plain records otherwise
+            cudaError_t ce = cudaEventRecordWithFlags(hd->probe_a, s, cudaEventRecordExternal);
+            if (ce == cudaSuccess) ce = launch();
+            if (ce == cudaSuccess) ce = cudaEventRecordWithFlags(hd->probe_b, s, cudaEventRecordExternal);
+            if (ce == cudaSuccess) hd->probe_armed = true;
+            return ce;
+        }
+        if (!tr) return launch();
+        TraceRec r{kind, level, nullptr, nullptr};
+        cudaError_t ce = cudaEventCreate(&r.a);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&r.b);
+        if (ce == cudaSuccess) ce = cudaEventRecord(r.a, s);
+        if (ce == cudaSuccess) ce = launch();
+        if (ce == cudaSuccess) ce = cudaEventRecord(r.b, s);
+        tr->push_back(r);
+        return ce;
+    };
     for (const Phase& ph : plan.phases) {
         const char* tab = hd->jobs_dev + ph.off;
         switch (ph.kind) {
             case Phase::PREP:
-                e = dis::launch_prep(dis::device_jobs(reinterpret_cast<const PrepJob*>(tab), ph.n), ph.total, hd->lc, s);
+                e = traced(DIS_LAUNCH_PREP, 0, [&] {
+                    return dis::launch_prep(dis::device_jobs(reinterpret_cast<const PrepJob*>(tab), ph.n), ph.total,
+                                            hd->lc, s);
+                });
                 break;
             case Phase::PYR:
-                e = dis::launch_pyr_down(dis::device_jobs(reinterpret_cast<const PyrJob*>(tab), ph.n), ph.total, hd->lc,
-                                         s);
+                e = traced(DIS_LAUNCH_PYRAMID, ph.s, [&] {
+                    return dis::launch_pyr_down(dis::device_jobs(reinterpret_cast<const PyrJob*>(tab), ph.n), ph.total,
+                                                hd->lc, s);
+                });
                 break;
             case Phase::LEVEL: {
                 auto js = dis::device_jobs(reinterpret_cast<const LevelJob*>(tab), ph.n);
-                e = dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s, hd->search_lanes[ps]);
-                if (e == cudaSuccess) e = dis::launch_densify(js, ph.total2, ps, stride, hd->lc, s);
+                const int lanes = hd->search_lanes[ps];
+                if (lanes == 1)
+                    e = traced(DIS_LAUNCH_SEARCH_PLANES, ph.s,
+                               [&] { return dis::launch_search_planes(js, ph.total2, hd->lc, s); });
+                if (e == cudaSuccess)
+                    e = traced(DIS_LAUNCH_SEARCH, ph.s, [&] {
+                        return dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s, lanes, lanes == 1);
+                    });
+                if (e == cudaSuccess)
+                    e = traced(DIS_LAUNCH_DENSIFY, ph.s,
+                               [&] { return dis::launch_densify(js, ph.total2, ps, stride, hd->lc, s); });
                 for (const auto& c : plan.copies)
                     if (e == cudaSuccess && c.s == ph.s) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s);
                 if (e == cudaSuccess && p.refine) {
@@ -377,12 +424,16 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                     a.gamma = p.gamma;
                     a.alpha = p.alpha;
                     a.omega = p.sor_omega;
-                    e = dis::launch_refine(js, ph.total2, ph.total3, a, hd->lc, s);
+                    e = traced(DIS_LAUNCH_REFINE, ph.s,
+                               [&] { return dis::launch_refine(js, ph.total2, ph.total3, a, hd->lc, s); });
                 }
                 break;
             }
             case Phase::UP:
-                e = dis::launch_upsample(dis::device_jobs(reinterpret_cast<const UpJob*>(tab), ph.n), ph.total, hd->lc, s);
+                e = traced(DIS_LAUNCH_UPSAMPLE, ph.s, [&] {
+                    return dis::launch_upsample(dis::device_jobs(reinterpret_cast<const UpJob*>(tab), ph.n), ph.total,
+                                                hd->lc, s);
+                });
                 break;
         }
         if (e != cudaSuccess) return e;
@@ -390,11 +441,11 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
     return cudaSuccess;
 }
 
-dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaStream_t s)
+// Stream-ordered upload of the job tables when they changed (from a pinned buffer whose
+// previous copy has completed).
+dis_status upload_jobs(dis_handle* hd, const Plan& plan, cudaStream_t s)
 {
     cudaError_t e;
-    // upload the job tables when they changed (stream-ordered, from a pinned buffer whose
-    // previous copy has completed)
     if (!hd->jobs_valid || hd->jobs_last != plan.blob) {
         if ((e = cudaEventSynchronize(hd->jobs_ev)) != cudaSuccess) return cuda_fail(hd, e, "job upload wait");
         std::memcpy(hd->jobs_pinned, plan.blob.data(), plan.blob.size());
@@ -405,6 +456,14 @@ dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaS
         hd->jobs_last = plan.blob;
         hd->jobs_valid = true;
     }
+    return DIS_OK;
+}
+
+dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaStream_t s)
+{
+    cudaError_t e;
+    dis_status ust = upload_jobs(hd, plan, s);
+    if (ust != DIS_OK) return ust;
     if (!hd->use_graphs || !plan.graphable) {
         if ((e = record_plan(hd, plan, p, s)) != cudaSuccess) return cuda_fail(hd, e, "kernel launch");
         return DIS_OK;
@@ -567,6 +626,8 @@ void dis_destroy(dis_handle* h)
     if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
     if (h->jobs_ev) cudaEventSynchronize(h->jobs_ev);
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    if (h->probe_a) cudaEventDestroy(h->probe_a);
+    if (h->probe_b) cudaEventDestroy(h->probe_b);
     if (h->arena) cudaFree(h->arena);
     if (h->jobs_pinned) cudaFreeHost(h->jobs_pinned);
     if (h->jobs_ev) cudaEventDestroy(h->jobs_ev);
@@ -621,6 +682,71 @@ dis_status dis_compute_flow_batched(dis_handle* hd, const dis_pair* pairs, int n
     return run_plan(hd, plan, *p, (cudaStream_t)stream);
 }
 
+dis_status dis_trace_batched(dis_handle* hd, const dis_pair* pairs, int n, const dis_params* p, void* stream,
+                             dis_launch_record* out, int cap, int* count)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    if (count) *count = 0;
+    std::string e;
+    dis_status st = validate(p, e);
+    if (st != DIS_OK) return fail(hd, st, e);
+    if (p->channels != hd->C) return fail(hd, DIS_ERR_INVALID_ARG, "params.channels differs from the handle's");
+    if (!pairs || n < 1 || n > hd->max_batch) return fail(hd, DIS_ERR_INVALID_ARG, "pairs NULL or n outside [1, max_batch]");
+    if (cap < 0 || (cap > 0 && !out)) return fail(hd, DIS_ERR_INVALID_ARG, "out NULL with cap > 0");
+    std::vector<PairIn> v;
+    for (int i = 0; i < n; ++i) {
+        PairIn q{pairs[i].I0, pairs[i].I1, pairs[i].width, pairs[i].height, (long long)pairs[i].pitch,
+                 pairs[i].flow_out, nullptr, nullptr, nullptr, nullptr};
+        if ((st = check_pair(hd, q, i)) != DIS_OK) return st;
+        v.push_back(q);
+    }
+    Plan plan;
+    if ((st = build_plan(hd, v, *p, plan)) != DIS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = upload_jobs(hd, plan, s)) != DIS_OK) return st;
+    std::vector<TraceRec> tr;
+    cudaError_t ce = record_plan(hd, plan, *p, s, &tr);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    int k = 0;
+    for (const TraceRec& r : tr) {
+        float ms = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (k < cap) out[k] = dis_launch_record{r.kind, r.level, ms};
+        ++k;
+        if (r.a) cudaEventDestroy(r.a);
+        if (r.b) cudaEventDestroy(r.b);
+    }
+    if (ce != cudaSuccess) return cuda_fail(hd, ce, "dis_trace_batched");
+    if (count) *count = k;
+    return DIS_OK;
+}
+
+dis_status dis_set_probe(dis_handle* hd, int kind, int level)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    if (kind > DIS_LAUNCH_UPSAMPLE || level < 0) return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_probe: bad kind or level");
+    if (kind >= 0 && !hd->probe_a) {
+        cudaError_t e = cudaEventCreate(&hd->probe_a);
+        if (e == cudaSuccess) e = cudaEventCreate(&hd->probe_b);
+        if (e != cudaSuccess) return cuda_fail(hd, e, "dis_set_probe");
+    }
+    hd->probe_kind = kind < 0 ? -1 : kind;
+    hd->probe_level = level;
+    hd->probe_armed = false;
+    return DIS_OK;
+}
+
+dis_status dis_probe_ms(dis_handle* hd, float* ms)
+{
+    if (!hd || !ms) return fail(hd, DIS_ERR_INVALID_ARG, "handle or ms is NULL");
+    if (hd->probe_kind < 0 || !hd->probe_armed)
+        return fail(hd, DIS_ERR_INVALID_ARG, "dis_probe_ms: no call has run the probed launch group");
+    cudaError_t e = cudaEventSynchronize(hd->probe_b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, hd->probe_a, hd->probe_b);
+    if (e != cudaSuccess) return cuda_fail(hd, e, "dis_probe_ms");
+    return DIS_OK;
+}
+
 // ---- per-stage entry points -------------------------------------------------------------
 static dis::LaunchCfg stage_lc()
 {
@@ -668,12 +794,19 @@ static bool level_args_ok(int w, int h, int64_t pitch, int ps, int stride, const
     return true;
 }
 
-dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
-                            int hc, float cscale, int ps, int stride, int iters, float* u_out, float* uinit_out,
-                            int* status_out, void* stream)
+dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
+                               int hc, float cscale, int ps, int stride, int iters, int variant, float* u_out,
+                               float* uinit_out, int* status_out, void* stream)
 {
     if (!I0 || !I1 || !u_out || iters < 0 || !level_args_ok(w, h, pitch, ps, stride, Uc, wc, hc, cscale))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: bad pointer, size, pitch or grid");
+    if (variant != 0) {
+        int opts[8];
+        const int n = dis_search_variants(ps, opts, 8);
+        bool ok = false;
+        for (int k = 0; k < n; ++k) ok = ok || opts[k] == variant;
+        if (!ok) return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: not a search variant of this patch size");
+    }
     LevelJob J;
     std::memset(&J, 0, sizeof(J));
     J.S0 = I0;
@@ -692,8 +825,16 @@ dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int6
     J.ny = grid_n(h, ps, stride);
     J.C = 1;
     cudaError_t e = dis::launch_search(dis::single_job(J), (long long)J.nx * J.ny, ps, stride, iters, stage_lc(),
-                                       (cudaStream_t)stream);
+                                       (cudaStream_t)stream, variant, false);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_search_level");
+}
+
+dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
+                            int hc, float cscale, int ps, int stride, int iters, float* u_out, float* uinit_out,
+                            int* status_out, void* stream)
+{
+    return dis_search_level_ex(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, 0, u_out, uinit_out,
+                               status_out, stream);
 }
 
 dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* u, int ps,
@@ -820,6 +961,28 @@ extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n,
     cudaEventDestroy(e1);
     if (chosen_lanes) *chosen_lanes = hd->search_lanes[ps];
     return st;
+}
+
+extern "C" int dis_search_variants(int patch_size, int* out, int cap)
+{
+    if (patch_size < 2 || patch_size > kMaxPatch) return 0;
+    int opts[8];
+    const int n = dis::search_lane_options(patch_size, opts);
+    for (int k = 0; out && k < n && k < cap; ++k) out[k] = opts[k];
+    return n;
+}
+
+extern "C" dis_status dis_set_search_variant(dis_handle* hd, int patch_size, int lanes)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    int opts[8];
+    const int n = dis_search_variants(patch_size, opts, 8);
+    for (int k = 0; k < n; ++k)
+        if (opts[k] == lanes) {
+            hd->search_lanes[patch_size] = lanes;
+            return DIS_OK;
+        }
+    return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_search_variant: not a variant of this patch size");
 }
 
 // ---- host helpers shared with the backward pass (dis_backward.cu) ------------------------

@@ -28,6 +28,8 @@ struct LevelJob {
     const float2* frozen; // replayed increments (nullable)
     float2* record;       // recorded increments (nullable)
     float* rs;            // refinement scratch: (15 C + 8) planes of `plane` floats
+    const float4* tpl;    // search planes (nullable; may alias rs, written before the search):
+    const float4* tap;    //   (I0, gx, gy, 0) and the four bilinear taps of I1 per pixel
     long long plane;      // pitch * h
     long long patch_base; // first flattened patch of this job
     long long pix_base;   // first flattened pixel
@@ -119,10 +121,19 @@ cudaError_t launch_prep(const Jobs<PrepJob>& js, long long total, const LaunchCf
 cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_sobel(const float* in, int w, int h, int pitch, float* gx, float* gy, int out_pitch,
                          const LaunchCfg& lc, cudaStream_t s);
-// lanes: lanes per patch (0 = default for the patch size; see search_lane_options).
+// lanes: lanes per patch (0 or 1 = the lane-per-patch form; see search_lane_options).  planes:
+// the jobs carry tpl / tap (written by launch_search_planes); used by the lane-per-patch form.
+cudaError_t launch_search_lane(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
+                               const LaunchCfg& lc, cudaStream_t s, bool planes);
 cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
-                          const LaunchCfg& lc, cudaStream_t s, int lanes = 0);
-// Group widths the search kernel offers for patch size ps (first = default); returns the count.
+                          const LaunchCfg& lc, cudaStream_t s, int lanes = 0, bool planes = false);
+// Warp-cooperative form with g patches per warp (k_search_coop.cu), for patch sizes 8 and 12.
+bool search_coop_supported(int ps, int g);
+cudaError_t launch_search_coop(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int g,
+                               const LaunchCfg& lc, cudaStream_t s);
+// Writes the search planes tpl / tap of every job (thread per pixel, flattened by pix_base).
+cudaError_t launch_search_planes(const Jobs<LevelJob>& js, long long total_pix, const LaunchCfg& lc, cudaStream_t s);
+// Lanes-per-patch variants the search offers for patch size ps (first = default); returns the count.
 int search_lane_options(int ps, int* out);
 cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, int stride, const LaunchCfg& lc,
                            cudaStream_t s);

@@ -219,13 +219,18 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     return cudaGetLastError();
 }
 
-// Lanes per patch: 8 by default up to 8x8 patches, 16 up to 16x16 (at most 16 pixels per lane);
-// the 8x8 and 12x12 patches of the presets get compile-time sizes and alternative group widths
-// `lanes` (0 = the default) for the autotuner.
+// Search variants: 0 = the default grouped form (8 lanes per patch up to 8x8 patches, 16
+// above); 4, 8, 16, 32 = this grouped form with that many lanes per patch (compile-time 8x8
+// and 12x12 sizes); 1 = the lane-per-patch form (k_search_lane.cu; `planes`: the jobs carry
+// the search planes); 100 + G = the warp-cooperative form with G patches per warp
+// (k_search_coop.cu).  Unsupported values fall back to the default.
 cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
-                          const LaunchCfg& lc, cudaStream_t s, int lanes)
+                          const LaunchCfg& lc, cudaStream_t s, int lanes, bool planes)
 {
     if (total <= 0) return cudaSuccess;
+    if (lanes > 100 && search_coop_supported(ps, lanes - 100))
+        return launch_search_coop(js, total, ps, stride, iters, lanes - 100, lc, s);
+    if (lanes == 1) return launch_search_lane(js, total, ps, stride, iters, lc, s, planes);
     const int n = ps * ps;
     if (ps == 8) {
         switch (lanes) {
@@ -256,15 +261,18 @@ cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int
 int search_lane_options(int ps, int* out)
 {
     if (ps == 8) {
-        out[0] = 8, out[1] = 4, out[2] = 16;
-        return 3;
+        const int v[6] = {8, 4, 1, 102, 104, 108};
+        for (int k = 0; k < 6; ++k) out[k] = v[k];
+        return 6;
     }
     if (ps == 12) {
-        out[0] = 16, out[1] = 8, out[2] = 32;
-        return 3;
+        const int v[5] = {16, 8, 1, 102, 104};
+        for (int k = 0; k < 5; ++k) out[k] = v[k];
+        return 5;
     }
-    out[0] = 0;
-    return 1;
+    out[0] = ps < 8 ? 8 : 16;
+    out[1] = 1;
+    return 2;
 }
 
 }  // namespace dis

@@ -73,9 +73,15 @@ _SIGS = {
     "dis_compute_flow_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dis_compute_flow_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp]),
     "dis_autotune": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, ctypes.POINTER(_i)]),
+    "dis_search_variants": (_i, [_i, ctypes.POINTER(_i), _i]),
+    "dis_set_probe": (_i, [_vp, _i, _i]),
+    "dis_probe_ms": (_i, [_vp, ctypes.POINTER(_f)]),
+    "dis_trace_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, _vp, _i, ctypes.POINTER(_i)]),
+    "dis_set_search_variant": (_i, [_vp, _i, _i]),
     "dis_pyr_down": (_i, [_vp, _i, _i, _i64, _vp, _i64, _vp]),
     "dis_sobel": (_i, [_vp, _i, _i, _i64, _vp, _vp, _i64, _vp]),
     "dis_search_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "dis_search_level_ex": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dis_densify_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _vp, _i, _i, _f, _vp, _vp]),
     "dis_refine_level": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
     "dis_upsample_flow": (_i, [_vp, _i, _i, _f, _vp, _i, _i, _vp]),
@@ -181,6 +187,48 @@ def dis_autotune(handle, pairs, n, params, stream=None):
     return lanes.value
 
 
+class dis_launch_record(ctypes.Structure):
+    _fields_ = [("kind", _i), ("level", _i), ("ms", _f)]
+
+
+LAUNCH_KINDS = ("prep", "pyramid", "search_planes", "search", "densify", "refine", "upsample")
+
+
+def dis_trace_batched(handle, pairs, n, params, stream=None, cap=256):
+    """Run the batched call once with events around every launch group; returns a list of
+    (kind name, level, milliseconds)."""
+    out = (dis_launch_record * cap)()
+    cnt = _i()
+    _check(_lib.dis_trace_batched(handle, pairs, n, ctypes.byref(params), _stream(stream), out, cap,
+                                  ctypes.byref(cnt)), handle)
+    return [(LAUNCH_KINDS[out[k].kind], out[k].level, out[k].ms) for k in range(min(cnt.value, cap))]
+
+
+def dis_set_probe(handle, kind, level=0):
+    """Record events around launch group (kind name or number, level) in every later call."""
+    k = LAUNCH_KINDS.index(kind) if isinstance(kind, str) else kind
+    _check(_lib.dis_set_probe(handle, k, level), handle)
+
+
+def dis_probe_ms(handle):
+    """Device time (ms) of the probed launch group in the most recent call."""
+    ms = _f()
+    _check(_lib.dis_probe_ms(handle, ctypes.byref(ms)), handle)
+    return ms.value
+
+
+def dis_search_variants(patch_size):
+    """Lanes-per-patch variants of the search for this patch size (the default first)."""
+    out = (_i * 8)()
+    n = _lib.dis_search_variants(patch_size, out, 8)
+    return [out[k] for k in range(n)]
+
+
+def dis_set_search_variant(handle, patch_size, lanes):
+    """Pin the search variant of the handle for this patch size."""
+    _check(_lib.dis_set_search_variant(handle, patch_size, lanes), handle)
+
+
 def dis_pyr_down(inp, w, h, in_pitch, out, out_pitch, stream=None):
     _check(_lib.dis_pyr_down(_ptr(inp), w, h, in_pitch, _ptr(out), out_pitch, _stream(stream)))
 
@@ -193,6 +241,12 @@ def dis_search_level(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters,
                      status_out=None, stream=None):
     _check(_lib.dis_search_level(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(Uc), wc, hc, cscale, ps, stride, iters,
                                  _ptr(u_out), _ptr(uinit_out), _ptr(status_out), _stream(stream)))
+
+
+def dis_search_level_ex(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, variant, u_out, uinit_out=None,
+                        status_out=None, stream=None):
+    _check(_lib.dis_search_level_ex(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(Uc), wc, hc, cscale, ps, stride, iters,
+                                    variant, _ptr(u_out), _ptr(uinit_out), _ptr(status_out), _stream(stream)))
 
 
 def dis_densify_level(I0, I1, w, h, pitch, u, ps, stride, Uc, wc, hc, cscale, U_out, stream=None):

@@ -109,3 +109,23 @@ def test_stride_reading_matches_oracle_for_decimal_overlaps(dis):
             q = oracle.params(patch_size=ps, overlap=ov, coarsest_scale=0, finest_scale=0)
             W = H = 64
             assert dis.dis_levels(W, H, p)[2] == oracle.total_patches(W, H, q), (ps, ov)
+
+
+def test_search_variants_are_listed_without_a_gpu(dis):
+    assert dis.dis_search_variants(8) == [8, 4, 1, 102, 104, 108]
+    assert dis.dis_search_variants(12) == [16, 8, 1, 102, 104]
+    for ps in range(2, 17):
+        v = dis.dis_search_variants(ps)
+        assert v[0] == (8 if ps <= 8 else 16) and 1 in v and len(set(v)) == len(v), ps
+    assert dis.dis_search_variants(1) == [] and dis.dis_search_variants(17) == []
+    lib = ctypes.CDLL(dis.LIB_PATH)
+    assert lib.dis_search_variants(12, None, 0) == 5
+    assert lib.dis_set_search_variant(None, 12, 1) == dis.DIS_ERR_INVALID_ARG
+
+
+def test_trace_and_probe_argument_checks_need_no_gpu(dis):
+    lib = ctypes.CDLL(dis.LIB_PATH)
+    assert lib.dis_set_probe(None, 3, 0) == dis.DIS_ERR_INVALID_ARG
+    assert lib.dis_probe_ms(None, None) == dis.DIS_ERR_INVALID_ARG
+    assert lib.dis_trace_batched(None, None, 1, None, None, None, 0, None) == dis.DIS_ERR_INVALID_ARG
+    assert dis.LAUNCH_KINDS.index("search") == 3 and len(dis.LAUNCH_KINDS) == 7

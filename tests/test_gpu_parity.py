@@ -95,23 +95,27 @@ def _flat_borderline(I0, ps, stride, idx):
     return (h00 * h11 - h01 * h01) / (0.5 * (h00 + h11)) ** 2
 
 
-def compare_search(I0, I1, Uc, cscale, ps, stride, iters, u_g, ui_g, st_g):
+def compare_search(I0, I1, Uc, cscale, ps, stride, iters, u_g, ui_g, st_g, ref=None):
     """Element-wise comparison of GPU and FP64 patch flows.
 
     A patch whose FP64 result moves by more than 1e-4 px when I1 is perturbed by 1e-5 (the
     size of FP32 rounding on the 0..255 scale) is not determined by its inputs at FP32
     resolution (a search that cycles instead of converging); such patches are counted,
     checked for validity and excluded.  Among the others a differing reset / flat decision
-    must be borderline in FP64."""
-    gx, gy = oracle.sobel(I0)
-    u_o, ui_o, st_o = oracle.search_level(I0, gx, gy, I1, ps, stride, iters, Uc=Uc, cscale=cscale)
-    u_o, ui_o, st_o = u_o.reshape(-1, 2), ui_o.reshape(-1, 2), st_o.reshape(-1)
+    must be borderline in FP64.  `ref`: the oracle results of an earlier call on the same
+    inputs (returned as the third value)."""
+    if ref is None:
+        gx, gy = oracle.sobel(I0)
+        u_o, ui_o, st_o = oracle.search_level(I0, gx, gy, I1, ps, stride, iters, Uc=Uc, cscale=cscale)
+        u_o, ui_o, st_o = u_o.reshape(-1, 2), ui_o.reshape(-1, 2), st_o.reshape(-1)
+        unstable = np.zeros(len(st_o), bool)
+        for seed in (1, 2):
+            I1p = I1 + 1e-5 * np.random.default_rng(seed).standard_normal(I1.shape)
+            u_p, _, st_p = oracle.search_level(I0, gx, gy, I1p, ps, stride, iters, Uc=Uc, cscale=cscale)
+            unstable |= (np.abs(u_p.reshape(-1, 2) - u_o).max(1) > 1e-4) | (st_p.reshape(-1) != st_o)
+        ref = (u_o, ui_o, st_o, unstable)
+    u_o, ui_o, st_o, unstable = ref
     assert np.abs(ui_g - ui_o).max() <= 1e-4
-    unstable = np.zeros(len(st_o), bool)
-    for seed in (1, 2):
-        I1p = I1 + 1e-5 * np.random.default_rng(seed).standard_normal(I1.shape)
-        u_p, _, st_p = oracle.search_level(I0, gx, gy, I1p, ps, stride, iters, Uc=Uc, cscale=cscale)
-        unstable |= (np.abs(u_p.reshape(-1, 2) - u_o).max(1) > 1e-4) | (st_p.reshape(-1) != st_o)
     assert unstable.mean() < 0.02, unstable.mean()
     assert np.isfinite(u_g).all()
     # a result of an unstable patch is still a valid outcome: within theta_ps of u_init
@@ -129,11 +133,12 @@ def compare_search(I0, I1, Uc, cscale, ps, stride, iters, u_g, ui_g, st_g):
             assert abs(dist - ps) < 1e-2, ("reset decision not borderline", k, dist)
     same = (st_g == st_o) & ~unstable
     err = np.abs(u_g - u_o)[same]
-    return err.max() if err.size else 0.0, "%d decisions differ, %d unstable" % (len(differ), unstable.sum()), u_o
+    return err.max() if err.size else 0.0, "%d decisions differ, %d unstable" % (len(differ), unstable.sum()), ref
 
 
 @pytest.mark.parametrize("case", ["translate", "layered-dense", "layered-fast", "ragged"])
 def test_search_stage(env, case):
+    """Per-stage search of every variant against the FP64 oracle on the same level inputs."""
     torch, dis, dev = env
     if case == "translate":
         I0, I1, _ = synth.translation_pair(0)
@@ -150,15 +155,19 @@ def test_search_stage(env, case):
     Uc_h = (ndimage_smooth(g.normal(0, 1.5, (hc, wc, 2))) * 1.0).astype(np.float32)
     Uc = torch.from_numpy(Uc_h).to(dev)
     nx, ny = oracle.grid_n(W, ps, stride), oracle.grid_n(H, ps, stride)
-    u = torch.zeros((ny * nx, 2), device=dev)
-    ui = torch.zeros((ny * nx, 2), device=dev)
-    st = torch.zeros(ny * nx, dtype=torch.int32, device=dev)
-    dis.dis_search_level(a, b, W, H, pitch, Uc, wc, hc, 2.0, ps, stride, iters, u, ui, st)
-    torch.cuda.synchronize()
-    e, ndiff, _ = compare_search(host(a, W), host(b, W), Uc_h.astype(np.float64), 2.0, ps, stride, iters, host(u),
-                                 host(ui), st.cpu().numpy())
-    print("search %s: %d patches, max |du| %.2e, %s" % (case, nx * ny, e, ndiff))
-    assert e <= STAGE_TOL
+    ref = None
+    for variant in [0] + dis.dis_search_variants(ps):
+        u = torch.zeros((ny * nx, 2), device=dev)
+        ui = torch.zeros((ny * nx, 2), device=dev)
+        st = torch.zeros(ny * nx, dtype=torch.int32, device=dev)
+        dis.dis_search_level_ex(a, b, W, H, pitch, Uc, wc, hc, 2.0, ps, stride, iters, variant, u, ui, st)
+        torch.cuda.synchronize()
+        e, ndiff, ref = compare_search(host(a, W), host(b, W), Uc_h.astype(np.float64), 2.0, ps, stride, iters,
+                                       host(u), host(ui), st.cpu().numpy(), ref)
+        print("search %s variant %d: %d patches, max |du| %.2e, %s" % (case, variant, nx * ny, e, ndiff))
+        assert e <= STAGE_TOL
+    with pytest.raises(dis.DisError):
+        dis.dis_search_level_ex(a, b, W, H, pitch, Uc, wc, hc, 2.0, ps, stride, iters, 3, u, ui, st)
 
 
 def ndimage_smooth(a):
@@ -406,26 +415,117 @@ def test_batched_matches_plain_bit_exact(env):
             assert np.array_equal(host(f), plain[k]), (preset, sizes[k])
 
 
-@pytest.mark.parametrize("preset", ["fast", "dense"])
-def test_autotuned_search_variant_keeps_parity(env, preset):
+def test_trace_and_probe(env):
+    """dis_trace_batched lists the plan's launch groups with device times and gives the same
+    flows as a normal call; the probe times one group inside the replayed graph."""
     torch, dis, dev = env
-    pairs = [synth.layered_pair(60 + k, width=320, height=240, n_ellipses=6, max_disp=12.0) for k in range(3)]
-    p = dis.dis_default_params(preset)
+    pairs = [synth.layered_pair(70 + k, width=320, height=240, n_ellipses=4, max_disp=10.0) for k in range(2)]
+    p = dis.dis_default_params("medium")
     h = dis.dis_create(320, 240, len(pairs), 1)
     try:
         dev_pairs = [(to_dev(torch, a, dev), to_dev(torch, b, dev)) for a, b, _ in pairs]
         flows = [torch.zeros((240, 320, 2), device=dev) for _ in pairs]
         arr = dis.make_pairs([(a, b, 320, 240, 320, f) for (a, b), f in zip(dev_pairs, flows)])
-        dis.dis_compute_flow_batched(h, arr, len(pairs), p)
+        recs = dis.dis_trace_batched(h, arr, len(pairs), p)
+        traced = [host(f) for f in flows]
+        ss, sf, _ = dis.dis_levels(320, 240, p)
+        kinds = [r[0] for r in recs]
+        print("trace:", ["%s%d %.3f" % r for r in recs])
+        assert kinds[0] == "prep" and kinds.count("pyramid") == ss
+        assert kinds.count("search") == kinds.count("densify") == kinds.count("refine") == ss - sf + 1
+        assert all(ms > 0 for _, _, ms in recs)
+        dis.dis_set_probe(h, "search", sf)
+        with pytest.raises(dis.DisError):
+            dis.dis_probe_ms(h)
+        for _ in range(2):  # the second call replays the cached graph, with the probe's events
+            dis.dis_compute_flow_batched(h, arr, len(pairs), p)
+        ms = dis.dis_probe_ms(h)
         torch.cuda.synchronize()
-        default = [host(f) for f in flows]
-        lanes = dis.dis_autotune(h, arr, len(pairs), p)
-        assert lanes in ((8, 4, 16, 32) if p.patch_size == 8 else (16, 8, 32))
-        dis.dis_compute_flow_batched(h, arr, len(pairs), p)
-        torch.cuda.synchronize()
+        assert ms > 0
+        for k, f in enumerate(flows):
+            assert np.array_equal(host(f), traced[k])
+        dis.dis_set_probe(h, -1)
+        with pytest.raises(dis.DisError):
+            dis.dis_probe_ms(h)
     finally:
         dis.dis_destroy(h)
-    for k, f in enumerate(flows):
-        d = np.abs(host(f) - default[k])
-        print("autotuned lanes %d vs default: mean %.2e p99.9 %.2e" % (lanes, d.mean(), np.quantile(d, 0.999)))
-        assert d.mean() <= E2E_MEAN and np.quantile(d, 0.999) <= E2E_P999
+
+
+@pytest.mark.parametrize("preset", ["fast", "dense"])
+def test_pipeline_search_equals_per_stage_search_bit_exact(env, preset):
+    """For every search variant, the pipeline's search (batched job tables; the lane-per-patch
+    variant reading the per-pixel search planes) and the per-stage entry point (one job; that
+    variant reading the images) give the same patch increments bit for bit at every level.
+    Refinement is off so that the checkpoint of level s+1 is the flow the search of level s
+    starts from."""
+    torch, dis, dev = env
+    I0, I1, _ = synth.layered_pair(1001)
+    W, H = 1024, 436
+    p = dis.dis_default_params(preset, coarsest_scale=4, refine=0)
+    ss, sf, ntot = dis.dis_levels(W, H, p)
+    ps = p.patch_size
+    stride = p.stride_override or max(1, ps - int(np.floor(p.overlap * ps + 1e-4)))
+    dims = [(W, H)]
+    for _ in range(ss):
+        dims.append(((dims[-1][0] + 1) // 2, (dims[-1][1] + 1) // 2))
+    a, b = to_dev(torch, I0, dev), to_dev(torch, I1, dev)
+    lv = gpu_level_images(torch, dis, dev, I0, I1, ss, scale=p.intensity_scale)
+    h = dis.dis_create(W, H, 1, 1)
+    try:
+        for variant in dis.dis_search_variants(ps):
+            dis.dis_set_search_variant(h, ps, variant)
+            ck = torch.zeros(sum(dims[s][0] * dims[s][1] for s in range(sf, ss + 1)) * 2, device=dev)
+            rec = torch.zeros((ntot, 2), device=dev)
+            flow = torch.zeros((H, W, 2), device=dev)
+            dis.dis_compute_flow_ex(h, a, b, W, H, W, p, None, None, rec, ck, flow)
+            off_r = off_c = 0
+            prev = None
+            for s in range(ss, sf - 1, -1):
+                A, B, w, hh, pitch = lv[s]
+                n = oracle.grid_n(w, ps, stride) * oracle.grid_n(hh, ps, stride)
+                u = torch.zeros((n, 2), device=dev)
+                ui = torch.zeros((n, 2), device=dev)
+                Uc, wc, hc, cs = (None, w, hh, 1.0) if prev is None else prev + (2.0,)
+                dis.dis_search_level_ex(A, B, w, hh, pitch, Uc, wc, hc, cs, ps, stride, p.grad_iters, variant, u, ui)
+                torch.cuda.synchronize()
+                nd = int((u - ui != rec[off_r:off_r + n]).any(1).sum())
+                print("variant %d level %d (%dx%d): %d patches, %d differ" % (variant, s, w, hh, n, nd))
+                assert nd == 0
+                off_r += n
+                prev = (ck[off_c:off_c + w * hh * 2], w, hh)
+                off_c += w * hh * 2
+    finally:
+        dis.dis_destroy(h)
+
+
+@pytest.mark.parametrize("preset", ["fast", "dense"])
+def test_every_search_variant_and_the_autotuner_keep_parity(env, preset):
+    """Each search variant (one lane per patch, and the grouped forms) end to end against the
+    FP64 oracle on the same pairs, then the variant the autotuner keeps."""
+    torch, dis, dev = env
+    pairs = [synth.layered_pair(60 + k, width=320, height=240, n_ellipses=6, max_disp=12.0) for k in range(2)]
+    p = dis.dis_default_params(preset)
+    refs = [oracle_e2e(a, b, oracle_params(p)) for a, b, _ in pairs]
+    variants = dis.dis_search_variants(p.patch_size)
+    assert 1 in variants and len(set(variants)) == len(variants) >= 2
+    h = dis.dis_create(320, 240, len(pairs), 1)
+    try:
+        dev_pairs = [(to_dev(torch, a, dev), to_dev(torch, b, dev)) for a, b, _ in pairs]
+        flows = [torch.zeros((240, 320, 2), device=dev) for _ in pairs]
+        arr = dis.make_pairs([(a, b, 320, 240, 320, f) for (a, b), f in zip(dev_pairs, flows)])
+        with pytest.raises(dis.DisError):
+            dis.dis_set_search_variant(h, p.patch_size, 3)
+        for lanes in variants:
+            dis.dis_set_search_variant(h, p.patch_size, lanes)
+            dis.dis_compute_flow_batched(h, arr, len(pairs), p)
+            torch.cuda.synchronize()
+            for k, f in enumerate(flows):
+                check_e2e("%s lanes=%d pair %d" % (preset, lanes, k), host(f), refs[k])
+        lanes = dis.dis_autotune(h, arr, len(pairs), p)
+        assert lanes in variants
+        dis.dis_compute_flow_batched(h, arr, len(pairs), p)
+        torch.cuda.synchronize()
+        for k, f in enumerate(flows):
+            check_e2e("%s autotuned lanes=%d pair %d" % (preset, lanes, k), host(f), refs[k])
+    finally:
+        dis.dis_destroy(h)
