@@ -76,6 +76,31 @@ __device__ __forceinline__ float2 init_flow_at(const float2* Uc, int wc, int hc,
     return make_float2(cscale * v.x, cscale * v.y);
 }
 
+// Advances a patch search by one accepted update (u, v) -> (un, vn) and reports whether every
+// later iteration is already known.  The update is a deterministic function of u, v and the
+// current cell sums, so: if it leaves (u, v) unchanged, all later iterations repeat it (fixed
+// point); if it returns to the iterate before the current one (u1, v1) without a rebuild of
+// the cell sums in between (quiet >= 2), the search alternates between the two points and the
+// last iterate follows from the parity of the `left` iterations still to run.  Either way
+// (u, v) is set to the result of the full iteration count, bit for bit.
+__device__ __forceinline__ bool search_cycle_exit(float& u, float& v, float un, float vn, float& u1, float& v1,
+                                                  int quiet, int left)
+{
+    if (un == u && vn == v) return true;
+    if (quiet >= 2 && un == u1 && vn == v1) {
+        if ((left & 1) == 0) {
+            u = un;
+            v = vn;
+        }
+        return true;
+    }
+    u1 = u;
+    v1 = v;
+    u = un;
+    v = vn;
+    return false;
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                 float Q[12];  // T0..T3, Gx0..Gx3, Gy0..Gy3 of the current cell
                 int ciu = INT_MIN, civ = INT_MIN;
                 float mref = mean0, mcur = mean0;
+                float u1 = 0.0f, v1 = 0.0f;  // the iterate before the current one
+                int quiet = 0;               // 1 + iterations since the last rebuild
                 for (int it = 0; it < iters; ++it) {
                     const float uc = fminf(fmaxf(u, -1.0e7f), 1.0e7f);
                     const float vc = fminf(fmaxf(v, -1.0e7f), 1.0e7f);
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                         ciu = iu;
                         civ = iv;
                         mref = mcur;
+                        quiet = 0;
                         const int xi = px + iu, yi = py + iv;
                         const bool inside = xi >= 0 && yi >= 0 && xi + ps <= w - 1 && yi + ps <= h - 1;
 #pragma unroll
@@ -178,8 +181,10 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                     const float e = (A0 + sT) * inv_n;  // mean of the window minus mref
                     const float b0 = fmaf(-e, sgx, Ax), b1 = fmaf(-e, sgy, Ay);
                     mcur = mref + e;
-                    u -= fmaf(k00, b0, k01 * b1);
-                    v -= fmaf(k01, b0, k11 * b1);
+                    const float un = u - fmaf(k00, b0, k01 * b1);
+                    const float vn = v - fmaf(k01, b0, k11 * b1);
+                    ++quiet;
+                    if (search_cycle_exit(u, v, un, vn, u1, v1, quiet, iters - 1 - it)) break;
                 }
                 const float ex = u - ui.x, ey = v - ui.y;
                 if (ex * ex + ey * ey > (float)(ps * ps)) {

@@ -183,12 +183,15 @@ __global__ void __launch_bounds__(kCoopWarps * 32, MINB)
             if (gl == 0) s_desc[wib][grp] = CoopDesc{J.S1, pitch, w, h, px, py};
         }
         __syncwarp();
-        if (__any_sync(kFull, run)) {
+        bool live = run;           // still iterating (a fixed point or a 2-cycle ends it early)
+        float u1 = 0.0f, v1 = 0.0f;  // the iterate before the current one
+        int quiet = 0;               // 1 + iterations since the last rebuild
+        if (__any_sync(kFull, live)) {
             for (int it = 0; it < iters; ++it) {
                 float ax = 0.0f, ay = 0.0f;
                 int iu = 0, iv = 0;
                 bool need = false;
-                if (run) {
+                if (live) {
                     const float uc = fminf(fmaxf(u, -1.0e7f), 1.0e7f);
                     const float vc = fminf(fmaxf(v, -1.0e7f), 1.0e7f);
                     const float fu = floorf(uc), fv = floorf(vc);
@@ -248,18 +251,22 @@ __global__ void __launch_bounds__(kCoopWarps * 32, MINB)
                         ciu = siu;
                         civ = siv;
                         mref = sref;
+                        quiet = 0;
                     }
                 }
-                if (run) {
+                if (live) {
                     const float A0 = fmaf(ay, fmaf(ax, Q[3], Q[2]), fmaf(ax, Q[1], Q[0]));
                     const float Ax = fmaf(ay, fmaf(ax, Q[7], Q[6]), fmaf(ax, Q[5], Q[4]));
                     const float Ay = fmaf(ay, fmaf(ax, Q[11], Q[10]), fmaf(ax, Q[9], Q[8]));
                     const float e = (A0 + sT) * inv_n;  // mean of the window minus mref
                     const float b0 = fmaf(-e, sgx, Ax), b1 = fmaf(-e, sgy, Ay);
                     mcur = mref + e;
-                    u -= fmaf(k00, b0, k01 * b1);
-                    v -= fmaf(k01, b0, k11 * b1);
+                    const float un = u - fmaf(k00, b0, k01 * b1);
+                    const float vn = v - fmaf(k01, b0, k11 * b1);
+                    ++quiet;
+                    if (search_cycle_exit(u, v, un, vn, u1, v1, quiet, iters - 1 - it)) live = false;
                 }
+                if (!__any_sync(kFull, live)) break;
             }
         }
         if (run) {
