@@ -151,6 +151,7 @@ struct Phase {
     int n;
     long long total, total2, total3;
     int s;
+    long long total4 = 0;  // refinement tiles of a LEVEL phase
 };
 
 struct Plan {
@@ -202,6 +203,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     const int32_t* pw = reinterpret_cast<const int32_t*>(&p);
     for (size_t i = 0; i < sizeof(dis_params) / 4; ++i) plan.key.push_back(pw[i]);
     plan.key.push_back(hd->search_lanes[p.patch_size]);
+    plan.key.push_back(hd->refine_fused ? 1 : 0);
     plan.key.push_back(hd->probe_kind);
     plan.key.push_back(hd->probe_level);
 
@@ -273,7 +275,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     // per-level chain
     for (int s = max_ss; s >= fsf; --s) {
         std::vector<LevelJob> t;
-        long long pb = 0, xb = 0, hb = 0;
+        long long pb = 0, xb = 0, hb = 0, tb = 0;
         for (int i = 0; i < n; ++i) {
             if (ss[i] < s) continue;
             LevelJob J;
@@ -319,6 +321,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.patch_base = pb;
             J.pix_base = xb;
             J.half_base = hb;
+            dis::set_refine_tiles(J, tb);
             pb += (long long)J.nx * J.ny;
             xb += (long long)w * h;
             hb += (long long)h * ((w + 1) / 2);
@@ -330,7 +333,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
                 plan.graphable = false;
             }
         }
-        plan.phases.push_back({Phase::LEVEL, push_table(plan.blob, t), (int)t.size(), pb, xb, hb, s});
+        plan.phases.push_back({Phase::LEVEL, push_table(plan.blob, t), (int)t.size(), pb, xb, hb, s, tb});
     }
     // final up-scaling
     if (fsf > 0) {
@@ -424,8 +427,10 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                     a.gamma = p.gamma;
                     a.alpha = p.alpha;
                     a.omega = p.sor_omega;
+                    a.fused = hd->refine_fused;
+                    a.C = p.channels;
                     e = traced(DIS_LAUNCH_REFINE, ph.s,
-                               [&] { return dis::launch_refine(js, ph.total2, ph.total3, a, hd->lc, s); });
+                               [&] { return dis::launch_refine(js, ph.total2, ph.total3, ph.total4, a, hd->lc, s); });
                 }
                 break;
             }
@@ -721,6 +726,13 @@ dis_status dis_trace_batched(dis_handle* hd, const dis_pair* pairs, int n, const
     return DIS_OK;
 }
 
+dis_status dis_set_refine_fusion(dis_handle* hd, int fused)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    hd->refine_fused = fused != 0;
+    return DIS_OK;
+}
+
 dis_status dis_set_probe(dis_handle* hd, int kind, int level)
 {
     if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
@@ -883,9 +895,11 @@ dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, in
     J.C = channels;
     J.U = reinterpret_cast<float2*>(U);
     J.rs = reinterpret_cast<float*>(hd->arena + hd->off_rs);
-    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega};
+    long long tiles = 0;
+    dis::set_refine_tiles(J, tiles);
+    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega, hd->refine_fused, channels};
     const long long tp = (long long)w * h, th = (long long)h * ((w + 1) / 2);
-    cudaError_t e = dis::launch_refine(dis::single_job(J), tp, th, a, hd->lc, (cudaStream_t)stream);
+    cudaError_t e = dis::launch_refine(dis::single_job(J), tp, th, tiles, a, hd->lc, (cudaStream_t)stream);
     return e == cudaSuccess ? DIS_OK : cuda_fail(hd, e, "dis_refine_level");
 }
 

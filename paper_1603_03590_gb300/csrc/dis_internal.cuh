@@ -34,6 +34,8 @@ struct LevelJob {
     long long patch_base; // first flattened patch of this job
     long long pix_base;   // first flattened pixel
     long long half_base;  // first flattened same-colour pixel (h * ceil(w/2) per colour)
+    long long tile_base;  // first flattened refinement tile (kRefineTile^2 pixels each)
+    int tiles_x;          // refinement tiles per row
     int w, h, pitch;
     int wc, hc;
     float cscale;
@@ -140,14 +142,26 @@ cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, in
 struct RefineArgs {
     int outer, inner;
     float delta, gamma, alpha, omega;
+    bool fused = true;  // one launch per outer iteration (temporal blocking) when inner allows
+    int C = 1;          // channels of every job of the launch
 };
-cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, const RefineArgs& a,
-                          const LaunchCfg& lc, cudaStream_t s);
-cudaError_t launch_refine_prepare(const Jobs<LevelJob>& js, long long total_pix, const LaunchCfg& lc, cudaStream_t s);
-cudaError_t launch_refine_weights(const Jobs<LevelJob>& js, long long total_pix, const RefineArgs& a,
-                                  const LaunchCfg& lc, cudaStream_t s);
-cudaError_t launch_refine_half_sweep(const Jobs<LevelJob>& js, long long total_half, int colour, float omega,
-                                     const LaunchCfg& lc, cudaStream_t s);
+// Square tiles of the fused outer-iteration kernel; at most kRefineMaxFusedInner inner sweeps
+// (2 half-sweeps each) run in one launch, the halo being as wide as the half-sweeps.
+constexpr int kRefineTile = 32;
+constexpr int kRefineMaxFusedInner = 5;
+constexpr long long kRefineFusedMaxPixels = 4LL << 20;  // larger launches use per-sweep kernels
+inline long long refine_tiles(int w, int h)
+{
+    return (long long)((w + kRefineTile - 1) / kRefineTile) * ((h + kRefineTile - 1) / kRefineTile);
+}
+inline void set_refine_tiles(LevelJob& J, long long& tile_base)
+{
+    J.tiles_x = (J.w + kRefineTile - 1) / kRefineTile;
+    J.tile_base = tile_base;
+    tile_base += refine_tiles(J.w, J.h);
+}
+cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, long long total_tiles,
+                          const RefineArgs& a, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_upsample(const Jobs<UpJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
 
 LaunchCfg query_launch_cfg();

@@ -76,9 +76,11 @@ extern "C" dis_status dis_refine_level_noalloc(const float* I0, const float* I1,
     J.C = channels;
     J.U = reinterpret_cast<float2*>(U);
     J.rs = scratch;  // every plane is written before it is read; the increments are zeroed first
-    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega};
-    e = dis::launch_refine(dis::single_job(J), (long long)w * h, (long long)h * ((w + 1) / 2), a, dis::stage_launch_cfg(),
-                           (cudaStream_t)stream);
+    long long tiles = 0;
+    dis::set_refine_tiles(J, tiles);
+    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega, true, channels};
+    e = dis::launch_refine(dis::single_job(J), (long long)w * h, (long long)h * ((w + 1) / 2), tiles, a,
+                           dis::stage_launch_cfg(), (cudaStream_t)stream);
     if (e != cudaSuccess) return noalloc_fail(DIS_ERR_CUDA, std::string("dis_refine_level_noalloc: ") + cudaGetErrorString(e));
     return DIS_OK;
 }

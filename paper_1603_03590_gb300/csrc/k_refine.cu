@@ -18,6 +18,13 @@
 //   weights  A (3), b (2), psiS from the data values and U + dU        (per outer pass)
 //   sor      one colour of one sweep                                   (2 per sweep)
 //   apply    U += dU                                                   (once per level)
+// or, fused (the default), weights and all half-sweeps of one outer pass in one launch: each
+// block loads a 32x32 tile with a halo as wide as the half-sweeps (K <= 10) into shared
+// memory, computes the lagged weights there, runs the K red-black half-sweeps with a block
+// barrier between them (the halo absorbs the values that go stale at the tile's edge: after
+// half-sweep j only pixels within K - j of the tile are still exact) and writes the tile's
+// increments to the other of two increment buffers.  The arithmetic is shared with the
+// per-sweep kernels, so both forms give the same result bit for bit.
 #include <algorithm>
 
 #include "dis_device.cuh"
@@ -112,18 +119,16 @@ __global__ void __launch_bounds__(256) refine_deriv2_kernel(const __grid_constan
     DIS_PIX_END
 }
 
-__global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_constant__ Jobs<LevelJob> js,
-                                                             long long total, float delta, float gamma, float alpha)
+// Lagged data terms of pixel o at increment (du, dv): the 2x2 system A dU = b of the data
+// energy with psi = weight * Psi'(.) frozen (summed over channels inside each Psi).
+__device__ __forceinline__ void refine_data_system(const float* __restrict__ rs, int C, long long pl, long long o,
+                                                   float du, float dv, float delta, float gamma, float& a11,
+                                                   float& a12, float& a22, float& b1, float& b2)
 {
     const float eps2 = 1.0e-6f;
-    DIS_PIX_LOOP(pix_base)
-    const long long pl = J.plane;
-    const float* du_p = J.rs + rs_du(J.C, 0) * pl;
-    const float* dv_p = J.rs + rs_du(J.C, 1) * pl;
-    const float du = du_p[o], dv = dv_p[o];
     float EI = 0.0f, EG = 0.0f;
-    for (int c = 0; c < J.C; ++c) {
-        const float* D = J.rs + rs_dat(J.C, c, 0) * pl + o;
+    for (int c = 0; c < C; ++c) {
+        const float* D = rs + rs_dat(C, c, 0) * pl + o;
         const float eI = fmaf(D[0], du, fmaf(D[pl], dv, D[2 * pl]));
         const float eX = fmaf(D[3 * pl], du, fmaf(D[4 * pl], dv, D[5 * pl]));
         const float eY = fmaf(D[6 * pl], du, fmaf(D[7 * pl], dv, D[8 * pl]));
@@ -132,9 +137,9 @@ __global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_consta
     }
     const float psiI = delta / (2.0f * sqrtf(EI + eps2));
     const float psiG = gamma / (2.0f * sqrtf(EG + eps2));
-    float a11 = 0.0f, a12 = 0.0f, a22 = 0.0f, b1 = 0.0f, b2 = 0.0f;
-    for (int c = 0; c < J.C; ++c) {
-        const float* D = J.rs + rs_dat(J.C, c, 0) * pl + o;
+    a11 = a12 = a22 = b1 = b2 = 0.0f;
+    for (int c = 0; c < C; ++c) {
+        const float* D = rs + rs_dat(C, c, 0) * pl + o;
         const float d0 = D[0], d1 = D[pl], d2 = D[2 * pl], d3 = D[3 * pl], d4 = D[4 * pl], d5 = D[5 * pl];
         const float d6 = D[6 * pl], d7 = D[7 * pl], d8 = D[8 * pl];
         a11 += psiI * d0 * d0 + psiG * (d3 * d3 + d6 * d6);
@@ -143,6 +148,30 @@ __global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_consta
         b1 -= psiI * d2 * d0 + psiG * (d5 * d3 + d8 * d6);
         b2 -= psiI * d2 * d1 + psiG * (d5 * d4 + d8 * d7);
     }
+}
+
+// Smoothness weight alpha * Psi'(|grad(u + du)|^2) from the four central differences.
+__device__ __forceinline__ float refine_smooth_weight(float ux, float uy, float vx, float vy, float alpha)
+{
+    const float ES = ux * ux + uy * uy + vx * vx + vy * vy;
+    return alpha / (2.0f * sqrtf(ES + 1.0e-6f));
+}
+
+// Central difference 0.5 * ((U_r + dU_r) - (U_l + dU_l)) of one component.
+__device__ __forceinline__ float refine_cdiff(float Ur, float dur, float Ul, float dul)
+{
+    return 0.5f * ((Ur + dur) - (Ul + dul));
+}
+
+__global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_constant__ Jobs<LevelJob> js,
+                                                             long long total, float delta, float gamma, float alpha)
+{
+    DIS_PIX_LOOP(pix_base)
+    const long long pl = J.plane;
+    const float* du_p = J.rs + rs_du(J.C, 0) * pl;
+    const float* dv_p = J.rs + rs_du(J.C, 1) * pl;
+    float a11, a12, a22, b1, b2;
+    refine_data_system(J.rs, J.C, pl, o, du_p[o], dv_p[o], delta, gamma, a11, a12, a22, b1, b2);
     // smoothness: central differences of u + du, replicated border
     const int xl = max(x - 1, 0), xr = min(x + 1, w - 1), yu = max(y - 1, 0), yd = min(y + 1, h - 1);
     const long long fl = (long long)y * w + xl, fr = (long long)y * w + xr;
@@ -150,19 +179,45 @@ __global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_consta
     const long long ol = (long long)y * pitch + xl, orr = (long long)y * pitch + xr;
     const long long ou = (long long)yu * pitch + x, od = (long long)yd * pitch + x;
     const float2 Ul = J.U[fl], Ur = J.U[fr], Uu = J.U[fu], Ud = J.U[fd];
-    const float ux = 0.5f * ((Ur.x + du_p[orr]) - (Ul.x + du_p[ol]));
-    const float vx = 0.5f * ((Ur.y + dv_p[orr]) - (Ul.y + dv_p[ol]));
-    const float uy = 0.5f * ((Ud.x + du_p[od]) - (Uu.x + du_p[ou]));
-    const float vy = 0.5f * ((Ud.y + dv_p[od]) - (Uu.y + dv_p[ou]));
-    const float ES = ux * ux + uy * uy + vx * vx + vy * vy;
+    const float ux = refine_cdiff(Ur.x, du_p[orr], Ul.x, du_p[ol]);
+    const float vx = refine_cdiff(Ur.y, dv_p[orr], Ul.y, dv_p[ol]);
+    const float uy = refine_cdiff(Ud.x, du_p[od], Uu.x, du_p[ou]);
+    const float vy = refine_cdiff(Ud.y, dv_p[od], Uu.y, dv_p[ou]);
     float* S = J.rs + rs_sys(J.C, 0) * pl + o;
     S[0] = a11;
     S[pl] = a12;
     S[2 * pl] = a22;
     S[3 * pl] = b1;
     S[4 * pl] = b2;
-    S[5 * pl] = alpha / (2.0f * sqrtf(ES + eps2));
+    S[5 * pl] = refine_smooth_weight(ux, uy, vx, vy, alpha);
     DIS_PIX_END
+}
+
+// One SOR update of pixel p: neighbours q (left, right, up, down; `in[q]` false outside the
+// image) with smoothness weights psq, flows Uq and increments dq; updates (du, dv) in place.
+__device__ __forceinline__ void refine_sor_update(float a11, float a12, float a22, float b1, float b2, float ps_p,
+                                                  const bool (&in)[4], const float (&psq)[4], const float2 (&Uq)[4],
+                                                  const float (&duq)[4], const float (&dvq)[4], float2 Up,
+                                                  float omega, float& du, float& dv)
+{
+    float sw = 0.0f, r1 = b1, r2 = b2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!in[q]) continue;
+        const float wq = 0.5f * (ps_p + psq[q]);
+        sw += wq;
+        r1 = fmaf(wq, (Uq[q].x + duq[q]) - Up.x, r1);
+        r2 = fmaf(wq, (Uq[q].y + dvq[q]) - Up.y, r2);
+    }
+    const float m11 = a11 + sw, m12 = a12, m22 = a22 + sw;
+    const float det = m11 * m22 - m12 * m12;
+    if (det > 0.0f) {
+        const float id = 1.0f / det;
+        const float d1 = (m22 * r1 - m12 * r2) * id;
+        const float d2 = (m11 * r2 - m12 * r1) * id;
+        du = (1.0f - omega) * du + omega * d1;
+        dv = (1.0f - omega) * dv + omega * d2;
+    }
 }
 
 // One colour of one red-black sweep: the pixels with (x + y) % 2 == colour.
@@ -182,46 +237,206 @@ __global__ void __launch_bounds__(256) refine_sor_kernel(const __grid_constant__
         const float* S = J.rs + rs_sys(J.C, 0) * pl;
         float* du_p = J.rs + rs_du(J.C, 0) * pl;
         float* dv_p = J.rs + rs_du(J.C, 1) * pl;
-        const float ps_ = S[5 * pl + o];
-        const float2 Up = J.U[f];
-        float sw = 0.0f, r1 = S[3 * pl + o], r2 = S[4 * pl + o];
         const int nxs[4] = {x - 1, x + 1, x, x};
         const int nys[4] = {y, y, y - 1, y + 1};
+        bool in[4];
+        float psq[4], duq[4], dvq[4];
+        float2 Uq[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int qx = nxs[q], qy = nys[q];
-            if (qx < 0 || qx >= w || qy < 0 || qy >= h) continue;
-            const long long oq = (long long)qy * pitch + qx;
-            const float wq = 0.5f * (ps_ + S[5 * pl + oq]);
-            const float2 Uq = J.U[(long long)qy * w + qx];
-            sw += wq;
-            r1 = fmaf(wq, (Uq.x + du_p[oq]) - Up.x, r1);
-            r2 = fmaf(wq, (Uq.y + dv_p[oq]) - Up.y, r2);
+            in[q] = qx >= 0 && qx < w && qy >= 0 && qy < h;
+            const long long oq = in[q] ? (long long)qy * pitch + qx : o;
+            psq[q] = S[5 * pl + oq];
+            duq[q] = du_p[oq];
+            dvq[q] = dv_p[oq];
+            Uq[q] = J.U[in[q] ? (long long)qy * w + qx : f];
         }
-        const float m11 = S[o] + sw, m12 = S[pl + o], m22 = S[2 * pl + o] + sw;
-        const float det = m11 * m22 - m12 * m12;
-        if (det > 0.0f) {
-            const float id = 1.0f / det;
-            const float d1 = (m22 * r1 - m12 * r2) * id;
-            const float d2 = (m11 * r2 - m12 * r1) * id;
-            du_p[o] = (1.0f - omega) * du_p[o] + omega * d1;
-            dv_p[o] = (1.0f - omega) * dv_p[o] + omega * d2;
-        }
+        float du = du_p[o], dv = dv_p[o];
+        refine_sor_update(S[o], S[pl + o], S[2 * pl + o], S[3 * pl + o], S[4 * pl + o], S[5 * pl + o], in, psq, Uq,
+                          duq, dvq, J.U[f], omega, du, dv);
+        du_p[o] = du;
+        dv_p[o] = dv;
     }
 }
 
-__global__ void __launch_bounds__(256) refine_apply_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total)
+// Weights and K half-sweeps of one outer pass on 32x32 tiles (see the header).  The increment
+// is read from planes `src` (rs_du or rs_mid(C, 0, .)) and written to planes `dst`.
+// Shared memory holds two square regions around the tile, each stored colour by colour (all
+// red pixels row by row, then all black ones) so that a half-sweep reads and writes
+// consecutive words: R1, halo K + 1, with U and the increment (du, dv) per pixel, and R0,
+// halo K, with the systems (a11, a12), (a22, b1), (b2, psiS).  The half-sweeps cover the tile
+// with a halo of K - 1 (the pixels whose neighbours all carry weights) as horizontal pixel
+// pairs, one pixel of each colour, with a fixed pair-to-thread assignment.
+constexpr int kOuterThreads = 512;
+
+// Index of local pixel (lx, ly) in a colour-split square region of even side S whose origin
+// has colour parity p.
+__device__ __forceinline__ int csplit(int lx, int ly, int S, int p)
+{
+    return ((lx + ly + p) & 1) * (S * S / 2) + ly * (S / 2) + (lx >> 1);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __grid_constant__ Jobs<LevelJob> js,
+                                                                        long long total_tiles, int src, int dst,
+                                                                        float delta, float gamma, float alpha,
+                                                                        float omega)
+{
+    extern __shared__ float4 sm4[];
+    constexpr int T = kRefineTile;
+    constexpr int H = K;                 // halo of the systems
+    constexpr int S1 = T + 2 * (H + 1);  // side of R1
+    constexpr int S0 = T + 2 * H;        // side of R0
+    constexpr int S2 = T + 2 * (H - 1);  // side of the swept region (even)
+    constexpr int E1 = S1 * S1, E0 = S0 * S0;
+    constexpr int npairs = S2 * S2 / 2, pairs_row = S2 / 2;
+    float4* r1 = sm4;                                       // (U.x, U.y, du, dv)
+    float2* r0 = reinterpret_cast<float2*>(sm4 + E1);       // 3 planes of E0 float2
+    for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        const LevelJob& J = job_ref(js, find_job(js, tile, &LevelJob::tile_base));
+        const long long tk = tile - J.tile_base;
+        const int ty = (int)(tk / J.tiles_x), tx = (int)(tk - (long long)ty * J.tiles_x);
+        const int w = J.w, h = J.h, pitch = J.pitch, C = J.C;
+        const long long pl = J.plane;
+        const float* rs = J.rs;
+        const float2* Ug = J.U;
+        const int x1 = tx * T - (H + 1), y1 = ty * T - (H + 1);  // origin of R1
+        const int p1 = (x1 + y1) & 1;                            // colour parity of R1's origin (= R0's)
+        const float* gdu = rs + (long long)src * pl;
+        const float* gdv = gdu + pl;
+        // U and the increments on R1 (zero outside the image, never used there)
+        for (int t = threadIdx.x; t < E1; t += kOuterThreads) {
+            const int ly = t / S1, lx = t - ly * S1;
+            const int x = x1 + lx, y = y1 + ly;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (x >= 0 && x < w && y >= 0 && y < h) {
+                const float2 U = Ug[(long long)y * w + x];
+                const long long o = (long long)y * pitch + x;
+                v = make_float4(U.x, U.y, gdu[o], gdv[o]);
+            }
+            r1[csplit(lx, ly, S1, p1)] = v;
+        }
+        __syncthreads();
+        // lagged weights on R0 (origin x1 + 1, y1 + 1: the same colour parity as R1)
+        for (int t = threadIdx.x; t < E0; t += kOuterThreads) {
+            const int ly = t / S0, lx = t - ly * S0;
+            const int x = x1 + 1 + lx, y = y1 + 1 + ly;
+            if (x < 0 || x >= w || y < 0 || y >= h) continue;
+            const float4 me = r1[csplit(lx + 1, ly + 1, S1, p1)];
+            // replicated border: a clamped neighbour is the pixel itself
+            const float4 L = x > 0 ? r1[csplit(lx, ly + 1, S1, p1)] : me;
+            const float4 R = x < w - 1 ? r1[csplit(lx + 2, ly + 1, S1, p1)] : me;
+            const float4 Up = y > 0 ? r1[csplit(lx + 1, ly, S1, p1)] : me;
+            const float4 Dn = y < h - 1 ? r1[csplit(lx + 1, ly + 2, S1, p1)] : me;
+            const long long o = (long long)y * pitch + x;
+            float a11, a12, a22, b1, b2;
+            refine_data_system(rs, C, pl, o, me.z, me.w, delta, gamma, a11, a12, a22, b1, b2);
+            const float ux = refine_cdiff(R.x, R.z, L.x, L.z);
+            const float vx = refine_cdiff(R.y, R.w, L.y, L.w);
+            const float uy = refine_cdiff(Dn.x, Dn.z, Up.x, Up.z);
+            const float vy = refine_cdiff(Dn.y, Dn.w, Up.y, Up.w);
+            const int c = csplit(lx, ly, S0, p1);
+            r0[c] = make_float2(a11, a12);
+            r0[E0 + c] = make_float2(a22, b1);
+            r0[2 * E0 + c] = make_float2(b2, refine_smooth_weight(ux, uy, vx, vy, alpha));
+        }
+        __syncthreads();
+        // K half-sweeps, red ((x + y) even) first
+        const int x2 = x1 + 2, y2 = y1 + 2;  // origin of the swept region
+        const bool interior = x1 >= 0 && y1 >= 0 && x1 + S1 <= w && y1 + S1 <= h;
+        for (int j = 0; j < K; ++j) {
+            const int colour = j & 1;
+            for (int pr = threadIdx.x; pr < npairs; pr += kOuterThreads) {
+                const int ly = pr / pairs_row;
+                const int y = y2 + ly;
+                const int lx = 2 * (pr - ly * pairs_row) + (((x2 + y) & 1) == colour ? 0 : 1);
+                const int x = x2 + lx;
+                if (!interior && (x < 0 || x >= w || y < 0 || y >= h)) continue;
+                // this pixel in R1 (lx + 2, ly + 2) and R0 (lx + 1, ly + 1); its neighbours
+                // have the other colour
+                const int i1 = csplit(lx + 2, ly + 2, S1, p1), i0 = csplit(lx + 1, ly + 1, S0, p1);
+                const int n1[4] = {csplit(lx + 1, ly + 2, S1, p1), csplit(lx + 3, ly + 2, S1, p1),
+                                   csplit(lx + 2, ly + 1, S1, p1), csplit(lx + 2, ly + 3, S1, p1)};
+                const int n0[4] = {csplit(lx, ly + 1, S0, p1), csplit(lx + 2, ly + 1, S0, p1),
+                                   csplit(lx + 1, ly, S0, p1), csplit(lx + 1, ly + 2, S0, p1)};
+                const bool in[4] = {interior || x > 0, interior || x < w - 1, interior || y > 0, interior || y < h - 1};
+                float psq[4], duq[4], dvq[4];
+                float2 Uq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = r1[in[q] ? n1[q] : i1];
+                    psq[q] = r0[2 * E0 + (in[q] ? n0[q] : i0)].y;
+                    Uq[q] = make_float2(v.x, v.y);
+                    duq[q] = v.z;
+                    dvq[q] = v.w;
+                }
+                float4 me = r1[i1];
+                const float2 s01 = r0[i0], s23 = r0[E0 + i0], s45 = r0[2 * E0 + i0];
+                float du = me.z, dv = me.w;
+                refine_sor_update(s01.x, s01.y, s23.x, s23.y, s45.x, s45.y, in, psq, Uq, duq, dvq,
+                                  make_float2(me.x, me.y), omega, du, dv);
+                me.z = du;
+                me.w = dv;
+                r1[i1] = me;
+            }
+            __syncthreads();
+        }
+        // the tile's increments to the other buffer
+        float* odu = J.rs + (long long)dst * pl;
+        float* odv = odu + pl;
+        for (int t = threadIdx.x; t < T * T; t += kOuterThreads) {
+            const int ly = t / T, lx = t - ly * T;
+            const int x = tx * T + lx, y = ty * T + ly;
+            if (x >= w || y >= h) continue;
+            const float4 v = r1[csplit(lx + H + 1, ly + H + 1, S1, p1)];
+            const long long o = (long long)y * pitch + x;
+            odu[o] = v.z;
+            odv[o] = v.w;
+        }
+        __syncthreads();  // shared memory is reloaded for the next tile
+    }
+}
+
+__global__ void __launch_bounds__(256) refine_apply_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
+                                                           int src)
 {
     DIS_PIX_LOOP(pix_base)
     float2 U = J.U[k];
-    U.x += J.rs[rs_du(J.C, 0) * J.plane + o];
-    U.y += J.rs[rs_du(J.C, 1) * J.plane + o];
+    U.x += J.rs[(long long)src * J.plane + o];
+    U.y += J.rs[(long long)(src + 1) * J.plane + o];
     J.U[k] = U;
     DIS_PIX_END
 }
 
-cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, const RefineArgs& a,
-                          const LaunchCfg& lc, cudaStream_t s)
+// a.outer fused passes with K half-sweeps each; on return `src` names the planes holding the
+// final increment.
+template <int K>
+static cudaError_t launch_outer(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int& src, int& dst,
+                                const LaunchCfg& lc, cudaStream_t s)
+{
+    constexpr int S1 = kRefineTile + 2 * (K + 1), S0 = kRefineTile + 2 * K;
+    constexpr size_t smem = sizeof(float4) * (size_t)S1 * S1 + sizeof(float2) * 3 * (size_t)S0 * S0;
+    static int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(refine_outer_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, refine_outer_kernel<K>, kOuterThreads, smem) !=
+                cudaSuccess ||
+            occ < 1)
+            occ = 1;
+    }
+    const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * occ);
+    for (int ot = 0; ot < a.outer; ++ot) {
+        refine_outer_kernel<K><<<gt, kOuterThreads, smem, s>>>(js, total_tiles, src, dst, a.delta, a.gamma, a.alpha,
+                                                                a.omega);
+        std::swap(src, dst);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, long long total_tiles,
+                          const RefineArgs& a, const LaunchCfg& lc, cudaStream_t s)
 {
     if (total_pix <= 0) return cudaSuccess;
     const long long cap = (long long)lc.sm_count * lc.max_blocks_256;
@@ -230,41 +445,37 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
     refine_warp_kernel<<<gp, 256, 0, s>>>(js, total_pix);
     refine_deriv1_kernel<<<gp, 256, 0, s>>>(js, total_pix);
     refine_deriv2_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    for (int ot = 0; ot < a.outer; ++ot) {
-        refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);
-        for (int it = 0; it < a.inner; ++it) {
-            refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 0, a.omega);
-            refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 1, a.omega);
+    // the increment starts in rs_du (zeroed by the warp kernel); the fused passes alternate it
+    // with the first two intermediate planes, which are free once deriv2 has run
+    const int du_plane = rs_du(a.C, 0), mid_plane = rs_mid(a.C, 0, 0);
+    // The fused form recomputes the halo (about 2.4x the swept pixels at 10 half-sweeps), so it
+    // wins where launches dominate and loses where the per-sweep kernels stream at full
+    // bandwidth: measured on GB300 the two break even near 4 M pixels per launch.
+    const bool fused = a.fused && a.inner > 0 && a.inner <= kRefineMaxFusedInner && total_tiles > 0 &&
+                       total_pix <= kRefineFusedMaxPixels;
+    if (!fused) {
+        for (int ot = 0; ot < a.outer; ++ot) {
+            refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);
+            for (int it = 0; it < a.inner; ++it) {
+                refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 0, a.omega);
+                refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 1, a.omega);
+            }
         }
+        refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, du_plane);
+        return cudaGetLastError();
     }
-    refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    return cudaGetLastError();
-}
-
-// Single phases of the refinement, for the backward pass, which recomputes the forward states
-// (derivatives, lagged weights, the increment before every half-sweep) level by level.
-cudaError_t launch_refine_prepare(const Jobs<LevelJob>& js, long long total_pix, const LaunchCfg& lc, cudaStream_t s)
-{
-    const int gp = (int)std::min<long long>((total_pix + 255) / 256, (long long)lc.sm_count * lc.max_blocks_256);
-    refine_warp_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    refine_deriv1_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    refine_deriv2_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refine_weights(const Jobs<LevelJob>& js, long long total_pix, const RefineArgs& a,
-                                  const LaunchCfg& lc, cudaStream_t s)
-{
-    const int gp = (int)std::min<long long>((total_pix + 255) / 256, (long long)lc.sm_count * lc.max_blocks_256);
-    refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refine_half_sweep(const Jobs<LevelJob>& js, long long total_half, int colour, float omega,
-                                     const LaunchCfg& lc, cudaStream_t s)
-{
-    const int gh = (int)std::min<long long>((total_half + 255) / 256, (long long)lc.sm_count * lc.max_blocks_256);
-    refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, colour, omega);
+    const int K = 2 * a.inner;
+    int src = du_plane, dst = mid_plane;
+    cudaError_t e = cudaSuccess;
+    switch (K) {
+        case 2: e = launch_outer<2>(js, total_tiles, a, src, dst, lc, s); break;
+        case 4: e = launch_outer<4>(js, total_tiles, a, src, dst, lc, s); break;
+        case 6: e = launch_outer<6>(js, total_tiles, a, src, dst, lc, s); break;
+        case 8: e = launch_outer<8>(js, total_tiles, a, src, dst, lc, s); break;
+        default: e = launch_outer<10>(js, total_tiles, a, src, dst, lc, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, src);
     return cudaGetLastError();
 }
 

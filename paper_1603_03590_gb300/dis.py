@@ -75,6 +75,7 @@ _SIGS = {
     "dis_autotune": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, ctypes.POINTER(_i)]),
     "dis_search_variants": (_i, [_i, ctypes.POINTER(_i), _i]),
     "dis_set_probe": (_i, [_vp, _i, _i]),
+    "dis_set_refine_fusion": (_i, [_vp, _i]),
     "dis_probe_ms": (_i, [_vp, ctypes.POINTER(_f)]),
     "dis_trace_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, _vp, _i, ctypes.POINTER(_i)]),
     "dis_set_search_variant": (_i, [_vp, _i, _i]),
@@ -202,6 +203,11 @@ def dis_trace_batched(handle, pairs, n, params, stream=None, cap=256):
     _check(_lib.dis_trace_batched(handle, pairs, n, ctypes.byref(params), _stream(stream), out, cap,
                                   ctypes.byref(cnt)), handle)
     return [(LAUNCH_KINDS[out[k].kind], out[k].level, out[k].ms) for k in range(min(cnt.value, cap))]
+
+
+def dis_set_refine_fusion(handle, fused):
+    """Fused (one launch per lagged-weight pass) or per-sweep refinement launches."""
+    _check(_lib.dis_set_refine_fusion(handle, 1 if fused else 0), handle)
 
 
 def dis_set_probe(handle, kind, level=0):

@@ -197,8 +197,10 @@ def test_densify_stage(env, case):
     assert e <= STAGE_TOL
 
 
-@pytest.mark.parametrize("case", ["translate", "layered", "rgb", "ragged"])
+@pytest.mark.parametrize("case", ["translate", "layered", "rgb", "ragged", "ragged-fused", "tiny"])
 def test_refine_stage(env, case):
+    """Refinement of one level against the FP64 oracle; the fused form (one launch per outer
+    pass, up to 5 inner sweeps) and the per-sweep form agree bit for bit."""
     torch, dis, dev = env
     outer, inner = 2, 5
     if case == "translate":
@@ -207,6 +209,12 @@ def test_refine_stage(env, case):
     elif case == "ragged":
         I0, I1, _ = synth.layered_pair(12, width=173, height=91, max_disp=6.0)
         lv, outer, inner = 0, 3, 7
+    elif case == "ragged-fused":
+        I0, I1, _ = synth.layered_pair(14, width=173, height=91, max_disp=6.0)
+        lv, outer, inner = 0, 3, 4
+    elif case == "tiny":
+        I0, I1, _ = synth.layered_pair(15, width=13, height=9, max_disp=1.0, n_ellipses=1)
+        lv, outer, inner = 0, 2, 5
     elif case == "rgb":
         I0, I1, _ = synth.layered_pair(13, width=160, height=120, max_disp=8.0, channels=3)
         lv = 0
@@ -234,12 +242,16 @@ def test_refine_stage(env, case):
     g = np.random.default_rng(3)
     U0 = ndimage_smooth(g.normal(0, 2.0, (Hl, Wl, 2))).astype(np.float32) * 3.0
     U = torch.from_numpy(U0).to(dev)
+    U2 = U.clone()
     h = dis.dis_create(pitch, Hl, 1, C)
     try:
         dis.dis_refine_level(h, a, b, Wl, Hl, pitch, C, U, outer, inner)
+        dis.dis_set_refine_fusion(h, False)
+        dis.dis_refine_level(h, a, b, Wl, Hl, pitch, C, U2, outer, inner)
         torch.cuda.synchronize()
     finally:
         dis.dis_destroy(h)
+    assert torch.equal(U, U2), float((U - U2).abs().max())
     Uo = oracle.refine_level(P0.astype(np.float64), P1.astype(np.float64), U0.astype(np.float64), outer, inner)
     e = np.abs(host(U) - Uo).max()
     print("refine %s: max |dU| %.2e (update magnitude %.2e)" % (case, e, np.abs(Uo - U0).max()))
@@ -353,6 +365,34 @@ def test_e2e_edge_sizes(env, W, H, kw):
     p = dis.dis_default_params(**kw)
     got, _ = run_gpu(torch, dis, dev, I0, I1, p, pitch_pad=1)
     check_e2e("edge %dx%d" % (W, H), got, oracle_e2e(I0, I1, oracle_params(p)))
+
+
+@pytest.mark.parametrize("preset,C", [("medium", 1), ("dense", 3)])
+def test_e2e_fused_refinement_equals_per_sweep_bit_exact(env, preset, C):
+    """Whole pipeline, batched over uneven sizes: fused and per-sweep refinement give the same
+    flows bit for bit."""
+    torch, dis, dev = env
+    sizes = [(173, 91), (320, 240), (64, 48)]
+    pairs = [synth.layered_pair(80 + k, width=w, height=h, n_ellipses=4, max_disp=0.04 * w, channels=C)
+             for k, (w, h) in enumerate(sizes)]
+    p = dis.dis_default_params(preset, channels=C, grad_iters=16)
+    h = dis.dis_create(320, 240, len(pairs), C)
+    try:
+        dev_pairs = [(to_dev(torch, a, dev, a.shape[-1] + 5), to_dev(torch, b, dev, b.shape[-1] + 5)) for a, b, _ in pairs]
+        out = []
+        for fused in (True, False):
+            dis.dis_set_refine_fusion(h, fused)
+            flows = [torch.full((a.shape[-2], a.shape[-1], 2), float("nan"), device=dev) for a, _, _ in pairs]
+            items = [(da, db, a.shape[-1], a.shape[-2], da.shape[-1], f)
+                     for (da, db), (a, _, _), f in zip(dev_pairs, pairs, flows)]
+            dis.dis_compute_flow_batched(h, dis.make_pairs(items), len(items), p)
+            torch.cuda.synchronize()
+            out.append([host(f) for f in flows])
+    finally:
+        dis.dis_destroy(h)
+    for k in range(len(pairs)):
+        assert np.isfinite(out[0][k]).all()
+        assert np.array_equal(out[0][k], out[1][k]), (preset, sizes[k])
 
 
 def test_e2e_rgb(env):
