@@ -169,9 +169,8 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1603_03590_gb300 import replicas
+    rank, local, world = replicas.env_rank_world()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -183,10 +182,7 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         tdist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            tdist.barrier()
+    barrier = replicas.barrier
 
     B = args.batch
     uniq = [synth.layered_pair(1000 + k) for k in range(args.unique)]
@@ -266,10 +262,7 @@ def main():
         stages[kind] = stages.get(kind, 0.0) + ms
 
     # max over ranks
-    t = torch.tensor([ms_b, ms_p, ms_e], device=dev, dtype=torch.float64)
-    if world > 1:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    ms_b, ms_p, ms_e = t.tolist()
+    ms_b, ms_p, ms_e, k_ms = replicas.max_over_ranks([ms_b, ms_p, ms_e, k_ms], device=dev)
     dis.dis_destroy(h)
     if rank != 0:
         return
@@ -282,9 +275,9 @@ def main():
     hbm = peaks.get("hbm_gbs", 6800.0)
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s: 152 SMs x 128 FP32 lanes x FMA
-    value = world * B * args.steps / (ms_b / 1000.0)
-    plain = world * B * plain_steps / (ms_p / 1000.0)
-    e2e = world * B * e2e_steps / (ms_e / 1000.0)
+    value = replicas.aggregate_rate(B * args.steps, world, ms_b / 1000.0)
+    plain = replicas.aggregate_rate(B * plain_steps, world, ms_p / 1000.0)
+    e2e = replicas.aggregate_rate(B * e2e_steps, world, ms_e / 1000.0)
     abytes = algorithmic_bytes(dis, p, W, H)
     achieved = flops * B / (k_ms / 1000.0) / 1e12
     line = {
