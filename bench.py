@@ -39,17 +39,24 @@ def preset_params(dis, name):
     return dis.dis_default_params(name, coarsest_scale=4)
 
 
-def launches_per_call(dis, p, width, height, lanes):
-    """Kernels one call launches (mirrors the host plan: prep, pyramid, per level search planes
-    (lane-per-patch search variant only) + search + densify (+ refinement: 3 setup, outer x
-    (weights + 2 x inner), apply), final up-scaling)."""
+def launches_per_call(dis, p, width, height, lanes, batch):
+    """Kernels one batched call launches (mirrors the host plan: prep, pyramid, per level search
+    planes (lane-per-patch search variant only) + search + densify (+ refinement: 3 setup, then
+    per outer pass one fused launch, or weights + 2 x inner per-sweep launches when inner > 5 or
+    the level has more than 4 Mi pixels over the batch, then apply), final up-scaling)."""
     ss, sf, _ = dis.dis_levels(width, height, p)
+    w, h = width, height
+    dims = [(w, h)]
+    for _ in range(ss):
+        w, h = (w + 1) // 2, (h + 1) // 2
+        dims.append((w, h))
     n = 1 + ss
     for s in range(ss, sf - 1, -1):
         n += 2 + (1 if lanes == 1 else 0)
         if p.refine:
             outer = s + 1 if p.var_outer < 0 else p.var_outer
-            n += 3 + outer * (1 + 2 * p.var_inner) + 1
+            fused = 0 < p.var_inner <= 5 and batch * dims[s][0] * dims[s][1] <= (4 << 20)
+            n += 3 + (outer if fused else outer * (1 + 2 * p.var_inner)) + 1
     return n + (1 if sf > 0 else 0)
 
 
@@ -165,6 +172,8 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--unique", type=int, default=4, help="distinct synthetic pairs cycled through the batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="search variant to pin (dis_search_variants); default: the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -194,7 +203,11 @@ def main():
     arr = dis.make_pairs([(a, b, W, H, W, f) for a, b, f in zip(I0d, I1d, flows)])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
-    lanes = dis.dis_autotune(h, arr, B, p, stream)  # before any timing
+    if args.variant is None:
+        lanes = dis.dis_autotune(h, arr, B, p, stream)  # before any timing
+    else:
+        dis.dis_set_search_variant(h, p.patch_size, args.variant)
+        lanes = args.variant
 
     def step_batched():
         dis.dis_compute_flow_batched(h, arr, B, p, stream)
@@ -287,7 +300,7 @@ def main():
         "config": {"workload": "layered 1024x436, %s preset, 5 levels, batch %d per GPU" % (args.preset, B),
                    "batch_per_gpu": B, "preset": args.preset, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-                   "autotuned": {"search_variant": lanes}},
+                   "search_variant": lanes, "search_variant_source": "pinned" if args.variant is not None else "autotuned"},
         "plain": {"value": plain, "unit": UNIT, "ms_per_pair": ms_p / (B * plain_steps)},
         "hbm_roofline": {"algorithmic_bytes_per_pair": abytes,
                          "achieved_gbs": abytes * value / world / 1e9, "peak_gbs": hbm,
@@ -301,7 +314,7 @@ def main():
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max},
         "stages_ms_per_step": {k: round(v, 4) for k, v in stages.items()},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_call(dis, p, W, H, lanes) * args.steps,
+        "gpu_launches": launches_per_call(dis, p, W, H, lanes, B) * args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

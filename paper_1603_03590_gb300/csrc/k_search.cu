@@ -34,6 +34,41 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask)
     return v;
 }
 
+// Sums the twelve cell sums Q over the LPP lanes of a group and leaves the totals in every
+// lane of it.  For 16 lanes a transposed reduction halves the values each lane carries at
+// every exchange (12 -> 6 -> 3 -> 2 or 1 -> 1), so that each sum ends complete in one lane, and
+// 12 broadcasts return them: 24 shuffles instead of 48.  Other widths use the butterfly (the
+// transposed form raised the register use of the 8-lane variants more than it saved).
+template <int LPP>
+__device__ __forceinline__ void group_sum12(float (&Q)[12], unsigned gmask, int gl, int gbase)
+{
+    if constexpr (LPP == 16) {
+        const bool h8 = gl & 8, h4 = gl & 4, h2 = gl & 2, h1 = gl & 1;
+        float a6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            a6[k] = (h8 ? Q[k + 6] : Q[k]) + __shfl_xor_sync(gmask, h8 ? Q[k] : Q[k + 6], 8);
+        float a3[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            a3[k] = (h4 ? a6[k + 3] : a6[k]) + __shfl_xor_sync(gmask, h4 ? a6[k] : a6[k + 3], 4);
+        // three values over bit 1: the low lane keeps 0 and 1, the high lane keeps 2
+        const float r0 = __shfl_xor_sync(gmask, h2 ? a3[0] : a3[2], 2);
+        const float r1 = __shfl_xor_sync(gmask, h2 ? a3[1] : 0.0f, 2);
+        const float w2a = (h2 ? a3[2] : a3[0]) + r0;
+        const float w2b = h2 ? 0.0f : a3[1] + r1;
+        const float w1 = (h1 ? w2b : w2a) + __shfl_xor_sync(gmask, h1 ? w2a : w2b, 1);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            Q[k] = __shfl_sync(gmask, w1, gbase + 8 * (k / 6) + 4 * ((k % 6) / 3) + 2 * (k % 3 == 2) + (k % 3 == 1));
+    } else {
+#pragma unroll
+        for (int o = LPP / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 12; ++q) Q[q] += __shfl_xor_sync(gmask, Q[q], o);
+    }
+}
+
 // PSC: compile-time patch size (0: the runtime `ps_rt`).  MINB: resident blocks per SM the
 // register allocation must allow (chosen per variant so that nothing spills).
 template <int LPP, int PPL, int PSC, int MINB>
@@ -89,10 +124,16 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
             }
             const float mean0 = group_sum<LPP>(s0, gmask) * inv_n;
             float h00 = 0.0f, h01 = 0.0f, h11 = 0.0f, sgx = 0.0f, sgy = 0.0f, sT = 0.0f;
+            __syncwarp(gmask);  // every lane has read its gradient neighbourhood
 #pragma unroll
             for (int m = 0; m < PPL; ++m) {
                 const int k = gl + LPP * m;
-                if (k < n) sT += win[(k / ps + 1) * ws + k % ps + 1] - mean0;
+                if (k < n) {
+                    // the template T = I0 - mean replaces the window value (read back by this lane only)
+                    float& tv = win[(k / ps + 1) * ws + k % ps + 1];
+                    tv -= mean0;
+                    sT += tv;
+                }
                 h00 = fmaf(gx[m], gx[m], h00);
                 h01 = fmaf(gx[m], gy[m], h01);
                 h11 = fmaf(gy[m], gy[m], h11);
@@ -144,7 +185,7 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                             const int k = gl + LPP * m;
                             if (k < n) {
                                 const int kx = k % ps, ky = k / ps;
-                                const float T = win[(ky + 1) * ws + kx + 1] - mean0;
+                                const float T = win[(ky + 1) * ws + kx + 1];  // mean already removed
                                 float a, b, c, d;
                                 if (inside) {
                                     const float* p = J.S1 + (long long)(yi + ky) * pitch + (xi + kx);
@@ -170,10 +211,7 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                                 }
                             }
                         }
-#pragma unroll
-                        for (int o = LPP / 2; o > 0; o >>= 1)
-#pragma unroll
-                            for (int q = 0; q < 12; ++q) Q[q] += __shfl_xor_sync(gmask, Q[q], o);
+                        group_sum12<LPP>(Q, gmask, gl, grp * LPP);
                     }
                     const float A0 = fmaf(ay, fmaf(ax, Q[3], Q[2]), fmaf(ax, Q[1], Q[0]));
                     const float Ax = fmaf(ay, fmaf(ax, Q[7], Q[6]), fmaf(ax, Q[5], Q[4]));
