@@ -3,8 +3,9 @@
 //
 // A group of LPP lanes (4, 8, 16 or 32) owns one patch; lane l of the group owns patch pixels
 // l, l + LPP, ... (PPL of them).  The prologue stages the (ps+2)^2 window of I0 around the
-// patch in shared memory and computes the Sobel/8 gradients S' = grad T of the mean-normalised
-// template T (kept in registers) and, by group shuffle reductions, the 2x2 Hessian
+// patch in shared memory, computes the Sobel/8 gradients S' = grad T of the mean-normalised
+// template T, leaves T (in the window) and S' in shared memory (registers stay free for
+// occupancy: 24 warps per SM at 12x12) and forms, by group shuffle reductions, the 2x2 Hessian
 // H' = sum S'^T S', sum S' and sum T.
 //
 // Iterations.  u is shared by the whole patch, so while the integer part of u stays in one cell
@@ -70,8 +71,9 @@ __device__ __forceinline__ void group_sum12(float (&Q)[12], unsigned gmask, int 
 }
 
 // PSC: compile-time patch size (0: the runtime `ps_rt`).  MINB: resident blocks per SM the
-// register allocation must allow (chosen per variant so that nothing spills).
-template <int LPP, int PPL, int PSC, int MINB>
+// register allocation must allow (chosen per variant so that nothing spills).  GSM: template
+// gradients in shared memory (else in registers; measured per variant, see launch_search).
+template <int LPP, int PPL, int PSC, int MINB, bool GSM>
 __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
                                                      int ps_rt, int stride, int iters)
 {
@@ -82,7 +84,9 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
     const int grp = lane / LPP, gl = lane % LPP;
     const unsigned gmask = (LPP == 32) ? 0xffffffffu : (((1u << LPP) - 1u) << (grp * LPP));
     const int ws = ps + 2, n = ps * ps;
-    float* win = smem + (wib * GPW + grp) * ws * ws;
+    float* win = smem + (wib * GPW + grp) * (ws * ws + (GSM ? 2 * n : 0));  // the group's I0 window,
+    float* gxs = win + ws * ws;                                             // then (GSM) the template
+    float* gys = gxs + n;                                                   // gradients
     const float inv_n = 1.0f / (float)n;
     const long long step = (long long)gridDim.x * wpb * GPW;
     for (long long g = ((long long)blockIdx.x * wpb + wib) * GPW + grp; g < total; g += step) {
@@ -106,24 +110,35 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                 win[t] = __ldg(J.S0 + (long long)clampi(py - 1 + b, 0, h - 1) * pitch + clampi(px - 1 + a, 0, w - 1));
             }
             __syncwarp(gmask);
-            float gx[PPL], gy[PPL];
-            float s0 = 0.0f;
+            float s0 = 0.0f, h00 = 0.0f, h01 = 0.0f, h11 = 0.0f, sgx = 0.0f, sgy = 0.0f, sT = 0.0f;
+            float gxr[GSM ? 1 : PPL], gyr[GSM ? 1 : PPL];
 #pragma unroll
             for (int m = 0; m < PPL; ++m) {
                 const int k = gl + LPP * m;
-                gx[m] = gy[m] = 0.0f;
+                if (!GSM) gxr[GSM ? 0 : m] = gyr[GSM ? 0 : m] = 0.0f;
                 if (k < n) {
                     const int kx = k % ps, ky = k / ps;
                     const float* c0 = win + ky * ws + kx;  // (x-1, y-1)
                     const float* c1 = c0 + ws;
                     const float* c2 = c1 + ws;
                     s0 += c1[1];
-                    gx[m] = 0.125f * ((c0[2] - c0[0]) + 2.0f * (c1[2] - c1[0]) + (c2[2] - c2[0]));
-                    gy[m] = 0.125f * ((c2[0] - c0[0]) + 2.0f * (c2[1] - c0[1]) + (c2[2] - c0[2]));
+                    const float gx = 0.125f * ((c0[2] - c0[0]) + 2.0f * (c1[2] - c1[0]) + (c2[2] - c2[0]));
+                    const float gy = 0.125f * ((c2[0] - c0[0]) + 2.0f * (c2[1] - c0[1]) + (c2[2] - c0[2]));
+                    if (GSM) {
+                        gxs[k] = gx;  // read back by this lane only
+                        gys[k] = gy;
+                    } else {
+                        gxr[GSM ? 0 : m] = gx;
+                        gyr[GSM ? 0 : m] = gy;
+                    }
+                    h00 = fmaf(gx, gx, h00);
+                    h01 = fmaf(gx, gy, h01);
+                    h11 = fmaf(gy, gy, h11);
+                    sgx += gx;
+                    sgy += gy;
                 }
             }
             const float mean0 = group_sum<LPP>(s0, gmask) * inv_n;
-            float h00 = 0.0f, h01 = 0.0f, h11 = 0.0f, sgx = 0.0f, sgy = 0.0f, sT = 0.0f;
             __syncwarp(gmask);  // every lane has read its gradient neighbourhood
 #pragma unroll
             for (int m = 0; m < PPL; ++m) {
@@ -134,11 +149,6 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                     tv -= mean0;
                     sT += tv;
                 }
-                h00 = fmaf(gx[m], gx[m], h00);
-                h01 = fmaf(gx[m], gy[m], h01);
-                h11 = fmaf(gy[m], gy[m], h11);
-                sgx += gx[m];
-                sgy += gy[m];
             }
 #pragma unroll
             for (int o = LPP / 2; o > 0; o >>= 1) {
@@ -186,6 +196,8 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                             if (k < n) {
                                 const int kx = k % ps, ky = k / ps;
                                 const float T = win[(ky + 1) * ws + kx + 1];  // mean already removed
+                                const float gx = GSM ? gxs[k] : gxr[GSM ? 0 : m];
+                                const float gy = GSM ? gys[k] : gyr[GSM ? 0 : m];
                                 float a, b, c, d;
                                 if (inside) {
                                     const float* p = J.S1 + (long long)(yi + ky) * pitch + (xi + kx);
@@ -206,8 +218,8 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) {
                                     Q[q] += t[q];
-                                    Q[4 + q] = fmaf(gx[m], t[q], Q[4 + q]);
-                                    Q[8 + q] = fmaf(gy[m], t[q], Q[8 + q]);
+                                    Q[4 + q] = fmaf(gx, t[q], Q[4 + q]);
+                                    Q[8 + q] = fmaf(gy, t[q], Q[8 + q]);
                                 }
                             }
                         }
@@ -242,15 +254,16 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
     }
 }
 
-template <int LPP, int PPL, int PSC, int MINB = 1>
+template <int LPP, int PPL, int PSC, int MINB = 1, bool GSM = true>
 static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
                              const LaunchCfg& lc, cudaStream_t s)
 {
     const int threads = 128, wpb = threads / 32, per_block = wpb * (32 / LPP);
-    const size_t smem = (size_t)per_block * (ps + 2) * (ps + 2) * sizeof(float);
+    const size_t smem = (size_t)per_block * ((ps + 2) * (ps + 2) + (GSM ? 2 * ps * ps : 0)) * sizeof(float);
     static int occ = 0;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC, MINB>, threads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC, MINB, GSM>, threads,
+                                                          smem) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
@@ -258,7 +271,7 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     long long blocks = (total + per_block - 1) / per_block;
     const long long cap = (long long)lc.sm_count * occ;
     if (blocks > cap) blocks = cap;
-    search_kernel<LPP, PPL, PSC, MINB><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
+    search_kernel<LPP, PPL, PSC, MINB, GSM><<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters);
     return cudaGetLastError();
 }
 
@@ -286,7 +299,7 @@ cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int
         switch (lanes) {
             case 8: return launch_lp<8, 18, 12>(js, total, ps, stride, iters, lc, s);
             case 32: return launch_lp<32, 5, 12>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<16, 9, 12, 5>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<16, 9, 12, 5, false>(js, total, ps, stride, iters, lc, s);
         }
     }
     if (ps < 8) {
