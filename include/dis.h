@@ -166,11 +166,13 @@ typedef struct dis_launch_record {
 dis_status dis_trace_batched(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream,
                              dis_launch_record* out, int cap, int* count);
 
-/* Refinement launch form (not in the paper) for handle h: fused != 0 (the default) runs each
+/* Refinement launch form (not in the paper) for handle h.  fused = 1 (the default) runs each
  * lagged-weight pass with its SOR sweeps in one kernel launch (shared-memory tiles with a halo
- * as wide as the half-sweeps) where that is faster: up to 5 sweeps per pass and up to 4 Mi
- * pixels per launch (all pairs of a level together); other levels use per-sweep launches.
- * 0 runs one launch per half-sweep everywhere.  Both give the same result bit for bit. */
+ * as wide as the half-sweeps) where that measures faster on GB300: up to 5 sweeps per pass and
+ * up to 4 Mi pixels per launch (all pairs of a level together); other levels use per-sweep
+ * launches.  fused = 2 fuses every level with up to 5 sweeps per pass; fused = 0 runs one launch
+ * per half-sweep everywhere.  All forms give the same result bit for bit.  Other values:
+ * DIS_ERR_INVALID_ARG. */
 dis_status dis_set_refine_fusion(dis_handle* h, int fused);
 
 /* Probe (not in the paper): from now on every call of handle h records two events of its own

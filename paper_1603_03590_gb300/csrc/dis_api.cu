@@ -203,7 +203,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     const int32_t* pw = reinterpret_cast<const int32_t*>(&p);
     for (size_t i = 0; i < sizeof(dis_params) / 4; ++i) plan.key.push_back(pw[i]);
     plan.key.push_back(hd->search_lanes[p.patch_size]);
-    plan.key.push_back(hd->refine_fused ? 1 : 0);
+    plan.key.push_back(hd->refine_fused);
     plan.key.push_back(hd->probe_kind);
     plan.key.push_back(hd->probe_level);
 
@@ -729,7 +729,8 @@ dis_status dis_trace_batched(dis_handle* hd, const dis_pair* pairs, int n, const
 dis_status dis_set_refine_fusion(dis_handle* hd, int fused)
 {
     if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
-    hd->refine_fused = fused != 0;
+    if (fused < 0 || fused > 2) return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_refine_fusion: mode must be 0, 1 or 2");
+    hd->refine_fused = fused;
     return DIS_OK;
 }
 

@@ -35,7 +35,7 @@ struct dis_handle {
     dis::LaunchCfg lc{};
     bool use_graphs = true;
     int search_lanes[17] = {};  // autotuned lanes per patch by patch size (0 = default)
-    bool refine_fused = true;   // refinement: one launch per outer iteration when possible
+    int refine_fused = 1;       // refinement launch form (dis_set_refine_fusion)
     // probe: events recorded around one launch group in every call (also inside graphs)
     int probe_kind = -1, probe_level = 0;
     cudaEvent_t probe_a = nullptr, probe_b = nullptr;

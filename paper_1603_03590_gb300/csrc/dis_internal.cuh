@@ -142,7 +142,8 @@ cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, in
 struct RefineArgs {
     int outer, inner;
     float delta, gamma, alpha, omega;
-    bool fused = true;  // one launch per outer iteration (temporal blocking) when inner allows
+    int fused = 1;      // 0: per-sweep launches; 1: fused passes up to kRefineFusedMaxPixels
+                        // per launch; 2: fused passes whenever inner allows
     int C = 1;          // channels of every job of the launch
 };
 // Square tiles of the fused outer-iteration kernel; at most kRefineMaxFusedInner inner sweeps

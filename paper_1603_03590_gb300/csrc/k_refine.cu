@@ -26,6 +26,7 @@
 // increments to the other of two increment buffers.  The arithmetic is shared with the
 // per-sweep kernels, so both forms give the same result bit for bit.
 #include <algorithm>
+#include <type_traits>
 
 #include "dis_device.cuh"
 
@@ -212,7 +213,7 @@ __device__ __forceinline__ void refine_sor_update(float a11, float a12, float a2
     const float m11 = a11 + sw, m12 = a12, m22 = a22 + sw;
     const float det = m11 * m22 - m12 * m12;
     if (det > 0.0f) {
-        const float id = 1.0f / det;
+        const float id = __frcp_rn(det);  // the correctly rounded 1 / det
         const float d1 = (m22 * r1 - m12 * r2) * id;
         const float d2 = (m11 * r2 - m12 * r1) * id;
         du = (1.0f - omega) * du + omega * d1;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(256) refine_sor_kernel(const __grid_constant__
 // halo K, with the systems (a11, a12), (a22, b1), (b2, psiS).  The half-sweeps cover the tile
 // with a halo of K - 1 (the pixels whose neighbours all carry weights) as horizontal pixel
 // pairs, one pixel of each colour, with a fixed pair-to-thread assignment.
-constexpr int kOuterThreads = 512;
+constexpr int kOuterThreads = 448;  // 1250 swept pairs at K = 10: 3 per thread (2.8 on average)
 
 // Index of local pixel (lx, ly) in a colour-split square region of even side S whose origin
 // has colour parity p.
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
     constexpr int S2 = T + 2 * (H - 1);  // side of the swept region (even)
     constexpr int E1 = S1 * S1, E0 = S0 * S0;
     constexpr int npairs = S2 * S2 / 2, pairs_row = S2 / 2;
+    constexpr int HS1 = S1 / 2, HE1 = E1 / 2, HS0 = S0 / 2, HE0 = E0 / 2;  // half rows / halves
     float4* r1 = sm4;                                       // (U.x, U.y, du, dv)
     float2* r0 = reinterpret_cast<float2*>(sm4 + E1);       // 3 planes of E0 float2
     for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
@@ -318,17 +320,23 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
             r1[csplit(lx, ly, S1, p1)] = v;
         }
         __syncthreads();
-        // lagged weights on R0 (origin x1 + 1, y1 + 1: the same colour parity as R1)
+        // lagged weights on R0 (origin x1 + 1, y1 + 1: the same colour parity as R1).  In a
+        // colour-split region a pixel (lx, ly) of colour c sits at c * half + ly * S/2 + lx/2;
+        // its left / right neighbours (the other colour) at the same position minus 1 when lx
+        // is even, plus 1 when lx is odd, and its upper / lower ones one half row away.
         for (int t = threadIdx.x; t < E0; t += kOuterThreads) {
             const int ly = t / S0, lx = t - ly * S0;
             const int x = x1 + 1 + lx, y = y1 + 1 + ly;
             if (x < 0 || x >= w || y < 0 || y >= h) continue;
-            const float4 me = r1[csplit(lx + 1, ly + 1, S1, p1)];
+            const int c = (x + y) & 1;
+            const int pos = (ly + 1) * HS1 + ((lx + 1) >> 1), oth = (1 - c) * HE1 + pos;
+            const int odd = (lx + 1) & 1;
+            const float4 me = r1[c * HE1 + pos];
             // replicated border: a clamped neighbour is the pixel itself
-            const float4 L = x > 0 ? r1[csplit(lx, ly + 1, S1, p1)] : me;
-            const float4 R = x < w - 1 ? r1[csplit(lx + 2, ly + 1, S1, p1)] : me;
-            const float4 Up = y > 0 ? r1[csplit(lx + 1, ly, S1, p1)] : me;
-            const float4 Dn = y < h - 1 ? r1[csplit(lx + 1, ly + 2, S1, p1)] : me;
+            const float4 L = x > 0 ? r1[oth - 1 + odd] : me;
+            const float4 R = x < w - 1 ? r1[oth + odd] : me;
+            const float4 Up = y > 0 ? r1[oth - HS1] : me;
+            const float4 Dn = y < h - 1 ? r1[oth + HS1] : me;
             const long long o = (long long)y * pitch + x;
             float a11, a12, a22, b1, b2;
             refine_data_system(rs, C, pl, o, me.z, me.w, delta, gamma, a11, a12, a22, b1, b2);
@@ -336,52 +344,59 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
             const float vx = refine_cdiff(R.y, R.w, L.y, L.w);
             const float uy = refine_cdiff(Dn.x, Dn.z, Up.x, Up.z);
             const float vy = refine_cdiff(Dn.y, Dn.w, Up.y, Up.w);
-            const int c = csplit(lx, ly, S0, p1);
-            r0[c] = make_float2(a11, a12);
-            r0[E0 + c] = make_float2(a22, b1);
-            r0[2 * E0 + c] = make_float2(b2, refine_smooth_weight(ux, uy, vx, vy, alpha));
+            const int c0 = c * HE0 + ly * HS0 + (lx >> 1);
+            r0[c0] = make_float2(a11, a12);
+            r0[E0 + c0] = make_float2(a22, b1);
+            r0[2 * E0 + c0] = make_float2(b2, refine_smooth_weight(ux, uy, vx, vy, alpha));
         }
         __syncthreads();
-        // K half-sweeps, red ((x + y) even) first
+        // K half-sweeps, red ((x + y) even) first.  Pair pr = (ly, k) covers swept pixels
+        // (2k, ly) and (2k + 1, ly); the one of the current colour is lx = 2k + first.
         const int x2 = x1 + 2, y2 = y1 + 2;  // origin of the swept region
         const bool interior = x1 >= 0 && y1 >= 0 && x1 + S1 <= w && y1 + S1 <= h;
-        for (int j = 0; j < K; ++j) {
-            const int colour = j & 1;
-            for (int pr = threadIdx.x; pr < npairs; pr += kOuterThreads) {
-                const int ly = pr / pairs_row;
-                const int y = y2 + ly;
-                const int lx = 2 * (pr - ly * pairs_row) + (((x2 + y) & 1) == colour ? 0 : 1);
-                const int x = x2 + lx;
-                if (!interior && (x < 0 || x >= w || y < 0 || y >= h)) continue;
-                // this pixel in R1 (lx + 2, ly + 2) and R0 (lx + 1, ly + 1); its neighbours
-                // have the other colour
-                const int i1 = csplit(lx + 2, ly + 2, S1, p1), i0 = csplit(lx + 1, ly + 1, S0, p1);
-                const int n1[4] = {csplit(lx + 1, ly + 2, S1, p1), csplit(lx + 3, ly + 2, S1, p1),
-                                   csplit(lx + 2, ly + 1, S1, p1), csplit(lx + 2, ly + 3, S1, p1)};
-                const int n0[4] = {csplit(lx, ly + 1, S0, p1), csplit(lx + 2, ly + 1, S0, p1),
-                                   csplit(lx + 1, ly, S0, p1), csplit(lx + 1, ly + 2, S0, p1)};
-                const bool in[4] = {interior || x > 0, interior || x < w - 1, interior || y > 0, interior || y < h - 1};
-                float psq[4], duq[4], dvq[4];
-                float2 Uq[4];
+        auto sweep = [&](auto inner_tag) {
+            constexpr bool INNER = decltype(inner_tag)::value;  // no image border in R1
+            for (int j = 0; j < K; ++j) {
+                const int colour = j & 1;
+                for (int pr = threadIdx.x; pr < npairs; pr += kOuterThreads) {
+                    const int ly = pr / pairs_row, k = pr - ly * pairs_row;
+                    const int y = y2 + ly;
+                    const int first = ((x2 + y) & 1) == colour ? 0 : 1;
+                    const int x = x2 + 2 * k + first;
+                    if (!INNER && (x < 0 || x >= w || y < 0 || y >= h)) continue;
+                    // R1 position (2k + first + 2, ly + 2), R0 position (2k + first + 1, ly + 1)
+                    const int pos1 = (ly + 2) * HS1 + k + 1, pos0 = (ly + 1) * HS0 + k + first;
+                    const int i1 = colour * HE1 + pos1, o1 = (1 - colour) * HE1 + pos1;
+                    const int i0 = colour * HE0 + pos0, o0 = (1 - colour) * HE0 + pos0;
+                    const int n1[4] = {o1 - 1 + first, o1 + first, o1 - HS1, o1 + HS1};
+                    const int n0[4] = {o0 - first, o0 + 1 - first, o0 - HS0, o0 + HS0};
+                    const bool in[4] = {INNER || x > 0, INNER || x < w - 1, INNER || y > 0, INNER || y < h - 1};
+                    float psq[4], duq[4], dvq[4];
+                    float2 Uq[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 v = r1[in[q] ? n1[q] : i1];
-                    psq[q] = r0[2 * E0 + (in[q] ? n0[q] : i0)].y;
-                    Uq[q] = make_float2(v.x, v.y);
-                    duq[q] = v.z;
-                    dvq[q] = v.w;
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 v = r1[INNER ? n1[q] : (in[q] ? n1[q] : i1)];
+                        psq[q] = r0[2 * E0 + (INNER ? n0[q] : (in[q] ? n0[q] : i0))].y;
+                        Uq[q] = make_float2(v.x, v.y);
+                        duq[q] = v.z;
+                        dvq[q] = v.w;
+                    }
+                    float4 me = r1[i1];
+                    const float2 s01 = r0[i0], s23 = r0[E0 + i0], s45 = r0[2 * E0 + i0];
+                    float du = me.z, dv = me.w;
+                    refine_sor_update(s01.x, s01.y, s23.x, s23.y, s45.x, s45.y, in, psq, Uq, duq, dvq,
+                                      make_float2(me.x, me.y), omega, du, dv);
+                    me.z = du;
+                    me.w = dv;
+                    r1[i1] = me;
                 }
-                float4 me = r1[i1];
-                const float2 s01 = r0[i0], s23 = r0[E0 + i0], s45 = r0[2 * E0 + i0];
-                float du = me.z, dv = me.w;
-                refine_sor_update(s01.x, s01.y, s23.x, s23.y, s45.x, s45.y, in, psq, Uq, duq, dvq,
-                                  make_float2(me.x, me.y), omega, du, dv);
-                me.z = du;
-                me.w = dv;
-                r1[i1] = me;
+                __syncthreads();
             }
-            __syncthreads();
-        }
+        };
+        if (interior)
+            sweep(std::true_type{});
+        else
+            sweep(std::false_type{});
         // the tile's increments to the other buffer
         float* odu = J.rs + (long long)dst * pl;
         float* odv = odu + pl;
@@ -451,8 +466,8 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
     // The fused form recomputes the halo (about 2.4x the swept pixels at 10 half-sweeps), so it
     // wins where launches dominate and loses where the per-sweep kernels stream at full
     // bandwidth: measured on GB300 the two break even near 4 M pixels per launch.
-    const bool fused = a.fused && a.inner > 0 && a.inner <= kRefineMaxFusedInner && total_tiles > 0 &&
-                       total_pix <= kRefineFusedMaxPixels;
+    const bool fused = a.fused != 0 && a.inner > 0 && a.inner <= kRefineMaxFusedInner && total_tiles > 0 &&
+                       (a.fused == 2 || total_pix <= kRefineFusedMaxPixels);
     if (!fused) {
         for (int ot = 0; ot < a.outer; ++ot) {
             refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);

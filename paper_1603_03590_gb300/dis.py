@@ -205,9 +205,10 @@ def dis_trace_batched(handle, pairs, n, params, stream=None, cap=256):
     return [(LAUNCH_KINDS[out[k].kind], out[k].level, out[k].ms) for k in range(min(cnt.value, cap))]
 
 
-def dis_set_refine_fusion(handle, fused):
-    """Fused (one launch per lagged-weight pass) or per-sweep refinement launches."""
-    _check(_lib.dis_set_refine_fusion(handle, 1 if fused else 0), handle)
+def dis_set_refine_fusion(handle, mode):
+    """Refinement launch form: 0 per-sweep launches, 1 fused where faster (default), 2 fused
+    wherever the sweep count allows (True / False map to 1 / 0)."""
+    _check(_lib.dis_set_refine_fusion(handle, int(mode)), handle)
 
 
 def dis_set_probe(handle, kind, level=0):

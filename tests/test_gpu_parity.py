@@ -380,7 +380,7 @@ def test_e2e_fused_refinement_equals_per_sweep_bit_exact(env, preset, C):
     try:
         dev_pairs = [(to_dev(torch, a, dev, a.shape[-1] + 5), to_dev(torch, b, dev, b.shape[-1] + 5)) for a, b, _ in pairs]
         out = []
-        for fused in (True, False):
+        for fused in (1, 0, 2):
             dis.dis_set_refine_fusion(h, fused)
             flows = [torch.full((a.shape[-2], a.shape[-1], 2), float("nan"), device=dev) for a, _, _ in pairs]
             items = [(da, db, a.shape[-1], a.shape[-2], da.shape[-1], f)
@@ -388,11 +388,13 @@ def test_e2e_fused_refinement_equals_per_sweep_bit_exact(env, preset, C):
             dis.dis_compute_flow_batched(h, dis.make_pairs(items), len(items), p)
             torch.cuda.synchronize()
             out.append([host(f) for f in flows])
+        with pytest.raises(dis.DisError):
+            dis.dis_set_refine_fusion(h, 3)
     finally:
         dis.dis_destroy(h)
     for k in range(len(pairs)):
         assert np.isfinite(out[0][k]).all()
-        assert np.array_equal(out[0][k], out[1][k]), (preset, sizes[k])
+        assert np.array_equal(out[0][k], out[1][k]) and np.array_equal(out[0][k], out[2][k]), (preset, sizes[k])
 
 
 def test_e2e_rgb(env):
