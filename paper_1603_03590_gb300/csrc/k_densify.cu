@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) densify_kernel(const __grid_constant__ Jo
                 const int i = ii > ihi ? nx - 1 : ii;
                 const float2 up = J.pu[(long long)j * nx + i];
                 const float d = sample_shift(J.S1, w, h, pitch, x, y, up.x, up.y) - i0;
-                const float wt = 1.0f / fmaxf(1.0f, fabsf(d));
+                const float wt = __frcp_rn(fmaxf(1.0f, fabsf(d)));  // the correctly rounded 1 / max(1, |d|)
                 nu = fmaf(wt, up.x, nu);
                 nv = fmaf(wt, up.y, nv);
                 Z += wt;

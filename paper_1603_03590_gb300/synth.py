@@ -145,6 +145,30 @@ def mixed_resolutions(seed, n):
     return [MIXED_SIZES[int(i)] for i in g.integers(0, len(MIXED_SIZES), size=n)]
 
 
+_WORKLOADS = {"translate128x96": (0, 1), "layered1024x436": (1000, 1), "mixed": (2000, 64),
+              "layered512x256": (3000, 8), "rgb3840x2160": (4000, 4)}
+
+
+def workload_pair(name, i, n=None, base_seed=None):
+    """Pair i of workload_pairs(name, n, base_seed), generated alone (for parallel generation)."""
+    b, dn = _WORKLOADS[name]
+    base_seed = b if base_seed is None else base_seed
+    n = dn if n is None else n
+    s = base_seed + i
+    if name == "translate128x96":
+        return translation_pair(s)
+    if name == "layered1024x436":
+        return layered_pair(s)
+    if name == "mixed":
+        w, h = mixed_resolutions(base_seed, n)[i]
+        return layered_pair(s, width=w, height=h, max_disp=0.04 * w)
+    if name == "layered512x256":
+        return layered_pair(s, width=512, height=256, max_disp=20.0)
+    if name == "rgb3840x2160":
+        return layered_pair(s, width=3840, height=2160, max_disp=100.0, channels=3, rotation_deg=2.0)
+    raise KeyError(name)
+
+
 def workload_pairs(name, n=None, base_seed=None):
     """Seeded pairs of the named workload; seed of pair i = base_seed + i.
 
@@ -154,27 +178,5 @@ def workload_pairs(name, n=None, base_seed=None):
     'layered512x256'       : layered_pair 512x256 (displacements scaled with width)
     'rgb3840x2160'         : layered_pair RGB 3840x2160, 2 degree rotation, up to 200 px total
     """
-    table = {"translate128x96": (0, 1), "layered1024x436": (1000, 1), "mixed": (2000, 64),
-             "layered512x256": (3000, 8), "rgb3840x2160": (4000, 4)}
-    b, dn = table[name]
-    base_seed = b if base_seed is None else base_seed
-    n = dn if n is None else n
-    out = []
-    if name == "mixed":
-        sizes = mixed_resolutions(base_seed, n)
-    for i in range(n):
-        s = base_seed + i
-        if name == "translate128x96":
-            out.append(translation_pair(s))
-        elif name == "layered1024x436":
-            out.append(layered_pair(s))
-        elif name == "mixed":
-            w, h = sizes[i]
-            out.append(layered_pair(s, width=w, height=h, max_disp=0.04 * w))
-        elif name == "layered512x256":
-            out.append(layered_pair(s, width=512, height=256, max_disp=20.0))
-        elif name == "rgb3840x2160":
-            out.append(layered_pair(s, width=3840, height=2160, max_disp=100.0, channels=3, rotation_deg=2.0))
-        else:
-            raise KeyError(name)
-    return out
+    n = _WORKLOADS[name][1] if n is None else n
+    return [workload_pair(name, i, n, base_seed) for i in range(n)]
