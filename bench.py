@@ -39,7 +39,7 @@ def preset_params(dis, name):
     return dis.dis_default_params(name, coarsest_scale=4)
 
 
-def launches_per_call(dis, p, width, height, lanes, batch):
+def launches_per_call(dis, p, width, height, lanes, batch, refine_form=1):
     """Kernels one batched call launches (mirrors the host plan: prep, pyramid, per level search
     planes (lane-per-patch search variant only) + search + densify (+ refinement: 3 setup, then
     per outer pass one fused launch, or weights + 2 x inner per-sweep launches when inner > 5 or
@@ -55,7 +55,8 @@ def launches_per_call(dis, p, width, height, lanes, batch):
         n += 2 + (1 if lanes == 1 else 0)
         if p.refine:
             outer = s + 1 if p.var_outer < 0 else p.var_outer
-            fused = 0 < p.var_inner <= 5 and batch * dims[s][0] * dims[s][1] <= (4 << 20)
+            npx = batch * dims[s][0] * dims[s][1]
+            fused = 0 < p.var_inner <= 5 and refine_form != 0 and (refine_form == 2 or npx <= (4 << 20))
             n += 3 + (outer if fused else outer * (1 + 2 * p.var_inner)) + 1
     return n + (1 if sf > 0 else 0)
 
@@ -208,6 +209,7 @@ def main():
     else:
         dis.dis_set_search_variant(h, p.patch_size, args.variant)
         lanes = args.variant
+    refine_form = dis.dis_get_tuning(h, p.patch_size)[1]
 
     def step_batched():
         dis.dis_compute_flow_batched(h, arr, B, p, stream)
@@ -300,7 +302,8 @@ def main():
         "config": {"workload": "layered 1024x436, %s preset, 5 levels, batch %d per GPU" % (args.preset, B),
                    "batch_per_gpu": B, "preset": args.preset, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-                   "search_variant": lanes, "search_variant_source": "pinned" if args.variant is not None else "autotuned"},
+                   "search_variant": lanes, "refine_launch_form": refine_form,
+                   "tuning": "pinned search variant" if args.variant is not None else "autotuned"},
         "plain": {"value": plain, "unit": UNIT, "ms_per_pair": ms_p / (B * plain_steps)},
         "hbm_roofline": {"algorithmic_bytes_per_pair": abytes,
                          "achieved_gbs": abytes * value / world / 1e9, "peak_gbs": hbm,
@@ -314,7 +317,7 @@ def main():
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max},
         "stages_ms_per_step": {k: round(v, 4) for k, v in stages.items()},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_call(dis, p, W, H, lanes, B) * args.steps,
+        "gpu_launches": launches_per_call(dis, p, W, H, lanes, B, refine_form) * args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

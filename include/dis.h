@@ -187,8 +187,10 @@ dis_status dis_probe_ms(dis_handle* h, float* ms);
 
 /* Autotuner (not in the paper): time the inverse-search variants the library offers for this
  * workload on the caller's pairs (the batched call, 4 runs per variant, synchronising
- * `stream`) and keep the fastest in the handle for later calls with the same patch size.  The
- * runs write the pairs' flow_out.  *chosen_lanes (nullable) receives the chosen variant code:
+ * `stream`) and keep the fastest in the handle for later calls with the same patch size; then,
+ * when p->refine is set, time the refinement launch forms of dis_set_refine_fusion (1, 0, 2)
+ * with that search and keep the fastest.  The runs write the pairs' flow_out.  *chosen_lanes
+ * (nullable) receives the chosen search variant code (dis_get_tuning reports both choices):
  *   4, 8, 16, 32   grouped: that many lanes share one patch (every group runs its own updates
  *                  and rebuilds its cell sums alone);
  *   1              lane per patch: one lane runs a patch's updates, the warp rebuilds the cell
@@ -198,6 +200,10 @@ dis_status dis_probe_ms(dis_handle* h, float* ms);
  * All variants compute the same method; they differ in rounding order only. */
 dis_status dis_autotune(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream,
                         int* chosen_lanes);
+
+/* The search variant (the default one when none is pinned) and the refinement launch form
+ * (dis_set_refine_fusion) handle h uses for patch size ps; either pointer may be NULL. */
+dis_status dis_get_tuning(const dis_handle* h, int patch_size, int* search_variant, int* refine_fusion);
 
 /* Search variants offered for patch size ps (codes as for dis_autotune, the default first):
  * writes up to `cap` of them to out (nullable when cap is 0) and returns their count, or 0 for

@@ -947,35 +947,70 @@ extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n,
         if (e0) cudaEventDestroy(e0);
         return fail(hd, DIS_ERR_CUDA, "dis_autotune: event creation failed");
     }
-    const int ps = p->patch_size;
-    const int keep = hd->search_lanes[ps];
-    float best_ms = 1e30f;
-    int best = keep;
-    dis_status st = DIS_OK;
-    for (int k = 0; k < nopt && st == DIS_OK; ++k) {
-        hd->search_lanes[ps] = opts[k];
-        st = dis_compute_flow_batched(hd, pairs, n, p, stream);  // warm-up, builds the graph
-        if (st != DIS_OK) break;
-        float tot = 0.0f;
-        for (int r = 0; r < 3 && st == DIS_OK; ++r) {
+    // one candidate: a warm-up call (builds its graph), then the sum of 3 timed calls
+    auto time_calls = [&](float& tot) -> dis_status {
+        dis_status r = dis_compute_flow_batched(hd, pairs, n, p, stream);
+        tot = 0.0f;
+        for (int k = 0; k < 3 && r == DIS_OK; ++k) {
             cudaEventRecord(e0, s);
-            st = dis_compute_flow_batched(hd, pairs, n, p, stream);
+            r = dis_compute_flow_batched(hd, pairs, n, p, stream);
             cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(hd, cudaGetLastError(), "dis_autotune");
+            if (cudaEventSynchronize(e1) != cudaSuccess) r = cuda_fail(hd, cudaGetLastError(), "dis_autotune");
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
             tot += ms;
         }
+        return r;
+    };
+    const int ps = p->patch_size;
+    const int keep = hd->search_lanes[ps], keep_refine = hd->refine_fused;
+    float best_ms = 1e30f;
+    int best = keep, best_refine = keep_refine;
+    dis_status st = DIS_OK;
+    // the search form first, with the refinement form as it is
+    for (int k = 0; k < nopt && st == DIS_OK; ++k) {
+        hd->search_lanes[ps] = opts[k];
+        float tot = 0.0f;
+        st = time_calls(tot);
         if (st == DIS_OK && tot < best_ms) {
             best_ms = tot;
             best = opts[k];
         }
     }
+    // then the refinement launch form (per-sweep, fused where faster, fused everywhere)
+    if (st == DIS_OK && p->refine) {
+        hd->search_lanes[ps] = best;
+        best_ms = 1e30f;
+        const int modes[3] = {1, 0, 2};
+        for (int k = 0; k < 3 && st == DIS_OK; ++k) {
+            hd->refine_fused = modes[k];
+            float tot = 0.0f;
+            st = time_calls(tot);
+            if (st == DIS_OK && tot < best_ms) {
+                best_ms = tot;
+                best_refine = modes[k];
+            }
+        }
+    }
     hd->search_lanes[ps] = (st == DIS_OK) ? best : keep;
+    hd->refine_fused = (st == DIS_OK) ? best_refine : keep_refine;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (chosen_lanes) *chosen_lanes = hd->search_lanes[ps];
     return st;
+}
+
+extern "C" dis_status dis_get_tuning(const dis_handle* hd, int patch_size, int* search_variant, int* refine_fusion)
+{
+    if (!hd || patch_size < 2 || patch_size > kMaxPatch)
+        return fail(const_cast<dis_handle*>(hd), DIS_ERR_INVALID_ARG, "dis_get_tuning: handle NULL or bad patch size");
+    if (search_variant) {
+        int opts[8];
+        dis::search_lane_options(patch_size, opts);
+        *search_variant = hd->search_lanes[patch_size] ? hd->search_lanes[patch_size] : opts[0];
+    }
+    if (refine_fusion) *refine_fusion = hd->refine_fused;
+    return DIS_OK;
 }
 
 extern "C" int dis_search_variants(int patch_size, int* out, int cap)

@@ -74,6 +74,7 @@ _SIGS = {
     "dis_compute_flow_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp]),
     "dis_autotune": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, ctypes.POINTER(_i)]),
     "dis_search_variants": (_i, [_i, ctypes.POINTER(_i), _i]),
+    "dis_get_tuning": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "dis_set_probe": (_i, [_vp, _i, _i]),
     "dis_set_refine_fusion": (_i, [_vp, _i]),
     "dis_probe_ms": (_i, [_vp, ctypes.POINTER(_f)]),
@@ -222,6 +223,13 @@ def dis_probe_ms(handle):
     ms = _f()
     _check(_lib.dis_probe_ms(handle, ctypes.byref(ms)), handle)
     return ms.value
+
+
+def dis_get_tuning(handle, patch_size):
+    """(search variant, refinement launch form) the handle uses for this patch size."""
+    v, r = _i(), _i()
+    _check(_lib.dis_get_tuning(handle, patch_size, ctypes.byref(v), ctypes.byref(r)), handle)
+    return v.value, r.value
 
 
 def dis_search_variants(patch_size):

@@ -565,6 +565,9 @@ def test_every_search_variant_and_the_autotuner_keep_parity(env, preset):
                 check_e2e("%s lanes=%d pair %d" % (preset, lanes, k), host(f), refs[k])
         lanes = dis.dis_autotune(h, arr, len(pairs), p)
         assert lanes in variants
+        tv, tr = dis.dis_get_tuning(h, p.patch_size)
+        assert tv == lanes and tr in ((0, 1, 2) if p.refine else (1,))
+        print("%s: autotuned search variant %d, refinement launch form %d" % (preset, tv, tr))
         dis.dis_compute_flow_batched(h, arr, len(pairs), p)
         torch.cuda.synchronize()
         for k, f in enumerate(flows):
