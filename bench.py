@@ -256,16 +256,39 @@ def main():
     hin1 = [torch.from_numpy(uniq[k % len(uniq)][1]).pin_memory() for k in range(B)]
     hout = [torch.empty((H, W, 2), pin_memory=True) for _ in range(B)]
 
-    def step_e2e():
-        for k in range(B):
-            I0d[k].copy_(hin0[k], non_blocking=True)
-            I1d[k].copy_(hin1[k], non_blocking=True)
-        dis.dis_compute_flow_batched(h, arr, B, p, stream)
-        for k in range(B):
-            hout[k].copy_(flows[k], non_blocking=True)
+    harr = dis.make_pairs([(a, b, W, H, W, f) for a, b, f in zip(hin0, hin1, hout)])
 
-    e2e_steps = max(3, args.steps // 4)
-    ms_e, _, _ = timed(step_e2e, e2e_steps, 3)
+    def step_e2e():
+        # host frames in, host flows out, through the library's host-buffer call (its copies
+        # overlap the computation of the previous step)
+        dis.dis_compute_flow_batched_host(h, harr, B, p, stream)
+
+    def timed_e2e(steps, warmup):
+        """The whole run of `steps` calls between two events, the last flows in host memory
+        before the closing event (the copies of one step overlap the next, so per-step event
+        pairs would miss them); L2 flushes between steps run inside."""
+        for _ in range(warmup):
+            step_e2e()
+        dis.dis_host_flows_ready(h, stream)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            flush.fill_(1.0)
+            step_e2e()
+        dis.dis_host_flows_ready(h, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1)
+
+    e2e_steps = args.steps
+    ms_e = timed_e2e(e2e_steps, 3)
+    # the flows really arrived: the last step's host flows equal the device-resident result
+    step_batched()
+    torch.cuda.synchronize()
+    assert all(torch.equal(hout[k], flows[k].cpu()) for k in range(B)), "host-buffer flows differ"
     h2d = B * 2 * W * H * 4
     d2h = B * W * H * 2 * 4
 

@@ -143,6 +143,21 @@ dis_status dis_compute_flow_ex(dis_handle* h, const float* I0, const float* I1, 
  * repeat. */
 dis_status dis_compute_flow_batched(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream);
 
+/* dis_compute_flow_batched on frames and flows in HOST memory (pinned memory gives full copy
+ * speed; pageable memory works, slower).  The handle copies the frames of the n pairs into
+ * device staging of its own (allocated on first use and grown when a call needs more), computes
+ * on `stream`, and copies the flows back into each pair's host flow_out.  The copies run on a
+ * stream of the handle, and the staging is double-buffered, so the copies of one call overlap
+ * the computation of the previous one.  The call returns once the work is enqueued: host
+ * buffers must stay valid and unchanged, and flows must not be read, until
+ * dis_host_flows_ready(h, stream) has been issued and `stream` synchronised. */
+dis_status dis_compute_flow_batched_host(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p,
+                                        void* stream);
+
+/* Makes `stream` wait until the flows of every earlier dis_compute_flow_batched_host call on h
+ * are in host memory (synchronise `stream` afterwards to wait on the host). */
+dis_status dis_host_flows_ready(dis_handle* h, void* stream);
+
 /* Tracing (not in the paper): runs the batched call once without a CUDA graph, with events on
  * `stream` on both sides of every launch group of the plan, synchronises `stream` and writes one
  * record per group (up to `cap`; *count receives the total): the kind below, the pyramid level

@@ -633,6 +633,16 @@ void dis_destroy(dis_handle* h)
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     if (h->probe_a) cudaEventDestroy(h->probe_a);
     if (h->probe_b) cudaEventDestroy(h->probe_b);
+    if (h->hs.cs_in) cudaStreamSynchronize(h->hs.cs_in);
+    if (h->hs.cs_out) cudaStreamSynchronize(h->hs.cs_out);
+    for (int b = 0; b < 2; ++b) {
+        if (h->hs.ev_in[b]) cudaEventDestroy(h->hs.ev_in[b]);
+        if (h->hs.ev_out[b]) cudaEventDestroy(h->hs.ev_out[b]);
+        if (h->hs.ev_done[b]) cudaEventDestroy(h->hs.ev_done[b]);
+    }
+    if (h->hs.buf) cudaFree(h->hs.buf);
+    if (h->hs.cs_in) cudaStreamDestroy(h->hs.cs_in);
+    if (h->hs.cs_out) cudaStreamDestroy(h->hs.cs_out);
     if (h->arena) cudaFree(h->arena);
     if (h->jobs_pinned) cudaFreeHost(h->jobs_pinned);
     if (h->jobs_ev) cudaEventDestroy(h->jobs_ev);
@@ -685,6 +695,100 @@ dis_status dis_compute_flow_batched(dis_handle* hd, const dis_pair* pairs, int n
     Plan plan;
     if ((st = build_plan(hd, v, *p, plan)) != DIS_OK) return st;
     return run_plan(hd, plan, *p, (cudaStream_t)stream);
+}
+
+dis_status dis_compute_flow_batched_host(dis_handle* hd, const dis_pair* pairs, int n, const dis_params* p,
+                                        void* stream)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    std::string e;
+    dis_status st = validate(p, e);
+    if (st != DIS_OK) return fail(hd, st, e);
+    if (p->channels != hd->C) return fail(hd, DIS_ERR_INVALID_ARG, "params.channels differs from the handle's");
+    if (!pairs || n < 1 || n > hd->max_batch) return fail(hd, DIS_ERR_INVALID_ARG, "pairs NULL or n outside [1, max_batch]");
+    const int C = p->channels;
+    // staging layout of one half: per pair I0, I1 (C planes of pitch x height) and the flow
+    std::vector<size_t> off_in(n), off_out(n);
+    size_t half = 0;
+    for (int i = 0; i < n; ++i) {
+        PairIn q{pairs[i].I0, pairs[i].I1, pairs[i].width, pairs[i].height, (long long)pairs[i].pitch,
+                 pairs[i].flow_out, nullptr, nullptr, nullptr, nullptr};
+        if ((st = check_pair(hd, q, i)) != DIS_OK) return st;
+        off_in[i] = half;
+        half = align_up(half + 2 * sizeof(float) * (size_t)C * q.pitch * q.h, kAlign);
+        off_out[i] = half;
+        half = align_up(half + sizeof(float) * 2 * (size_t)q.w * q.h, kAlign);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto& H = hd->hs;
+    cudaError_t ce = cudaSuccess;
+    if (!H.cs_in) {
+        ce = cudaStreamCreateWithFlags(&H.cs_in, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&H.cs_out, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
+            ce = cudaEventCreateWithFlags(&H.ev_in[b], cudaEventDisableTiming);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&H.ev_out[b], cudaEventDisableTiming);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&H.ev_done[b], cudaEventDisableTiming);
+        }
+        if (ce != cudaSuccess) return cuda_fail(hd, ce, "host staging setup");
+    }
+    if (half > H.half_bytes) {
+        // grow: every earlier call must be done with the old staging
+        if ((ce = cudaStreamSynchronize(H.cs_in)) != cudaSuccess || (ce = cudaStreamSynchronize(H.cs_out)) != cudaSuccess ||
+            (ce = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(hd, ce, "host staging wait");
+        if (H.buf) cudaFree(H.buf);
+        H.buf = nullptr;
+        H.half_bytes = 0;
+        H.used[0] = H.used[1] = false;
+        if ((ce = cudaMalloc(&H.buf, 2 * half)) != cudaSuccess) {
+            H.buf = nullptr;
+            return fail(hd, DIS_ERR_OUT_OF_MEMORY, "host staging allocation failed");
+        }
+        H.half_bytes = half;
+    }
+    const int b = H.next;
+    char* base = H.buf + (size_t)b * H.half_bytes;
+    // frames in, once the previous computation on this half has read its frames
+    if (H.used[b]) ce = cudaStreamWaitEvent(H.cs_in, H.ev_out[b], 0);
+    std::vector<dis_pair> dev(n);
+    for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+        const size_t frame = sizeof(float) * (size_t)C * pairs[i].pitch * pairs[i].height;
+        float* d0 = reinterpret_cast<float*>(base + off_in[i]);
+        float* d1 = reinterpret_cast<float*>(base + off_in[i] + frame);
+        ce = cudaMemcpyAsync(d0, pairs[i].I0, frame, cudaMemcpyHostToDevice, H.cs_in);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(d1, pairs[i].I1, frame, cudaMemcpyHostToDevice, H.cs_in);
+        dev[i] = pairs[i];
+        dev[i].I0 = d0;
+        dev[i].I1 = d1;
+        dev[i].flow_out = reinterpret_cast<float*>(base + off_out[i]);
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_in[b], H.cs_in);
+    // compute once the frames are in and the previous flows of this half are out
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, H.ev_in[b], 0);
+    if (ce == cudaSuccess && H.used[b]) ce = cudaStreamWaitEvent(s, H.ev_done[b], 0);
+    if (ce != cudaSuccess) return cuda_fail(hd, ce, "host frames copy");
+    if ((st = dis_compute_flow_batched(hd, dev.data(), n, p, stream)) != DIS_OK) return st;
+    // flows out once computed
+    ce = cudaEventRecord(H.ev_out[b], s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(H.cs_out, H.ev_out[b], 0);
+    for (int i = 0; i < n && ce == cudaSuccess; ++i)
+        ce = cudaMemcpyAsync(pairs[i].flow_out, dev[i].flow_out, sizeof(float) * 2 * (size_t)pairs[i].width * pairs[i].height,
+                             cudaMemcpyDeviceToHost, H.cs_out);
+    if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_done[b], H.cs_out);
+    if (ce != cudaSuccess) return cuda_fail(hd, ce, "host flows copy");
+    H.used[b] = true;
+    H.last = b;
+    H.next = b ^ 1;
+    return DIS_OK;
+}
+
+dis_status dis_host_flows_ready(dis_handle* hd, void* stream)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    if (hd->hs.last < 0) return DIS_OK;
+    cudaError_t ce = cudaStreamWaitEvent((cudaStream_t)stream, hd->hs.ev_done[hd->hs.last], 0);
+    return ce == cudaSuccess ? DIS_OK : cuda_fail(hd, ce, "dis_host_flows_ready");
 }
 
 dis_status dis_trace_batched(dis_handle* hd, const dis_pair* pairs, int n, const dis_params* p, void* stream,

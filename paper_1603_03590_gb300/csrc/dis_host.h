@@ -40,6 +40,17 @@ struct dis_handle {
     int probe_kind = -1, probe_level = 0;
     cudaEvent_t probe_a = nullptr, probe_b = nullptr;
     bool probe_armed = false;  // a call with the probe has been issued since it was set
+    // host-buffer batched calls: two halves of device staging (frames in, flows out), a stream
+    // for the copies in and one for the copies out, and per half the events "frames copied in",
+    // "flows computed", "flows copied out"
+    struct HostStage {
+        char* buf = nullptr;
+        size_t half_bytes = 0;
+        cudaStream_t cs_in = nullptr, cs_out = nullptr;
+        cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+        bool used[2] = {false, false};
+        int next = 0, last = -1;
+    } hs;
     std::string err = "no error";
 };
 

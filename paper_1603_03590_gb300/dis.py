@@ -72,6 +72,8 @@ _SIGS = {
     "dis_compute_flow": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp]),
     "dis_compute_flow_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dis_compute_flow_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp]),
+    "dis_compute_flow_batched_host": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp]),
+    "dis_host_flows_ready": (_i, [_vp, _vp]),
     "dis_autotune": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, ctypes.POINTER(_i)]),
     "dis_search_variants": (_i, [_i, ctypes.POINTER(_i), _i]),
     "dis_get_tuning": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -180,6 +182,16 @@ def make_pairs(items):
 
 def dis_compute_flow_batched(handle, pairs, n, params, stream=None):
     _check(_lib.dis_compute_flow_batched(handle, pairs, n, ctypes.byref(params), _stream(stream)), handle)
+
+
+def dis_compute_flow_batched_host(handle, pairs, n, params, stream=None):
+    """Batched call on host frames and flows (make_pairs of CPU tensors / arrays); asynchronous."""
+    _check(_lib.dis_compute_flow_batched_host(handle, pairs, n, ctypes.byref(params), _stream(stream)), handle)
+
+
+def dis_host_flows_ready(handle, stream=None):
+    """Order `stream` after the host copies of all earlier host-buffer calls."""
+    _check(_lib.dis_host_flows_ready(handle, _stream(stream)), handle)
 
 
 def dis_autotune(handle, pairs, n, params, stream=None):

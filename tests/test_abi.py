@@ -131,3 +131,9 @@ def test_trace_and_probe_argument_checks_need_no_gpu(dis):
     assert lib.dis_probe_ms(None, None) == dis.DIS_ERR_INVALID_ARG
     assert lib.dis_trace_batched(None, None, 1, None, None, None, 0, None) == dis.DIS_ERR_INVALID_ARG
     assert dis.LAUNCH_KINDS.index("search") == 3 and len(dis.LAUNCH_KINDS) == 7
+
+
+def test_host_buffer_call_argument_checks_need_no_gpu(dis):
+    lib = ctypes.CDLL(dis.LIB_PATH)
+    assert lib.dis_compute_flow_batched_host(None, None, 1, None, None) == dis.DIS_ERR_INVALID_ARG
+    assert lib.dis_host_flows_ready(None, None) == dis.DIS_ERR_INVALID_ARG

@@ -457,6 +457,44 @@ def test_batched_matches_plain_bit_exact(env):
             assert np.array_equal(host(f), plain[k]), (preset, sizes[k])
 
 
+def test_host_buffer_calls_match_device_calls(env):
+    """dis_compute_flow_batched_host on host frames (pinned and pageable) gives the flows of the
+    device call bit for bit, over consecutive calls that alternate the staging halves."""
+    torch, dis, dev = env
+    sizes = [(173, 91), (320, 240), (64, 48)]
+    sets = [[synth.layered_pair(90 + 10 * r + k, width=w, height=h, n_ellipses=4, max_disp=0.04 * w)
+             for k, (w, h) in enumerate(sizes)] for r in range(3)]
+    p = dis.dis_default_params("medium")
+    h = dis.dis_create(320, 240, len(sizes), 1)
+    try:
+        want = []
+        for pairs in sets:
+            flows = [torch.zeros((a.shape[0], a.shape[1], 2), device=dev) for a, _, _ in pairs]
+            items = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev), a.shape[1], a.shape[0], a.shape[1], f)
+                     for (a, b, _), f in zip(pairs, flows)]
+            dis.dis_compute_flow_batched(h, dis.make_pairs(items), len(items), p)
+            torch.cuda.synchronize()
+            want.append([host(f) for f in flows])
+        keep, outs = [], []
+        for r, pairs in enumerate(sets):
+            pin = r != 1  # the middle call uses pageable memory
+            fr = [(torch.from_numpy(a), torch.from_numpy(b)) for a, b, _ in pairs]
+            if pin:
+                fr = [(a.pin_memory(), b.pin_memory()) for a, b in fr]
+            out = [torch.full((a.shape[0], a.shape[1], 2), float("nan"), pin_memory=pin) for a, _, _ in pairs]
+            arr = dis.make_pairs([(a, b, a.shape[1], a.shape[0], a.shape[1], f) for (a, b), f in zip(fr, out)])
+            dis.dis_compute_flow_batched_host(h, arr, len(pairs), p)
+            keep.append((fr, arr))
+            outs.append(out)
+        dis.dis_host_flows_ready(h)
+        torch.cuda.synchronize()
+        for r in range(len(sets)):
+            for k in range(len(sizes)):
+                assert np.array_equal(outs[r][k].numpy().astype(np.float64), want[r][k]), (r, k)
+    finally:
+        dis.dis_destroy(h)
+
+
 def test_trace_and_probe(env):
     """dis_trace_batched lists the plan's launch groups with device times and gives the same
     flows as a normal call; the probe times one group inside the replayed graph."""
