@@ -42,8 +42,8 @@ def preset_params(dis, name):
 def launches_per_call(dis, p, width, height, lanes, batch, refine_form=1):
     """Kernels one batched call launches (mirrors the host plan: prep, pyramid, per level search
     planes (lane-per-patch search variant only) + search + densify (+ refinement: 3 setup, then
-    per outer pass one fused launch, or weights + 2 x inner per-sweep launches when inner > 5 or
-    the level has more than 4 Mi pixels over the batch, then apply), final up-scaling)."""
+    per outer pass one fused launch, two when the level has more than 128 Ki pixels over the batch,
+    or weights + 2 x inner per-sweep launches, then apply), final up-scaling)."""
     ss, sf, _ = dis.dis_levels(width, height, p)
     w, h = width, height
     dims = [(w, h)]
@@ -56,8 +56,9 @@ def launches_per_call(dis, p, width, height, lanes, batch, refine_form=1):
         if p.refine:
             outer = s + 1 if p.var_outer < 0 else p.var_outer
             npx = batch * dims[s][0] * dims[s][1]
-            fused = 0 < p.var_inner <= 5 and refine_form != 0 and (refine_form == 2 or npx <= (4 << 20))
-            n += 3 + (outer if fused else outer * (1 + 2 * p.var_inner)) + 1
+            fused = 0 < p.var_inner <= 5 and refine_form != 0
+            split = refine_form == 3 or (refine_form == 1 and npx > (1 << 17))
+            n += 3 + ((2 * outer if split else outer) if fused else outer * (1 + 2 * p.var_inner)) + 1
     return n + (1 if sf > 0 else 0)
 
 

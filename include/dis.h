@@ -181,13 +181,13 @@ typedef struct dis_launch_record {
 dis_status dis_trace_batched(dis_handle* h, const dis_pair* pairs, int n, const dis_params* p, void* stream,
                              dis_launch_record* out, int cap, int* count);
 
-/* Refinement launch form (not in the paper) for handle h.  fused = 1 (the default) runs each
- * lagged-weight pass with its SOR sweeps in one kernel launch (shared-memory tiles with a halo
- * as wide as the half-sweeps) where that measures faster on GB300: up to 5 sweeps per pass and
- * up to 4 Mi pixels per launch (all pairs of a level together); other levels use per-sweep
- * launches.  fused = 2 fuses every level with up to 5 sweeps per pass; fused = 0 runs one launch
- * per half-sweep everywhere.  All forms give the same result bit for bit.  Other values:
- * DIS_ERR_INVALID_ARG. */
+/* Refinement launch form (not in the paper) for handle h.  A fused launch runs lagged-weight
+ * passes with their SOR sweeps on shared-memory tiles whose halo is as wide as the half-sweeps
+ * it runs (up to 5 sweeps per pass; more always use per-sweep launches).  fused = 1 (the
+ * default) runs each pass in one fused launch up to 128 Ki pixels per launch (all pairs of a
+ * level together) and in two fused launches of half the sweeps (half the halo) above, which
+ * measures fastest on GB300; 2 always uses one launch per pass, 3 always two, 0 one launch per
+ * half-sweep.  All forms give the same result bit for bit.  Other values: DIS_ERR_INVALID_ARG. */
 dis_status dis_set_refine_fusion(dis_handle* h, int fused);
 
 /* Probe (not in the paper): from now on every call of handle h records two events of its own
@@ -203,7 +203,7 @@ dis_status dis_probe_ms(dis_handle* h, float* ms);
 /* Autotuner (not in the paper): time the inverse-search variants the library offers for this
  * workload on the caller's pairs (the batched call, 4 runs per variant, synchronising
  * `stream`) and keep the fastest in the handle for later calls with the same patch size; then,
- * when p->refine is set, time the refinement launch forms of dis_set_refine_fusion (1, 0, 2)
+ * when p->refine is set, time the refinement launch forms of dis_set_refine_fusion (1, 0, 2, 3)
  * with that search and keep the fastest.  The runs write the pairs' flow_out.  *chosen_lanes
  * (nullable) receives the chosen search variant code (dis_get_tuning reports both choices):
  *   4, 8, 16, 32   grouped: that many lanes share one patch (every group runs its own updates

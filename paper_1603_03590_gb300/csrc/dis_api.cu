@@ -833,7 +833,7 @@ dis_status dis_trace_batched(dis_handle* hd, const dis_pair* pairs, int n, const
 dis_status dis_set_refine_fusion(dis_handle* hd, int fused)
 {
     if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
-    if (fused < 0 || fused > 2) return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_refine_fusion: mode must be 0, 1 or 2");
+    if (fused < 0 || fused > 3) return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_refine_fusion: mode must be 0 to 3");
     hd->refine_fused = fused;
     return DIS_OK;
 }
@@ -1085,8 +1085,8 @@ extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n,
     if (st == DIS_OK && p->refine) {
         hd->search_lanes[ps] = best;
         best_ms = 1e30f;
-        const int modes[3] = {1, 0, 2};
-        for (int k = 0; k < 3 && st == DIS_OK; ++k) {
+        const int modes[4] = {1, 0, 2, 3};
+        for (int k = 0; k < 4 && st == DIS_OK; ++k) {
             hd->refine_fused = modes[k];
             float tot = 0.0f;
             st = time_calls(tot);

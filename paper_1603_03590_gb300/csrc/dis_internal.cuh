@@ -142,15 +142,16 @@ cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, in
 struct RefineArgs {
     int outer, inner;
     float delta, gamma, alpha, omega;
-    int fused = 1;      // 0: per-sweep launches; 1: fused passes up to kRefineFusedMaxPixels
-                        // per launch; 2: fused passes whenever inner allows
+    int fused = 1;      // 0: per-sweep launches; 1: each pass in one fused launch up to
+                        // kRefineFusedMaxPixels per launch, in two above; 2: one fused launch,
+                        // 3: two fused launches per pass, whenever inner allows
     int C = 1;          // channels of every job of the launch
 };
 // Square tiles of the fused outer-iteration kernel; at most kRefineMaxFusedInner inner sweeps
 // (2 half-sweeps each) run in one launch, the halo being as wide as the half-sweeps.
 constexpr int kRefineTile = 32;
 constexpr int kRefineMaxFusedInner = 5;
-constexpr long long kRefineFusedMaxPixels = 4LL << 20;  // larger launches use per-sweep kernels
+constexpr long long kRefineFusedMaxPixels = 1LL << 17;  // larger launches split each pass in two
 inline long long refine_tiles(int w, int h)
 {
     return (long long)((w + kRefineTile - 1) / kRefineTile) * ((h + kRefineTile - 1) / kRefineTile);

@@ -278,7 +278,11 @@ __device__ __forceinline__ int csplit(int lx, int ly, int S, int p)
     return ((lx + ly + p) & 1) * (S * S / 2) + ly * (S / 2) + (lx >> 1);
 }
 
-template <int K>
+// PHASE 0: the whole pass (weights, K half-sweeps).  PHASE 1 / 2: the first / second half of
+// a pass split in two launches of K half-sweeps each, which halves the halo: the first computes
+// the weights and also stores the tile's systems (rs_sys planes) for the second, which loads
+// them with its halo instead of recomputing them from an increment it no longer has.
+template <int K, int PHASE>
 __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __grid_constant__ Jobs<LevelJob> js,
                                                                         long long total_tiles, int src, int dst,
                                                                         float delta, float gamma, float alpha,
@@ -324,11 +328,20 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
         // colour-split region a pixel (lx, ly) of colour c sits at c * half + ly * S/2 + lx/2;
         // its left / right neighbours (the other colour) at the same position minus 1 when lx
         // is even, plus 1 when lx is odd, and its upper / lower ones one half row away.
+        float* gsys = J.rs + (long long)rs_sys(C, 0) * pl;
         for (int t = threadIdx.x; t < E0; t += kOuterThreads) {
             const int ly = t / S0, lx = t - ly * S0;
             const int x = x1 + 1 + lx, y = y1 + 1 + ly;
             if (x < 0 || x >= w || y < 0 || y >= h) continue;
             const int c = (x + y) & 1;
+            const int c0 = c * HE0 + ly * HS0 + (lx >> 1);
+            const long long o = (long long)y * pitch + x;
+            if (PHASE == 2) {
+                r0[c0] = make_float2(gsys[o], gsys[pl + o]);
+                r0[E0 + c0] = make_float2(gsys[2 * pl + o], gsys[3 * pl + o]);
+                r0[2 * E0 + c0] = make_float2(gsys[4 * pl + o], gsys[5 * pl + o]);
+                continue;
+            }
             const int pos = (ly + 1) * HS1 + ((lx + 1) >> 1), oth = (1 - c) * HE1 + pos;
             const int odd = (lx + 1) & 1;
             const float4 me = r1[c * HE1 + pos];
@@ -337,17 +350,25 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
             const float4 R = x < w - 1 ? r1[oth + odd] : me;
             const float4 Up = y > 0 ? r1[oth - HS1] : me;
             const float4 Dn = y < h - 1 ? r1[oth + HS1] : me;
-            const long long o = (long long)y * pitch + x;
             float a11, a12, a22, b1, b2;
             refine_data_system(rs, C, pl, o, me.z, me.w, delta, gamma, a11, a12, a22, b1, b2);
             const float ux = refine_cdiff(R.x, R.z, L.x, L.z);
             const float vx = refine_cdiff(R.y, R.w, L.y, L.w);
             const float uy = refine_cdiff(Dn.x, Dn.z, Up.x, Up.z);
             const float vy = refine_cdiff(Dn.y, Dn.w, Up.y, Up.w);
-            const int c0 = c * HE0 + ly * HS0 + (lx >> 1);
+            const float psS = refine_smooth_weight(ux, uy, vx, vy, alpha);
             r0[c0] = make_float2(a11, a12);
             r0[E0 + c0] = make_float2(a22, b1);
-            r0[2 * E0 + c0] = make_float2(b2, refine_smooth_weight(ux, uy, vx, vy, alpha));
+            r0[2 * E0 + c0] = make_float2(b2, psS);
+            if (PHASE == 1 && lx >= H && lx < H + T && ly >= H && ly < H + T) {
+                // the tile's own systems, for the second half of the pass
+                gsys[o] = a11;
+                gsys[pl + o] = a12;
+                gsys[2 * pl + o] = a22;
+                gsys[3 * pl + o] = b1;
+                gsys[4 * pl + o] = b2;
+                gsys[5 * pl + o] = psS;
+            }
         }
         __syncthreads();
         // K half-sweeps, red ((x + y) even) first.  Pair pr = (ly, k) covers swept pixels
@@ -357,7 +378,7 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
         auto sweep = [&](auto inner_tag) {
             constexpr bool INNER = decltype(inner_tag)::value;  // no image border in R1
             for (int j = 0; j < K; ++j) {
-                const int colour = j & 1;
+                const int colour = (j + (PHASE == 2 ? K : 0)) & 1;  // the second half continues
                 for (int pr = threadIdx.x; pr < npairs; pr += kOuterThreads) {
                     const int ly = pr / pairs_row, k = pr - ly * pairs_row;
                     const int y = y2 + ly;
@@ -424,30 +445,48 @@ __global__ void __launch_bounds__(256) refine_apply_kernel(const __grid_constant
     DIS_PIX_END
 }
 
-// a.outer fused passes with K half-sweeps each; on return `src` names the planes holding the
-// final increment.
-template <int K>
-static cudaError_t launch_outer(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int& src, int& dst,
+template <int K, int PHASE>
+static cudaError_t outer_launch(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int src, int dst,
                                 const LaunchCfg& lc, cudaStream_t s)
 {
     constexpr int S1 = kRefineTile + 2 * (K + 1), S0 = kRefineTile + 2 * K;
     constexpr size_t smem = sizeof(float4) * (size_t)S1 * S1 + sizeof(float2) * 3 * (size_t)S0 * S0;
     static int occ = 0;
     if (occ == 0) {
-        cudaError_t e = cudaFuncSetAttribute(refine_outer_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(refine_outer_kernel<K, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, refine_outer_kernel<K>, kOuterThreads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, refine_outer_kernel<K, PHASE>, kOuterThreads, smem) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
     }
     const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * occ);
-    for (int ot = 0; ot < a.outer; ++ot) {
-        refine_outer_kernel<K><<<gt, kOuterThreads, smem, s>>>(js, total_tiles, src, dst, a.delta, a.gamma, a.alpha,
-                                                                a.omega);
-        std::swap(src, dst);
-    }
+    refine_outer_kernel<K, PHASE><<<gt, kOuterThreads, smem, s>>>(js, total_tiles, src, dst, a.delta, a.gamma, a.alpha,
+                                                                   a.omega);
     return cudaGetLastError();
+}
+
+// a.outer fused passes of 2 * a.inner half-sweeps, each in one launch (split = false) or in two
+// (split = true); on return `src` names the planes holding the final increment.
+template <int KI>
+static cudaError_t launch_outer(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, bool split,
+                                int& src, int& dst, const LaunchCfg& lc, cudaStream_t s)
+{
+    for (int ot = 0; ot < a.outer; ++ot) {
+        cudaError_t e;
+        if (!split) {
+            e = outer_launch<2 * KI, 0>(js, total_tiles, a, src, dst, lc, s);
+            std::swap(src, dst);
+        } else {
+            e = outer_launch<KI, 1>(js, total_tiles, a, src, dst, lc, s);
+            std::swap(src, dst);
+            if (e == cudaSuccess) e = outer_launch<KI, 2>(js, total_tiles, a, src, dst, lc, s);
+            std::swap(src, dst);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, long long total_tiles,
@@ -463,11 +502,11 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
     // the increment starts in rs_du (zeroed by the warp kernel); the fused passes alternate it
     // with the first two intermediate planes, which are free once deriv2 has run
     const int du_plane = rs_du(a.C, 0), mid_plane = rs_mid(a.C, 0, 0);
-    // The fused form recomputes the halo (about 2.4x the swept pixels at 10 half-sweeps), so it
-    // wins where launches dominate and loses where the per-sweep kernels stream at full
-    // bandwidth: measured on GB300 the two break even near 4 M pixels per launch.
-    const bool fused = a.fused != 0 && a.inner > 0 && a.inner <= kRefineMaxFusedInner && total_tiles > 0 &&
-                       (a.fused == 2 || total_pix <= kRefineFusedMaxPixels);
+    // The fused form recomputes the halo: about 2.4x the swept pixels at 10 half-sweeps in one
+    // launch, 1.6x when the pass is split in two launches of 5 (which also stores and reloads
+    // the systems).  Measured on GB300 the single launch wins up to about 128 K pixels per
+    // launch, the split pass above (and both beat the per-sweep kernels); mode 2 / 3 force one.
+    const bool fused = a.fused != 0 && a.inner > 0 && a.inner <= kRefineMaxFusedInner && total_tiles > 0;
     if (!fused) {
         for (int ot = 0; ot < a.outer; ++ot) {
             refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);
@@ -479,15 +518,15 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
         refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, du_plane);
         return cudaGetLastError();
     }
-    const int K = 2 * a.inner;
+    const bool split = a.fused == 3 || (a.fused == 1 && total_pix > kRefineFusedMaxPixels);
     int src = du_plane, dst = mid_plane;
     cudaError_t e = cudaSuccess;
-    switch (K) {
-        case 2: e = launch_outer<2>(js, total_tiles, a, src, dst, lc, s); break;
-        case 4: e = launch_outer<4>(js, total_tiles, a, src, dst, lc, s); break;
-        case 6: e = launch_outer<6>(js, total_tiles, a, src, dst, lc, s); break;
-        case 8: e = launch_outer<8>(js, total_tiles, a, src, dst, lc, s); break;
-        default: e = launch_outer<10>(js, total_tiles, a, src, dst, lc, s); break;
+    switch (a.inner) {
+        case 1: e = launch_outer<1>(js, total_tiles, a, split, src, dst, lc, s); break;
+        case 2: e = launch_outer<2>(js, total_tiles, a, split, src, dst, lc, s); break;
+        case 3: e = launch_outer<3>(js, total_tiles, a, split, src, dst, lc, s); break;
+        case 4: e = launch_outer<4>(js, total_tiles, a, split, src, dst, lc, s); break;
+        default: e = launch_outer<5>(js, total_tiles, a, split, src, dst, lc, s); break;
     }
     if (e != cudaSuccess) return e;
     refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, src);

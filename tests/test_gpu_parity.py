@@ -246,12 +246,17 @@ def test_refine_stage(env, case):
     h = dis.dis_create(pitch, Hl, 1, C)
     try:
         dis.dis_refine_level(h, a, b, Wl, Hl, pitch, C, U, outer, inner)
-        dis.dis_set_refine_fusion(h, False)
-        dis.dis_refine_level(h, a, b, Wl, Hl, pitch, C, U2, outer, inner)
+        others = []
+        for mode in (0, 3):
+            dis.dis_set_refine_fusion(h, mode)
+            Uk = U2.clone()
+            dis.dis_refine_level(h, a, b, Wl, Hl, pitch, C, Uk, outer, inner)
+            others.append(Uk)
         torch.cuda.synchronize()
     finally:
         dis.dis_destroy(h)
-    assert torch.equal(U, U2), float((U - U2).abs().max())
+    for Uk in others:
+        assert torch.equal(U, Uk), float((U - Uk).abs().max())
     Uo = oracle.refine_level(P0.astype(np.float64), P1.astype(np.float64), U0.astype(np.float64), outer, inner)
     e = np.abs(host(U) - Uo).max()
     print("refine %s: max |dU| %.2e (update magnitude %.2e)" % (case, e, np.abs(Uo - U0).max()))
@@ -380,7 +385,7 @@ def test_e2e_fused_refinement_equals_per_sweep_bit_exact(env, preset, C):
     try:
         dev_pairs = [(to_dev(torch, a, dev, a.shape[-1] + 5), to_dev(torch, b, dev, b.shape[-1] + 5)) for a, b, _ in pairs]
         out = []
-        for fused in (1, 0, 2):
+        for fused in (1, 0, 2, 3):
             dis.dis_set_refine_fusion(h, fused)
             flows = [torch.full((a.shape[-2], a.shape[-1], 2), float("nan"), device=dev) for a, _, _ in pairs]
             items = [(da, db, a.shape[-1], a.shape[-2], da.shape[-1], f)
@@ -389,12 +394,12 @@ def test_e2e_fused_refinement_equals_per_sweep_bit_exact(env, preset, C):
             torch.cuda.synchronize()
             out.append([host(f) for f in flows])
         with pytest.raises(dis.DisError):
-            dis.dis_set_refine_fusion(h, 3)
+            dis.dis_set_refine_fusion(h, 4)
     finally:
         dis.dis_destroy(h)
     for k in range(len(pairs)):
         assert np.isfinite(out[0][k]).all()
-        assert np.array_equal(out[0][k], out[1][k]) and np.array_equal(out[0][k], out[2][k]), (preset, sizes[k])
+        assert all(np.array_equal(out[0][k], o[k]) for o in out[1:]), (preset, sizes[k])
 
 
 def test_e2e_rgb(env):
@@ -604,7 +609,7 @@ def test_every_search_variant_and_the_autotuner_keep_parity(env, preset):
         lanes = dis.dis_autotune(h, arr, len(pairs), p)
         assert lanes in variants
         tv, tr = dis.dis_get_tuning(h, p.patch_size)
-        assert tv == lanes and tr in ((0, 1, 2) if p.refine else (1,))
+        assert tv == lanes and tr in ((0, 1, 2, 3) if p.refine else (1,))
         print("%s: autotuned search variant %d, refinement launch form %d" % (preset, tv, tr))
         dis.dis_compute_flow_batched(h, arr, len(pairs), p)
         torch.cuda.synchronize()

@@ -133,12 +133,15 @@ def test_rgb_4k_batch_of_4(env):
     h = dis.dis_create(W, H, 1, C)
     try:
         dis.dis_refine_level(h, a, b, W, H, W, C, U, 1, 5)
-        dis.dis_set_refine_fusion(h, 2)  # the fused form on all 8.3 M pixels too
+        dis.dis_set_refine_fusion(h, 2)  # one fused launch on all 8.3 M pixels too
         dis.dis_refine_level(h, a, b, W, H, W, C, U2, 1, 5)
+        U3 = torch.from_numpy(U0).to(dev)
+        dis.dis_set_refine_fusion(h, 0)  # and one launch per half-sweep
+        dis.dis_refine_level(h, a, b, W, H, W, C, U3, 1, 5)
         torch.cuda.synchronize()
     finally:
         dis.dis_destroy(h)
-    assert torch.equal(U, U2)
+    assert torch.equal(U, U2) and torch.equal(U, U3)
     Ug = host(U)
     M = 16
     for (y0, x0, hh, ww) in [(0, 0, 96, 128), (1000, 1800, 96, 96), (H - 80, W - 112, 80, 112)]:
