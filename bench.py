@@ -57,8 +57,8 @@ def launches_per_call(dis, p, width, height, lanes, batch, refine_form=1):
             outer = s + 1 if p.var_outer < 0 else p.var_outer
             npx = batch * dims[s][0] * dims[s][1]
             fused = 0 < p.var_inner <= 5 and refine_form != 0
-            split = refine_form == 3 or (refine_form == 1 and npx > (1 << 17))
-            n += 3 + ((2 * outer if split else outer) if fused else outer * (1 + 2 * p.var_inner)) + 1
+            chunks = 2 if refine_form == 3 or (refine_form == 1 and npx > (1 << 17)) else 1
+            n += 3 + (outer * chunks if fused else outer * (1 + 2 * p.var_inner)) + 1
     return n + (1 if sf > 0 else 0)
 
 

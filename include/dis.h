@@ -187,7 +187,8 @@ dis_status dis_trace_batched(dis_handle* h, const dis_pair* pairs, int n, const 
  * default) runs each pass in one fused launch up to 128 Ki pixels per launch (all pairs of a
  * level together) and in two fused launches of half the sweeps (half the halo) above, which
  * measures fastest on GB300; 2 always uses one launch per pass, 3 always two, 0 one launch per
- * half-sweep.  All forms give the same result bit for bit.  Other values: DIS_ERR_INVALID_ARG. */
+ * half-sweep (no halo, no shared memory).  All forms give the same result bit for bit.  Other
+ * values: DIS_ERR_INVALID_ARG. */
 dis_status dis_set_refine_fusion(dis_handle* h, int fused);
 
 /* Probe (not in the paper): from now on every call of handle h records two events of its own

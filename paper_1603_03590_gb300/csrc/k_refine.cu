@@ -278,15 +278,16 @@ __device__ __forceinline__ int csplit(int lx, int ly, int S, int p)
     return ((lx + ly + p) & 1) * (S * S / 2) + ly * (S / 2) + (lx >> 1);
 }
 
-// PHASE 0: the whole pass (weights, K half-sweeps).  PHASE 1 / 2: the first / second half of
-// a pass split in two launches of K half-sweeps each, which halves the halo: the first computes
-// the weights and also stores the tile's systems (rs_sys planes) for the second, which loads
-// them with its halo instead of recomputing them from an increment it no longer has.
+// PHASE 0: the whole pass (weights, K half-sweeps).  PHASE 1 / 2: the first / a later chunk of
+// a pass split into launches of K half-sweeps each, which narrows the halo to K: the first
+// computes the weights and also stores the tile's systems (rs_sys planes) for the later ones,
+// which load them with their halo instead of recomputing them from an increment they no longer
+// have.  j0: index of the chunk's first half-sweep in the pass (its colour parity).
 template <int K, int PHASE>
 __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __grid_constant__ Jobs<LevelJob> js,
                                                                         long long total_tiles, int src, int dst,
-                                                                        float delta, float gamma, float alpha,
-                                                                        float omega)
+                                                                        int j0, float delta, float gamma,
+                                                                        float alpha, float omega)
 {
     extern __shared__ float4 sm4[];
     constexpr int T = kRefineTile;
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
         auto sweep = [&](auto inner_tag) {
             constexpr bool INNER = decltype(inner_tag)::value;  // no image border in R1
             for (int j = 0; j < K; ++j) {
-                const int colour = (j + (PHASE == 2 ? K : 0)) & 1;  // the second half continues
+                const int colour = (j + j0) & 1;  // later chunks continue the pass's alternation
                 for (int pr = threadIdx.x; pr < npairs; pr += kOuterThreads) {
                     const int ly = pr / pairs_row, k = pr - ly * pairs_row;
                     const int y = y2 + ly;
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(256) refine_apply_kernel(const __grid_constant
 
 template <int K, int PHASE>
 static cudaError_t outer_launch(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int src, int dst,
-                                const LaunchCfg& lc, cudaStream_t s)
+                                int j0, const LaunchCfg& lc, cudaStream_t s)
 {
     constexpr int S1 = kRefineTile + 2 * (K + 1), S0 = kRefineTile + 2 * K;
     constexpr size_t smem = sizeof(float4) * (size_t)S1 * S1 + sizeof(float2) * 3 * (size_t)S0 * S0;
@@ -462,27 +463,29 @@ static cudaError_t outer_launch(const Jobs<LevelJob>& js, long long total_tiles,
             occ = 1;
     }
     const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * occ);
-    refine_outer_kernel<K, PHASE><<<gt, kOuterThreads, smem, s>>>(js, total_tiles, src, dst, a.delta, a.gamma, a.alpha,
-                                                                   a.omega);
+    refine_outer_kernel<K, PHASE><<<gt, kOuterThreads, smem, s>>>(js, total_tiles, src, dst, j0, a.delta, a.gamma,
+                                                                   a.alpha, a.omega);
     return cudaGetLastError();
 }
 
-// a.outer fused passes of 2 * a.inner half-sweeps, each in one launch (split = false) or in two
-// (split = true); on return `src` names the planes holding the final increment.
-template <int KI>
-static cudaError_t launch_outer(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, bool split,
-                                int& src, int& dst, const LaunchCfg& lc, cudaStream_t s)
+// a.outer fused passes of KT half-sweeps, each in one launch (KC == KT) or in KT / KC launches
+// of KC; on return `src` names the planes holding the final increment.
+template <int KT, int KC>
+static cudaError_t launch_outer(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int& src,
+                                int& dst, const LaunchCfg& lc, cudaStream_t s)
 {
+    static_assert(KT % KC == 0, "chunks divide the pass");
     for (int ot = 0; ot < a.outer; ++ot) {
-        cudaError_t e;
-        if (!split) {
-            e = outer_launch<2 * KI, 0>(js, total_tiles, a, src, dst, lc, s);
+        cudaError_t e = cudaSuccess;
+        if (KC == KT) {
+            e = outer_launch<KT, 0>(js, total_tiles, a, src, dst, 0, lc, s);
             std::swap(src, dst);
         } else {
-            e = outer_launch<KI, 1>(js, total_tiles, a, src, dst, lc, s);
-            std::swap(src, dst);
-            if (e == cudaSuccess) e = outer_launch<KI, 2>(js, total_tiles, a, src, dst, lc, s);
-            std::swap(src, dst);
+            for (int j0 = 0; j0 < KT && e == cudaSuccess; j0 += KC) {
+                e = j0 == 0 ? outer_launch<KC, 1>(js, total_tiles, a, src, dst, j0, lc, s)
+                            : outer_launch<KC, 2>(js, total_tiles, a, src, dst, j0, lc, s);
+                std::swap(src, dst);
+            }
         }
         if (e != cudaSuccess) return e;
     }
@@ -518,15 +521,23 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
         refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, du_plane);
         return cudaGetLastError();
     }
-    const bool split = a.fused == 3 || (a.fused == 1 && total_pix > kRefineFusedMaxPixels);
+    // chunks per pass: 1 (mode 2, or small launches in mode 1) or 2 (mode 3, or large launches in
+    // mode 1).  (Chunks of one full sweep, halo 2, measured slower than both: each reloads the
+    // systems.)
+    const int chunks = (a.fused == 3 || (a.fused == 1 && total_pix > kRefineFusedMaxPixels)) ? 2 : 1;
     int src = du_plane, dst = mid_plane;
     cudaError_t e = cudaSuccess;
-    switch (a.inner) {
-        case 1: e = launch_outer<1>(js, total_tiles, a, split, src, dst, lc, s); break;
-        case 2: e = launch_outer<2>(js, total_tiles, a, split, src, dst, lc, s); break;
-        case 3: e = launch_outer<3>(js, total_tiles, a, split, src, dst, lc, s); break;
-        case 4: e = launch_outer<4>(js, total_tiles, a, split, src, dst, lc, s); break;
-        default: e = launch_outer<5>(js, total_tiles, a, split, src, dst, lc, s); break;
+    switch (a.inner * 10 + chunks) {
+        case 11: e = launch_outer<2, 2>(js, total_tiles, a, src, dst, lc, s); break;
+        case 12: e = launch_outer<2, 1>(js, total_tiles, a, src, dst, lc, s); break;
+        case 21: e = launch_outer<4, 4>(js, total_tiles, a, src, dst, lc, s); break;
+        case 22: e = launch_outer<4, 2>(js, total_tiles, a, src, dst, lc, s); break;
+        case 31: e = launch_outer<6, 6>(js, total_tiles, a, src, dst, lc, s); break;
+        case 32: e = launch_outer<6, 3>(js, total_tiles, a, src, dst, lc, s); break;
+        case 41: e = launch_outer<8, 8>(js, total_tiles, a, src, dst, lc, s); break;
+        case 42: e = launch_outer<8, 4>(js, total_tiles, a, src, dst, lc, s); break;
+        case 51: e = launch_outer<10, 10>(js, total_tiles, a, src, dst, lc, s); break;
+        default: e = launch_outer<10, 5>(js, total_tiles, a, src, dst, lc, s); break;
     }
     if (e != cudaSuccess) return e;
     refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, src);

@@ -219,8 +219,8 @@ def dis_trace_batched(handle, pairs, n, params, stream=None, cap=256):
 
 
 def dis_set_refine_fusion(handle, mode):
-    """Refinement launch form: 0 per-sweep launches, 1 fused as measured fastest (default), 2 one
-    fused launch per pass, 3 two fused launches per pass (True / False map to 1 / 0)."""
+    """Refinement launch form: 0 per-half-sweep launches, 1 fused as measured fastest (default),
+    2 one fused launch per pass, 3 two per pass (True / False map to 1 / 0)."""
     _check(_lib.dis_set_refine_fusion(handle, int(mode)), handle)
 
 
