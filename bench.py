@@ -336,7 +336,12 @@ def main():
                                "search variant %d), timed inside the timed steps" % (sf, B, npatch, p.grad_iters, lanes),
                      "ms_per_launch": k_ms, "launches_timed": len(probe),
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak,
+                     # DRAM bytes of the same launch at 4 pairs (ncu dram__bytes_read.sum +
+                     # dram__bytes_write.sum, 17.82 MB: the level images and the coarser flow,
+                     # each read once), scaled by the pairs a launch processes
+                     "traffic": 17.82e6 * B / 4 if args.preset == "dense" and lanes == 16 else None,
+                     "traffic_source": "ncu capture of the 4-pair launch, scaled by pairs (profiles/)",
                      "algorithmic_flops_per_launch": flops * B,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max},
         "stages_ms_per_step": {k: round(v, 4) for k, v in stages.items()},
