@@ -570,8 +570,10 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
 {
     if (!out) return fail(nullptr, DIS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    // the kernels index a pair's pixels (and up to 8 planes of a level-1 image) with 32-bit
+    // integers: at most 2^30 pixels per frame
     if (max_w < 1 || max_h < 1 || max_batch < 1 || (channels != 1 && channels != 3) || max_w > (1 << 16) ||
-        max_h > (1 << 16) || max_batch > 4096)
+        max_h > (1 << 16) || max_batch > 4096 || (long long)max_w * max_h > (1LL << 30))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "invalid handle size");
     dis_handle* h = new dis_handle();
     h->max_w = max_w;
@@ -878,7 +880,7 @@ static dis::LaunchCfg stage_lc()
 
 dis_status dis_pyr_down(const float* in, int w, int h, int64_t in_pitch, float* out, int64_t out_pitch, void* stream)
 {
-    if (!in || !out || w < 1 || h < 1 || in_pitch < w || out_pitch < (w + 1) / 2)
+    if (!in || !out || w < 1 || h < 1 || in_pitch < w || out_pitch < (w + 1) / 2 || (long long)w * h > (1LL << 30))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_pyr_down: bad pointer, size or pitch");
     PyrJob J;
     std::memset(&J, 0, sizeof(J));
@@ -907,6 +909,7 @@ dis_status dis_sobel(const float* in, int w, int h, int64_t pitch, float* gx, fl
 static bool level_args_ok(int w, int h, int64_t pitch, int ps, int stride, const float* Uc, int wc, int hc, float cscale)
 {
     if (w < 1 || h < 1 || pitch < w || ps < 2 || ps > kMaxPatch || stride < 1 || w < ps || h < ps) return false;
+    if ((long long)w * h > (1LL << 30)) return false;  // 32-bit pixel indices
     if (Uc && (wc < 1 || hc < 1 || !(cscale > 0.0f))) return false;
     return true;
 }
@@ -1010,7 +1013,8 @@ dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, in
 
 dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, float* Uout, int wo, int ho, void* stream)
 {
-    if (!Uin || !Uout || wi < 1 || hi < 1 || wo < 1 || ho < 1 || !(factor > 0.0f) || !finite(factor))
+    if (!Uin || !Uout || wi < 1 || hi < 1 || wo < 1 || ho < 1 || !(factor > 0.0f) || !finite(factor) ||
+        (long long)wo * ho > (1LL << 30) || (long long)wi * hi > (1LL << 30))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_upsample_flow: bad pointer, size or factor");
     UpJob J;
     std::memset(&J, 0, sizeof(J));

@@ -8,27 +8,31 @@
 namespace dis {
 
 // Range [lo, hi] of regular grid indices (those below n - 1, at i * stride) whose patch
-// covers coordinate q, and whether the last patch (at L - ps) covers it.
-__device__ __forceinline__ void cover_range(int q, int L, int ps, int stride, int n, int& lo, int& hi, bool& last)
+// covers coordinate q, and whether the last patch (at L - ps) covers it.  SC: compile-time
+// stride (0: the runtime `stride`), so that the divisions become multiplications.
+template <int SC>
+__device__ __forceinline__ void cover_range(int q, int L, int ps, int stride_rt, int n, int& lo, int& hi, bool& last)
 {
+    const int stride = SC ? SC : stride_rt;
     const int t = q - ps + 1;
     lo = t <= 0 ? 0 : (t + stride - 1) / stride;
     hi = min(n - 2, q / stride);
     last = q >= L - ps;
 }
 
+template <int SC>
 __global__ void __launch_bounds__(256) densify_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
                                                       int ps, int stride)
 {
     for (long long g = gtid(); g < total; g += gstride()) {
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::pix_base));
-        const long long k = g - J.pix_base;
+        const int k = (int)(g - J.pix_base);  // < w * h < 2^31
         const int w = J.w, h = J.h, pitch = J.pitch, nx = J.nx, ny = J.ny;
-        const int y = (int)(k / w), x = (int)(k - (long long)y * w);
+        const int y = k / w, x = k - y * w;
         int ilo, ihi, jlo, jhi;
         bool ilast, jlast;
-        cover_range(x, w, ps, stride, nx, ilo, ihi, ilast);
-        cover_range(y, h, ps, stride, ny, jlo, jhi, jlast);
+        cover_range<SC>(x, w, ps, stride, nx, ilo, ihi, ilast);
+        cover_range<SC>(y, h, ps, stride, ny, jlo, jhi, jlast);
         const float i0 = __ldg(J.S0 + (long long)y * pitch + x);
         float nu = 0.0f, nv = 0.0f, Z = 0.0f;
         const int jend = jhi + (jlast ? 1 : 0), iend = ihi + (ilast ? 1 : 0);
@@ -61,7 +65,13 @@ cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, in
     long long b = (total + 255) / 256;
     const long long cap = (long long)lc.sm_count * lc.max_blocks_256;
     if (b > cap) b = cap;
-    densify_kernel<<<(int)b, 256, 0, s>>>(js, total, ps, stride);
+    switch (stride) {  // the strides of the presets
+        case 3: densify_kernel<3><<<(int)b, 256, 0, s>>>(js, total, ps, stride); break;
+        case 4: densify_kernel<4><<<(int)b, 256, 0, s>>>(js, total, ps, stride); break;
+        case 5: densify_kernel<5><<<(int)b, 256, 0, s>>>(js, total, ps, stride); break;
+        case 6: densify_kernel<6><<<(int)b, 256, 0, s>>>(js, total, ps, stride); break;
+        default: densify_kernel<0><<<(int)b, 256, 0, s>>>(js, total, ps, stride); break;
+    }
     return cudaGetLastError();
 }
 

@@ -11,8 +11,8 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ Jobs<
 {
     for (long long g = gtid(); g < total; g += gstride()) {
         const PrepJob& J = job_ref(js, find_job(js, g, &PrepJob::base));
-        const long long k = g - J.base;
-        const int y = (int)(k / J.w), x = (int)(k - (long long)y * J.w);
+        const int k = (int)(g - J.base);  // < w * h < 2^31
+        const int y = k / J.w, x = k - y * J.w;
         const long long io = (long long)y * J.in_pitch + x, oo = (long long)y * J.out_pitch + x;
         float a = 0.0f, b = 0.0f;
         for (int c = 0; c < J.C; ++c) {
@@ -37,11 +37,11 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ J
 {
     for (long long g = gtid(); g < total; g += gstride()) {
         const PyrJob& J = job_ref(js, find_job(js, g, &PyrJob::base));
-        const long long k = g - J.base;
-        const long long npix = (long long)J.wout * J.hout;
-        const int p = (int)(k / npix);
-        const long long r = k - (long long)p * npix;
-        const int y = (int)(r / J.wout), x = (int)(r - (long long)y * J.wout);
+        const int k = (int)(g - J.base);  // < planes * w * h < 2^31
+        const int npix = J.wout * J.hout;
+        const int p = k / npix;
+        const int r = k - p * npix;
+        const int y = r / J.wout, x = r - y * J.wout;
         const float* in = J.in + p * J.in_plane;
         const int xs[5] = {clampi(2 * x - 2, 0, J.win - 1), clampi(2 * x - 1, 0, J.win - 1), min(2 * x, J.win - 1),
                            clampi(2 * x + 1, 0, J.win - 1), clampi(2 * x + 2, 0, J.win - 1)};
@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(256) upsample_kernel(const __grid_constant__ J
 {
     for (long long g = gtid(); g < total; g += gstride()) {
         const UpJob& J = job_ref(js, find_job(js, g, &UpJob::base));
-        const long long k = g - J.base;
-        const int y = (int)(k / J.wo), x = (int)(k - (long long)y * J.wo);
+        const int k = (int)(g - J.base);  // < w * h < 2^31
+        const int y = k / J.wo, x = k - y * J.wo;
         const float2 v = sample_flow(J.in, J.wi, J.hi, (float)x / J.factor, (float)y / J.factor);
         J.out[k] = make_float2(J.factor * v.x, J.factor * v.y);
     }

@@ -35,9 +35,9 @@ namespace dis {
 #define DIS_PIX_LOOP(BASE)                                                               \
     for (long long g = gtid(); g < total; g += gstride()) {                              \
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::BASE));               \
-        const long long k = g - J.BASE;                                                  \
+        const int k = (int)(g - J.BASE); /* < w * h < 2^31 */                            \
         const int w = J.w, h = J.h, pitch = J.pitch;                                     \
-        const int y = (int)(k / w), x = (int)(k - (long long)y * w);                     \
+        const int y = k / w, x = k - y * w;                                              \
         const long long o = (long long)y * pitch + x;                                    \
         (void)h;
 
@@ -227,11 +227,11 @@ __global__ void __launch_bounds__(256) refine_sor_kernel(const __grid_constant__
 {
     for (long long g = gtid(); g < total; g += gstride()) {
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::half_base));
-        const long long k = g - J.half_base;
+        const int k = (int)(g - J.half_base);  // < h * ceil(w / 2) < 2^31
         const int w = J.w, h = J.h, pitch = J.pitch;
         const int hw = (w + 1) >> 1;
-        const int y = (int)(k / hw);
-        const int x = 2 * (int)(k - (long long)y * hw) + ((y + colour) & 1);
+        const int y = k / hw;
+        const int x = 2 * (k - y * hw) + ((y + colour) & 1);
         if (x >= w) continue;
         const long long pl = J.plane;
         const long long o = (long long)y * pitch + x, f = (long long)y * w + x;

@@ -137,3 +137,11 @@ def test_host_buffer_call_argument_checks_need_no_gpu(dis):
     lib = ctypes.CDLL(dis.LIB_PATH)
     assert lib.dis_compute_flow_batched_host(None, None, 1, None, None) == dis.DIS_ERR_INVALID_ARG
     assert lib.dis_host_flows_ready(None, None) == dis.DIS_ERR_INVALID_ARG
+
+
+def test_frames_beyond_32_bit_pixel_indexing_are_refused(dis):
+    lib = ctypes.CDLL(dis.LIB_PATH)
+    h = ctypes.c_void_p()
+    assert lib.dis_create(ctypes.byref(h), 65536, 32768, 1, 1) == dis.DIS_ERR_INVALID_ARG and not h.value
+    assert lib.dis_pyr_down(ctypes.c_void_p(16), 65536, 32768, ctypes.c_int64(65536), ctypes.c_void_p(16),
+                            ctypes.c_int64(32768), None) == dis.DIS_ERR_INVALID_ARG
