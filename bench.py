@@ -157,9 +157,13 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": warmup, "ms_per_step": 1000 * dt / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "layered 1024x436, %s preset, 5 levels" % args.preset, "batch": 1},
+            "config": {"workload": "layered 1024x436, %s preset, 5 levels, batch %d per GPU" % (args.preset, args.batch),
+                       "batch_per_gpu": args.batch, "preset": args.preset,
+                       "parallelism": "replicas" if world > 1 else "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step one 512x218 pair (1/4 area), scaled by area"},
+                             "sample": "per step one 512x218 pair of the workload (1/4 of the area, one level "
+                                       "fewer), scaled by area to pairs/s at 1024x436; the batch's other pairs "
+                                       "would cost the same each"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
