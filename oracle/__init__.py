@@ -46,6 +46,9 @@ class OrParams(ctypes.Structure):
         ("sor_omega", ctypes.c_double),
         ("intensity_scale", ctypes.c_double),
         ("channels", ctypes.c_int),
+        ("dof", ctypes.c_int),
+        ("norm", ctypes.c_int),
+        ("huber_b", ctypes.c_double),
     ]
 
 
@@ -53,7 +56,7 @@ def params(**kw):
     """Parameter set with the paper's defaults (Sec. 3.1) overridden by keyword."""
     d = dict(patch_size=8, overlap=0.3, stride_override=0, grad_iters=16, coarsest_scale=-1,
              finest_scale=0, refine=1, var_outer=-1, var_inner=5, delta=5.0, gamma=10.0,
-             alpha=10.0, sor_omega=1.6, intensity_scale=255.0, channels=1)
+             alpha=10.0, sor_omega=1.6, intensity_scale=255.0, channels=1, dof=2, norm=0, huber_b=5.0)
     d.update(kw)
     return OrParams(**d)
 
@@ -71,15 +74,16 @@ def _load():
         P = ctypes.POINTER(OrParams)
         sig = {
             "or_bilinear": (d, [_D, i, i, d, d]),
+            "or_robust_error": (d, [d, i, d]),
             "or_pyr_down": (None, [_D, i, i, _D]),
             "or_sobel": (None, [_D, i, i, _D, _D]),
             "or_stride": (i, [i, d, i]),
             "or_grid_n": (i, [i, i, i]),
             "or_grid_pos": (i, [i, i, i, i]),
             "or_levels": (i, [i, i, P, _I, _I]),
-            "or_search_level": (None, [_D, _D, _D, _D, i, i, _D, i, i, d, i, i, i, _D, _D, _D, _I]),
+            "or_search_level": (None, [_D, _D, _D, _D, i, i, _D, i, i, d, i, i, i, _D, _D, _D, _I, i, i, d]),
             "or_densify_level": (None, [_D, _D, i, i, _D, i, i, _D, i, i, d, _D]),
-            "or_refine_level": (None, [_D, _D, i, i, i, _D, i, i, d, d, d, d]),
+            "or_refine_level": (None, [_D, _D, i, i, i, _D, i, i, d, d, d, d, i]),
             "or_upsample_flow": (None, [_D, i, i, d, _D, i, i]),
             "or_total_patches": (i, [i, i, P]),
             "or_dis_flow": (i, [_D, _D, i, i, P, _D, _D, _D, _D, u64p]),
@@ -141,9 +145,15 @@ def levels(W, H, prm):
     return rc, ss.value, sf.value
 
 
-def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen=None):
+def robust_error(e, norm, huber_b=5.0):
+    """Per-pixel error transform of the robust norms (0 L2, 1 L1, 2 Huber)."""
+    return _load().or_robust_error(float(e), int(norm), float(huber_b))
+
+
+def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen=None, dof=2, norm=0, huber_b=5.0):
     """Inverse search of one level.  Returns (u, u_init, status) with u, u_init of shape
-    (ny, nx, 2) and status (ny, nx) in {0 ok, 1 reset, 2 flat}."""
+    (ny, nx, 2) and status (ny, nx) in {0 ok, 1 reset, 2 flat}.  dof = 1: horizontal only;
+    norm: 0 L2, 1 L1, 2 Huber with threshold huber_b."""
     I0, Ix, Iy, I1 = _f64(I0), _f64(Ix), _f64(Iy), _f64(I1)
     h, w = I0.shape
     nx, ny = grid_n(w, ps, stride_), grid_n(h, ps, stride_)
@@ -156,7 +166,8 @@ def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen
         hc, wc = Uc.shape[:2]
     fz = None if frozen is None else _f64(frozen)
     _load().or_search_level(_p(I0), _p(Ix), _p(Iy), _p(I1), w, h, _p(Uc), wc, hc, float(cscale), ps, stride_,
-                            iters, _p(fz), _p(u), _p(ui), st.ctypes.data_as(_I))
+                            iters, _p(fz), _p(u), _p(ui), st.ctypes.data_as(_I), int(dof), int(norm),
+                            float(huber_b))
     return u, ui, st
 
 
@@ -172,15 +183,16 @@ def densify_level(I0, I1, u, ps, stride_, Uc=None, cscale=2.0):
     return U
 
 
-def refine_level(I0, I1, U, outer, inner, delta=5.0, gamma=10.0, alpha=10.0, omega=1.6):
-    """Variational refinement of one level; I0, I1 are (H, W) or (C, H, W).  Returns U + dU."""
+def refine_level(I0, I1, U, outer, inner, delta=5.0, gamma=10.0, alpha=10.0, omega=1.6, dof=2):
+    """Variational refinement of one level; I0, I1 are (H, W) or (C, H, W).  Returns U + dU.
+    dof = 1: the increment is horizontal only."""
     I0, I1 = _f64(I0), _f64(I1)
     if I0.ndim == 2:
         I0, I1 = I0[None], I1[None]
     C, h, w = I0.shape
     U = _f64(U).copy()
     _load().or_refine_level(_p(I0), _p(I1), w, h, C, _p(U), outer, inner, float(delta), float(gamma),
-                            float(alpha), float(omega))
+                            float(alpha), float(omega), int(dof))
     return U
 
 

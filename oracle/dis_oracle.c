@@ -42,7 +42,27 @@ typedef struct or_params {
     double sor_omega;      /* [R14] over-relaxation factor */
     double intensity_scale;/* [R1] inputs in [0,1] are multiplied by this (255) */
     int channels;          /* 1 or 3 */
+    int dof;               /* 2: optical flow; 1: horizontal displacement only (supp. depth from stereo) [R20] */
+    int norm;              /* search error norm (supp. robust error norms): 0 L2, 1 L1, 2 Huber [R21] */
+    double huber_b;        /* Huber threshold b on the intensity scale [R21] */
 } or_params;
+
+enum { OR_NORM_L2 = 0, OR_NORM_L1 = 1, OR_NORM_HUBER = 2 };
+
+/* [R21] Robust error norms (supplementary, robust error norms): before the update, the error of
+ * every pixel is transformed so that squaring it gives the L1 or the Huber penalty:
+ *   L1:    e <- sign(e) sqrt(|e|)
+ *   Huber: e <- e if |e| < b, else sign(e) sqrt(2 b |e| - b^2)
+ * (the printed condition "e < b" is read as |e| < b; b is a parameter). */
+double or_robust_error(double e, int norm, double b)
+{
+    if (norm == OR_NORM_L1) return (e < 0 ? -1.0 : 1.0) * sqrt(fabs(e));
+    if (norm == OR_NORM_HUBER) {
+        if (fabs(e) < b) return e;
+        return (e < 0 ? -1.0 : 1.0) * sqrt(2.0 * b * fabs(e) - b * b);
+    }
+    return e;
+}
 
 enum { OR_OK = 0, OR_ERR_INVALID = 1, OR_ERR_TOO_SMALL = 4 };
 enum { OR_PATCH_OK = 0, OR_PATCH_RESET = 1, OR_PATCH_FLAT = 2 };
@@ -226,10 +246,16 @@ static void init_at(const double* Uc, int wc, int hc, double cscale, double x, d
  * change a gradient).  [R7] flat patches keep u_init.
  * frozen != NULL replaces the search by u = u_init + frozen[i] (no reset test): the
  * differentiable map's stop-gradient search, with increments recorded by a previous run.
- * uinit_out and status_out may be NULL. */
+ * uinit_out and status_out may be NULL.
+ * [R20] dof = 1 (supplementary, depth from stereo: the vertical degree of freedom removed):
+ * v stays at its initial value and u takes the scalar step du = sum S'_x e / sum S'_x^2; the
+ * patch is flat when sum S'_x^2 <= 1e-6 tr(H') / 2.
+ * [R21] norm / huber_b: the per-pixel error e = (w - mean w) - T is transformed by
+ * or_robust_error before it enters sum S'^T e. */
 void or_search_level(const double* I0, const double* Ix, const double* Iy, const double* I1, int w, int h,
                      const double* Uc, int wc, int hc, double cscale, int ps, int stride, int iters,
-                     const double* frozen, double* u_out, double* uinit_out, int* status_out)
+                     const double* frozen, double* u_out, double* uinit_out, int* status_out, int dof, int norm,
+                     double huber_b)
 {
     int nx = or_grid_n(w, ps, stride), ny = or_grid_n(h, ps, stride), n = ps * ps;
     double* T = (double*)malloc(sizeof(double) * n);
@@ -272,7 +298,9 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
             double u = ui[0], v = ui[1];
             double det = h00 * h11 - h01 * h01, tr = h00 + h11;
             int st = OR_PATCH_OK;
-            if (det <= OR_DEGENERATE_REL * (0.5 * tr) * (0.5 * tr)) {
+            const int flat = dof == 1 ? h00 <= OR_DEGENERATE_REL * 0.5 * tr
+                                      : det <= OR_DEGENERATE_REL * (0.5 * tr) * (0.5 * tr);
+            if (flat) {
                 st = OR_PATCH_FLAT;
             } else {
                 for (int it = 0; it < iters; it++) {
@@ -286,14 +314,18 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
                     mw /= n;
                     double b0 = 0.0, b1 = 0.0;
                     for (int q = 0; q < n; q++) {
-                        double r = (wv[q] - mw) - T[q];
+                        double r = or_robust_error((wv[q] - mw) - T[q], norm, huber_b);
                         b0 += gx[q] * r;
                         b1 += gy[q] * r;
                     }
-                    double du = (h11 * b0 - h01 * b1) / det;
-                    double dv = (h00 * b1 - h01 * b0) / det;
-                    u -= du;
-                    v -= dv;
+                    if (dof == 1) {
+                        u -= b0 / h00;
+                    } else {
+                        double du = (h11 * b0 - h01 * b1) / det;
+                        double dv = (h00 * b1 - h01 * b0) / det;
+                        u -= du;
+                        v -= dv;
+                    }
                 }
                 double ex = u - ui[0], ey = v - ui[1];
                 if (sqrt(ex * ex + ey * ey) > (double)ps) {
@@ -365,8 +397,10 @@ void or_densify_level(const double* I0, const double* I1, int w, int h, const do
  *   (A_p + sum_q w_pq I) d = b_p + sum_q w_pq (U_q + dU_q - U_p),  w_pq = (psiS_p + psiS_q)/2,
  * dU_p <- (1 - omega) dU_p + omega d, red ((x + y) even) pixels first.  Finally U += dU.
  * I0 and I1 hold C planes each. */
+/* [R20] dof = 1: the increment dv stays 0; each SOR step solves the scalar equation
+ * (A11 + sum w_pq) du = b1 + sum w_pq (U_q + dU_q - U_p). */
 void or_refine_level(const double* I0, const double* I1, int w, int h, int C, double* U, int outer, int inner,
-                     double delta, double gamma, double alpha, double omega)
+                     double delta, double gamma, double alpha, double omega, int dof)
 {
     size_t n = (size_t)w * h;
     /* per channel: Ix Iy Iz Ixx Ixy Iyy Ixz Iyz b0 bx by */
@@ -473,7 +507,9 @@ void or_refine_level(const double* I0, const double* I1, int w, int h, int C, do
                         }
                         double m11 = Ao[0] + sw, m12 = Ao[1], m22 = Ao[2] + sw;
                         double det = m11 * m22 - m12 * m12;
-                        if (det > 0.0) {
+                        if (dof == 1) {
+                            if (m11 > 0.0) dU[2 * o] = (1.0 - omega) * dU[2 * o] + omega * (r1 / m11);
+                        } else if (det > 0.0) {
                             double d1 = (m22 * r1 - m12 * r2) / det;
                             double d2 = (m11 * r2 - m12 * r1) / det;
                             dU[2 * o] = (1.0 - omega) * dU[2 * o] + omega * d1;
@@ -533,6 +569,7 @@ int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_param
 {
     int C = p->channels, ss, sf;
     if (C != 1 && C != 3) return OR_ERR_INVALID;
+    if ((p->dof != 1 && p->dof != 2) || p->norm < 0 || p->norm > 2 || !(p->huber_b > 0.0)) return OR_ERR_INVALID;
     int rc = or_levels(W, H, p, &ss, &sf);
     if (rc != OR_OK) return rc;
     int ps = p->patch_size, stride = or_stride(ps, p->overlap, p->stride_override);
@@ -603,7 +640,7 @@ int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_param
             cs = 1.0;
         }
         or_search_level(S0[s], Ix, Iy, S1[s], w, h, Uc, wc, hc, cs, ps, stride, p->grad_iters,
-                        frozen ? frozen + 2 * off : NULL, u, ui, NULL);
+                        frozen ? frozen + 2 * off : NULL, u, ui, NULL, p->dof, p->norm, p->huber_b);
         if (record)
             for (int k = 0; k < 2 * np; k++) record[2 * off + k] = u[k] - ui[k];
         double* U = (double*)malloc(sizeof(double) * 2 * ns);
@@ -617,7 +654,8 @@ int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_param
                 memcpy(Q1 + ns * c, P1[s * C + c], sizeof(double) * ns);
             }
             int outer = p->var_outer < 0 ? s + 1 : p->var_outer;
-            or_refine_level(Q0, Q1, w, h, C, U, outer, p->var_inner, p->delta, p->gamma, p->alpha, p->sor_omega);
+            or_refine_level(Q0, Q1, w, h, C, U, outer, p->var_inner, p->delta, p->gamma, p->alpha, p->sor_omega,
+                            p->dof);
             free(Q0);
             free(Q1);
         }

@@ -502,3 +502,159 @@ def test_charbonnier_loss_closed_forms():
     zero = np.zeros((9, 10, 2))
     assert abs(oracle.charbonnier_loss(I0, I0, zero, 1e-3) - 1e-3) < 1e-15
     assert abs(oracle.charbonnier_loss(I0, I0 + 0.25, zero, 1e-3) - math.sqrt(0.0625 + 1e-6)) < 1e-12
+
+
+# ---- stereo: the vertical degree of freedom removed (supplementary, depth from stereo) ----
+
+def test_stereo_search_contracts_by_scalar_closed_form():
+    # Horizontal translation of a bilinear image, v held at 0: the mean-normalised residual is
+    # exactly (g_x - mean g_x) du, so one scalar step maps du -> rho du with
+    # rho = n mean(g_x)^2 / sum g_x^2 (the 1-D case of the contraction M of the flow search).
+    h = w = 64
+    ps, st_, px, py = 8, 8, 24, 32
+    c = (2.0, -0.3 * 34, -0.3, 0.3)  # g_x = 0.3 (y - 34) changes sign inside the patch
+    t = np.array([0.8, 0.0])
+    I0, I1, gx, gy = _bilinear_scene(h, w, c, t)
+    Y, X = np.mgrid[py:py + ps, px:px + ps].astype(float)
+    Gx = (c[1] + c[3] * Y).ravel()
+    rho = ps * ps * Gx.mean() ** 2 / (Gx ** 2).sum()
+    assert 0.05 < rho < 0.95
+    k = _patch_index(w, ps, st_, px, py)
+    for iters in range(1, 6):
+        u, _, st = oracle.search_level(I0, gx, gy, I1, ps, st_, iters, dof=1)
+        err = u.reshape(-1, 2)[k] - t
+        assert abs(err[0] - rho ** iters * (-t[0])) < 1e-11 and err[1] == 0.0, (iters, err)
+
+
+def test_stereo_search_keeps_v_and_needs_horizontal_texture():
+    g = np.random.default_rng(21)
+    h, w = 40, 48
+    I0 = ndimage.gaussian_filter(g.standard_normal((h, w)), 1.5) * 40 + 120
+    I1 = np.roll(I0, 1, axis=1)
+    gx, gy = oracle.sobel(I0)
+    Uc = np.zeros((h, w, 2))
+    Uc[..., 1] = 0.75  # the initial vertical displacement survives unchanged
+    u, ui, st = oracle.search_level(I0, gx, gy, I1, 8, 4, 8, Uc=Uc, cscale=1.0, dof=1)
+    assert (u[..., 1] == 0.75).all() and (st == 0).any()
+    # texture along y only: no horizontal gradient, every patch is flat in the scalar search
+    Iy = np.tile(ndimage.gaussian_filter(g.standard_normal(h), 1.0)[:, None] * 30 + 100, (1, w))
+    gx, gy = oracle.sobel(Iy)
+    _, _, st = oracle.search_level(Iy, gx, gy, Iy, 8, 4, 8, dof=1)
+    assert (st == 2).all()
+
+
+def test_stereo_refine_pure_smoothing_matches_flow_u_and_keeps_v():
+    # delta = gamma = 0: the 2x2 systems decouple (A = 0), so within one outer pass (fixed
+    # smoothness weights) the horizontal component of the flow refinement and the scalar
+    # refinement take identical steps; v does not move.  (A second pass differs: the lagged
+    # weights see the smoothed v of the flow refinement.)
+    g = np.random.default_rng(22)
+    I0, I1 = g.uniform(0, 255, (11, 13)), g.uniform(0, 255, (11, 13))
+    U = g.uniform(-1, 1, (11, 13, 2))
+    a = oracle.refine_level(I0, I1, U, 1, 6, delta=0.0, gamma=0.0)
+    b = oracle.refine_level(I0, I1, U, 1, 6, delta=0.0, gamma=0.0, dof=1)
+    assert np.abs(a[..., 0] - b[..., 0]).max() < 1e-13
+    assert np.array_equal(b[..., 1], U[..., 1])
+
+
+def test_stereo_refine_brightness_term_recovers_horizontal_translation():
+    # one channel suffices in 1-D: a ramp along x translated by t gives I_x du + I_z = 0 at du = t
+    h, w = 30, 40
+    t = 0.65
+    I0, I1 = _ramp_pair(h, w, 2.5, 1.5, (t, 0.0))
+    out = oracle.refine_level(I0, I1, np.zeros((h, w, 2)), 1, 80, delta=5.0, gamma=10.0, alpha=1e-4, dof=1)
+    assert np.abs(out[10:20, 10:30, 0] - t).max() < 1e-8 and (out[..., 1] == 0.0).all()
+
+
+def test_stereo_pipeline_recovers_horizontal_translation_of_saddle_image():
+    # the scalar form of the saddle-scene pipeline pin: every level stays bilinear in its
+    # interior and each interior patch contracts onto t / 2^s by the scalar factor rho < 1
+    h = w = 48
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    t = 1.3
+    f = lambda X, Y: 0.5 * (X - 23.5) * (Y - 23.5) + 100.0  # noqa: E731
+    I0, I1 = f(x, y), f(x - t, y)
+    q = oracle.params(patch_size=8, stride_override=4, grad_iters=5000, coarsest_scale=1, refine=0,
+                      intensity_scale=1.0, dof=1)
+    flow = oracle.dis_flow(I0, I1, q)
+    assert np.abs(flow[12:36, 12:36, 0] - t).max() < 1e-6 and (flow[..., 1] == 0.0).all()
+
+
+# ---- robust error norms (supplementary, robust error norms) ----
+
+def test_robust_error_closed_forms():
+    for e in (-7.3, -0.2, 0.0, 0.4, 2.0, 31.0):
+        assert oracle.robust_error(e, 0) == e
+        v = oracle.robust_error(e, 1)
+        assert math.copysign(1, v) == math.copysign(1, e) or e == 0.0
+        assert abs(v * v - abs(e)) < 1e-12  # squared: the L1 penalty
+        b = 2.0
+        hv = oracle.robust_error(e, 2, b)
+        huber2 = e * e if abs(e) < b else 2 * b * abs(e) - b * b  # twice the Huber penalty
+        assert abs(hv * hv - huber2) < 1e-12 and (hv >= 0) == (e >= 0)
+    # continuity of the Huber branch at |e| = b
+    assert abs(oracle.robust_error(2.0 - 1e-12, 2, 2.0) - oracle.robust_error(2.0, 2, 2.0)) < 1e-9
+
+
+def test_robust_search_fixed_points_and_large_huber_threshold():
+    g = np.random.default_rng(23)
+    h, w, t = 40, 44, (2, -1)
+    I0 = ndimage.gaussian_filter(g.standard_normal((h, w)), 1.5) * 50 + 100
+    I1 = np.roll(np.roll(I0, t[1], axis=0), t[0], axis=1)
+    gx, gy = oracle.sobel(I0)
+    Uc = np.zeros((h, w, 2))
+    Uc[..., 0], Uc[..., 1] = t
+    # an exact integer translation: zero error at u = t, a fixed point of every norm
+    for norm in (1, 2):
+        u, _, _ = oracle.search_level(I0, gx, gy, I1, 8, 4, 10, Uc=Uc, cscale=1.0, norm=norm, huber_b=3.0)
+        inner = u[2:-2, 2:-2]
+        assert np.abs(inner - t).max() < 1e-9, norm
+    # a Huber threshold above every error leaves the L2 iterates unchanged
+    I1s = ndimage.shift(I0, (0.3, -0.45), order=1, mode="nearest")
+    a, _, _ = oracle.search_level(I0, gx, gy, I1s, 8, 4, 12)
+    b, _, _ = oracle.search_level(I0, gx, gy, I1s, 8, 4, 12, norm=2, huber_b=1e9)
+    assert np.array_equal(a, b)
+
+
+def test_robust_norms_downweight_an_outlier_block():
+    # a patch whose lower-right quarter is replaced by garbage in I1: the L1 and Huber
+    # searches end closer to the true subpixel translation than L2
+    g = np.random.default_rng(24)
+    h = w = 48
+    I0 = ndimage.gaussian_filter(g.standard_normal((h, w)), 2.0) * 60 + 128
+    t = (0.6, -0.35)
+    I1 = ndimage.shift(I0, (t[1], t[0]), order=3, mode="nearest")
+    px = py = 16
+    I1[py + 6:py + 12, px + 6:px + 12] = g.uniform(0, 255, (6, 6))
+    gx, gy = oracle.sobel(I0)
+    k = _patch_index(w, 12, 4, px, py)
+    errs = {}
+    for norm in (0, 1, 2):
+        u, _, st = oracle.search_level(I0, gx, gy, I1, 12, 4, 60, norm=norm, huber_b=4.0)
+        errs[norm] = float(np.hypot(*(u.reshape(-1, 2)[k] - t)))
+    assert errs[1] < errs[0] and errs[2] < errs[0], errs
+
+
+@pytest.mark.parametrize("norm,b", [(1, 5.0), (2, 0.6)])
+def test_robust_search_one_step_on_centred_saddle(norm, b):
+    # saddle centred on the patch: zero mean gradient, so the mean-normalised error at u = 0 is
+    # exactly e_q = g_q . t and H' = H; one step gives u = H^-1 sum_q g_q psi(g_q . t) with psi
+    # the norm's error transform (for L2 this is the exact one-step pin above).
+    h = w = 48
+    ps, px, py = 8, 16, 16
+    x0 = y0 = px + (ps - 1) / 2
+    c3, t = 0.8, np.array([1.37, -0.61])
+    c = (c3 * x0 * y0 + 5.0, -c3 * y0, -c3 * x0, c3)
+    I0, I1, gx, gy = _bilinear_scene(h, w, c, t)
+    Y, X = np.mgrid[py:py + ps, px:px + ps].astype(float)
+    G = np.stack([(c[1] + c[3] * Y).ravel(), (c[2] + c[3] * X).ravel()], 1)
+    e = G @ t
+    if norm == 1:
+        psi = np.sign(e) * np.sqrt(np.abs(e))
+    else:
+        psi = np.where(np.abs(e) < b, e, np.sign(e) * np.sqrt(np.maximum(2 * b * np.abs(e) - b * b, 0.0)))
+    assert (np.abs(e) >= b).any() or norm == 1  # both Huber branches are exercised
+    ref = np.linalg.solve(G.T @ G, G.T @ psi)
+    u, _, _ = oracle.search_level(I0, gx, gy, I1, ps, 16, 1, norm=norm, huber_b=b)
+    got = u.reshape(-1, 2)[_patch_index(w, ps, 16, px, py)]
+    assert np.abs(got - ref).max() < 1e-12 and np.abs(got - t).max() > 1e-3
