@@ -60,13 +60,22 @@ typedef struct dis_params {
     float sor_omega;         /* SOR over-relaxation, (0, 2) (the paper does not state it: 1.6) */
     float intensity_scale;   /* 255 */
     int32_t channels;        /* 1 (grayscale) or 3 (RGB, planar) */
+    int32_t dof;             /* 2: optical flow; 1: stereo, horizontal displacements only (supplementary,
+                              * depth from stereo: v keeps its initial value, the search takes the scalar
+                              * step of the x component, the refinement leaves dv at 0) */
+    int32_t norm;            /* search error norm (supplementary, robust error norms): 0 L2, 1 L1
+                              * (e <- sign(e) sqrt|e|), 2 Huber (e <- e if |e| < huber_b, else
+                              * sign(e) sqrt(2 huber_b |e| - huber_b^2)); e = I1(x + u) - mean - T */
+    float huber_b;           /* Huber threshold on the intensity_scale scale, > 0 (5) */
 } dis_params;
 
 /* Presets for dis_default_params.  OP1..OP4 are the paper's operating points
  * (Sec. 3.3: theta_sf/theta_it/theta_ps/theta_ov = 3/16/8/0.30 without refinement,
  * 3/12/8/0.40, 1/16/12/0.75, 0/256/12/0.75).  FAST/MEDIUM/DENSE are the workload presets
  * used by the benchmarks (patch 8 / 30 % / 16 it / finest 2 / no refinement; patch 8 / 50 %
- * / 32 it / refinement; patch 12 / 75 % / 128 it / refinement). */
+ * / 32 it / refinement; patch 12 / 75 % / 128 it / refinement).  STEREO_OP1..OP4 and
+ * STEREO_DENSE are OP1..OP4 and DENSE for depth from stereo (supplementary, depth from stereo):
+ * dof = 1 and theta_it halved. */
 enum {
     DIS_PRESET_DEFAULT = 0,
     DIS_PRESET_OP1 = 1,
@@ -75,7 +84,12 @@ enum {
     DIS_PRESET_OP4 = 4,
     DIS_PRESET_FAST = 5,
     DIS_PRESET_MEDIUM = 6,
-    DIS_PRESET_DENSE = 7
+    DIS_PRESET_DENSE = 7,
+    DIS_PRESET_STEREO_OP1 = 8,
+    DIS_PRESET_STEREO_OP2 = 9,
+    DIS_PRESET_STEREO_OP3 = 10,
+    DIS_PRESET_STEREO_OP4 = 11,
+    DIS_PRESET_STEREO_DENSE = 12
 };
 
 typedef struct dis_handle dis_handle;
@@ -261,6 +275,16 @@ dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, i
                                int hc, float cscale, int ps, int stride, int iters, int variant, float* u_out,
                                float* uinit_out, int* status_out, void* stream);
 
+/* dis_search_level_ex with the search's degrees of freedom and error norm (dis_params.dof, norm
+ * and huber_b).  dof 1 leaves the v component of u_out at u_init; status 2 (flat) then means
+ * sum S'_x^2 <= 1e-6 tr(H') / 2.  The stereo and robust-norm searches run in the grouped form
+ * whatever the variant; dof 2 with norm 0 is dis_search_level_ex.  DIS_ERR_INVALID_ARG for a
+ * dof outside {1, 2}, a norm outside {0, 1, 2} or huber_b <= 0. */
+dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc,
+                                int wc, int hc, float cscale, int ps, int stride, int iters, int variant, int dof,
+                                int norm, float huber_b, float* u_out, float* uinit_out, int* status_out,
+                                void* stream);
+
 /* Step 4 of Alg. 1 (Eq. 3): U(x) = sum_i w_i(x) u_i / sum_i w_i(x) over the patches covering
  * x, w_i(x) = 1 / max(1, |I1(x + u_i) - I0(x)|).  u: nx*ny*2 patch flows; U_out: w*h*2.
  * Uc / cscale give the fallback for uncovered pixels as in dis_search_level. */
@@ -274,6 +298,13 @@ dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int
 dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
                             int channels, float* U, int outer, int inner, float delta, float gamma, float alpha,
                             float omega, void* stream);
+
+/* dis_refine_level with the degrees of freedom: dof 1 (stereo) keeps the v component of U and
+ * solves, at every SOR step, the scalar equation of the x increment,
+ * (A11 + sum_q w_pq) du = b1 + sum_q w_pq (U_q + dU_q - U_p)_x; dof 2 is dis_refine_level. */
+dis_status dis_refine_level_ex(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
+                               int channels, float* U, int outer, int inner, float delta, float gamma, float alpha,
+                               float omega, int dof, void* stream);
 
 /* Up-scaling (Sec. 3.1, last paragraph): Uout(x) = factor * Uin(x / factor), bilinear with
  * clamping.  Uin: wi*hi*2, Uout: wo*ho*2. */
@@ -289,8 +320,9 @@ dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, flo
  * (record_out); dis_replay_flow evaluates F and dis_backward its gradient.  Both compute in
  * double precision: the refinement's robust weights Psi'(a^2) = 1 / (2 sqrt(a^2 + eps^2))
  * (eps = 0.001) make the gradient depend on flow and residual differences near 1e-6, below the
- * resolution of FP32 flow values.  Grayscale and finest_scale == 0 only (DIS_ERR_NOT_SUPPORTED
- * otherwise).  frozen: dis_levels' total_patches x 2 floats, coarsest level first; init_flow
+ * resolution of FP32 flow values.  Grayscale, finest_scale == 0 and dof == 2 only
+ * (DIS_ERR_NOT_SUPPORTED otherwise); the search norm does not enter F (it only decides the
+ * recorded increments).  frozen: dis_levels' total_patches x 2 floats, coarsest level first; init_flow
  * (nullable): level theta_ss resolution, dense, 2 floats per pixel.  Nothing is allocated: the
  * caller passes a device workspace of dis_backward_workspace_bytes bytes. */
 

@@ -87,6 +87,14 @@ dis_status validate(const dis_params* p, std::string& err)
         err = "refinement weights must be finite and >= 0, sor_omega in (0, 2), intensity_scale > 0";
         return DIS_ERR_INVALID_ARG;
     }
+    if (p->dof != 1 && p->dof != 2) {
+        err = "dof must be 1 (stereo) or 2 (optical flow)";
+        return DIS_ERR_INVALID_ARG;
+    }
+    if (p->norm < 0 || p->norm > 2 || !finite(p->huber_b) || !(p->huber_b > 0.0f)) {
+        err = "norm must be 0 (L2), 1 (L1) or 2 (Huber), huber_b finite and > 0";
+        return DIS_ERR_INVALID_ARG;
+    }
     return DIS_OK;
 }
 
@@ -407,11 +415,14 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
             case Phase::LEVEL: {
                 auto js = dis::device_jobs(reinterpret_cast<const LevelJob*>(tab), ph.n);
                 const int lanes = hd->search_lanes[ps];
-                if (lanes == 1)
+                if (lanes == 1 && p.dof == 2 && p.norm == 0)
                     e = traced(DIS_LAUNCH_SEARCH_PLANES, ph.s,
                                [&] { return dis::launch_search_planes(js, ph.total2, hd->lc, s); });
                 if (e == cudaSuccess)
                     e = traced(DIS_LAUNCH_SEARCH, ph.s, [&] {
+                        if (p.dof != 2 || p.norm != 0)
+                            return dis::launch_search_mode(js, ph.total, ps, stride, p.grad_iters, p.dof, p.norm,
+                                                           p.huber_b, hd->lc, s);
                         return dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s, lanes, lanes == 1);
                     });
                 if (e == cudaSuccess)
@@ -429,6 +440,7 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                     a.omega = p.sor_omega;
                     a.fused = hd->refine_fused;
                     a.C = p.channels;
+                    a.dof = p.dof;
                     e = traced(DIS_LAUNCH_REFINE, ph.s,
                                [&] { return dis::launch_refine(js, ph.total2, ph.total3, ph.total4, a, hd->lc, s); });
                 }
@@ -535,6 +547,14 @@ void dis_default_params(dis_params* p, int preset)
     p->sor_omega = 1.6f;
     p->intensity_scale = 255.0f;
     p->channels = 1;
+    p->dof = 2;
+    p->norm = 0;
+    p->huber_b = 5.0f;
+    int stereo = 0;
+    if (preset >= DIS_PRESET_STEREO_OP1 && preset <= DIS_PRESET_STEREO_DENSE) {
+        stereo = 1;
+        preset = preset == DIS_PRESET_STEREO_DENSE ? DIS_PRESET_DENSE : preset - DIS_PRESET_STEREO_OP1 + DIS_PRESET_OP1;
+    }
     switch (preset) {
         case DIS_PRESET_OP1: p->finest_scale = 3; p->grad_iters = 16; p->patch_size = 8; p->overlap = 0.30f; p->refine = 0; break;
         case DIS_PRESET_OP2: p->finest_scale = 3; p->grad_iters = 12; p->patch_size = 8; p->overlap = 0.40f; break;
@@ -544,6 +564,10 @@ void dis_default_params(dis_params* p, int preset)
         case DIS_PRESET_MEDIUM: p->finest_scale = 0; p->grad_iters = 32; p->patch_size = 8; p->overlap = 0.50f; break;
         case DIS_PRESET_DENSE: p->finest_scale = 0; p->grad_iters = 128; p->patch_size = 12; p->overlap = 0.75f; break;
         default: break;
+    }
+    if (stereo) {  // supplementary, depth from stereo: the same operating points, theta_it halved
+        p->dof = 1;
+        p->grad_iters /= 2;
     }
 }
 
@@ -914,12 +938,15 @@ static bool level_args_ok(int w, int h, int64_t pitch, int ps, int stride, const
     return true;
 }
 
-dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
-                               int hc, float cscale, int ps, int stride, int iters, int variant, float* u_out,
-                               float* uinit_out, int* status_out, void* stream)
+dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc,
+                                int wc, int hc, float cscale, int ps, int stride, int iters, int variant, int dof,
+                                int norm, float huber_b, float* u_out, float* uinit_out, int* status_out,
+                                void* stream)
 {
     if (!I0 || !I1 || !u_out || iters < 0 || !level_args_ok(w, h, pitch, ps, stride, Uc, wc, hc, cscale))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: bad pointer, size, pitch or grid");
+    if ((dof != 1 && dof != 2) || norm < 0 || norm > 2 || !finite(huber_b) || !(huber_b > 0.0f))
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: dof, norm or huber_b out of range");
     if (variant != 0) {
         int opts[8];
         const int n = dis_search_variants(ps, opts, 8);
@@ -944,9 +971,21 @@ dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, i
     J.nx = grid_n(w, ps, stride);
     J.ny = grid_n(h, ps, stride);
     J.C = 1;
-    cudaError_t e = dis::launch_search(dis::single_job(J), (long long)J.nx * J.ny, ps, stride, iters, stage_lc(),
-                                       (cudaStream_t)stream, variant, false);
+    const long long np = (long long)J.nx * J.ny;
+    cudaError_t e = (dof != 2 || norm != 0)
+                        ? dis::launch_search_mode(dis::single_job(J), np, ps, stride, iters, dof, norm, huber_b,
+                                                  stage_lc(), (cudaStream_t)stream)
+                        : dis::launch_search(dis::single_job(J), np, ps, stride, iters, stage_lc(),
+                                             (cudaStream_t)stream, variant, false);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_search_level");
+}
+
+dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
+                               int hc, float cscale, int ps, int stride, int iters, int variant, float* u_out,
+                               float* uinit_out, int* status_out, void* stream)
+{
+    return dis_search_level_ex2(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, variant, 2, 0, 5.0f,
+                                u_out, uinit_out, status_out, stream);
 }
 
 dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
@@ -982,13 +1021,14 @@ dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_densify_level");
 }
 
-dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
-                            int channels, float* U, int outer, int inner, float delta, float gamma, float alpha,
-                            float omega, void* stream)
+dis_status dis_refine_level_ex(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
+                               int channels, float* U, int outer, int inner, float delta, float gamma, float alpha,
+                               float omega, int dof, void* stream)
 {
     if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
     if (!I0 || !I1 || !U || w < 1 || h < 1 || pitch < w || channels < 1 || channels > 3 || outer < 0 || inner < 0 ||
-        !finite(delta) || !finite(gamma) || !finite(alpha) || !(omega > 0.0f && omega < 2.0f))
+        !finite(delta) || !finite(gamma) || !finite(alpha) || !(omega > 0.0f && omega < 2.0f) ||
+        (dof != 1 && dof != 2))
         return fail(hd, DIS_ERR_INVALID_ARG, "dis_refine_level: bad pointer, size, pitch or parameter");
     if ((size_t)dis::rs_planes(channels) * (size_t)pitch * (size_t)h > hd->rs_floats)
         return fail(hd, DIS_ERR_INVALID_ARG, "dis_refine_level: level larger than the handle's scratch");
@@ -1005,10 +1045,18 @@ dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, in
     J.rs = reinterpret_cast<float*>(hd->arena + hd->off_rs);
     long long tiles = 0;
     dis::set_refine_tiles(J, tiles);
-    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega, hd->refine_fused, channels};
+    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega, hd->refine_fused, channels, dof};
     const long long tp = (long long)w * h, th = (long long)h * ((w + 1) / 2);
     cudaError_t e = dis::launch_refine(dis::single_job(J), tp, th, tiles, a, hd->lc, (cudaStream_t)stream);
     return e == cudaSuccess ? DIS_OK : cuda_fail(hd, e, "dis_refine_level");
+}
+
+dis_status dis_refine_level(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
+                            int channels, float* U, int outer, int inner, float delta, float gamma, float alpha,
+                            float omega, void* stream)
+{
+    return dis_refine_level_ex(hd, I0, I1, w, h, pitch, channels, U, outer, inner, delta, gamma, alpha, omega, 2,
+                               stream);
 }
 
 dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, float* Uout, int wo, int ho, void* stream)
@@ -1048,7 +1096,9 @@ extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n,
     dis_status vst = validate(p, verr);
     if (vst != DIS_OK) return fail(hd, vst, verr);
     int opts[8];
-    const int nopt = dis::search_lane_options(p->patch_size, opts);
+    // the stereo and robust-norm searches have one form: only the refinement is tuned for them
+    const bool flow_l2 = p->dof == 2 && p->norm == 0;
+    const int nopt = flow_l2 ? dis::search_lane_options(p->patch_size, opts) : 0;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

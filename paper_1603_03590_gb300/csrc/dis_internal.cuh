@@ -137,6 +137,10 @@ cudaError_t launch_search_coop(const Jobs<LevelJob>& js, long long total, int ps
 cudaError_t launch_search_planes(const Jobs<LevelJob>& js, long long total_pix, const LaunchCfg& lc, cudaStream_t s);
 // Lanes-per-patch variants the search offers for patch size ps (first = default); returns the count.
 int search_lane_options(int ps, int* out);
+// The stereo (dof 1) and robust-norm (norm 1 L1, 2 Huber with threshold huber_b) searches, in the
+// grouped form whatever the variant; dof 2 with norm 0 is launch_search.
+cudaError_t launch_search_mode(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int dof,
+                               int norm, float huber_b, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, int stride, const LaunchCfg& lc,
                            cudaStream_t s);
 struct RefineArgs {
@@ -146,6 +150,7 @@ struct RefineArgs {
                         // kRefineFusedMaxPixels per launch, in two above; 2: one fused launch,
                         // 3: two fused launches per pass, whenever inner allows
     int C = 1;          // channels of every job of the launch
+    int dof = 2;        // 1: stereo, the vertical increment stays 0
 };
 // Square tiles of the fused outer-iteration kernel; at most kRefineMaxFusedInner inner sweeps
 // (2 half-sweeps each) run in one launch, the halo being as wide as the half-sweeps.

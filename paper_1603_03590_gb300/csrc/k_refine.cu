@@ -196,11 +196,26 @@ __global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_consta
 
 // One SOR update of pixel p: neighbours q (left, right, up, down; `in[q]` false outside the
 // image) with smoothness weights psq, flows Uq and increments dq; updates (du, dv) in place.
+// dof 1 (stereo, the vertical degree of freedom removed): dv stays, du solves the scalar
+// equation (a11 + sum w) du = b1 + sum w (Uq.x + duq - Up.x).
 __device__ __forceinline__ void refine_sor_update(float a11, float a12, float a22, float b1, float b2, float ps_p,
                                                   const bool (&in)[4], const float (&psq)[4], const float2 (&Uq)[4],
                                                   const float (&duq)[4], const float (&dvq)[4], float2 Up,
-                                                  float omega, float& du, float& dv)
+                                                  float omega, int dof, float& du, float& dv)
 {
+    if (dof == 1) {
+        float sw = 0.0f, r1 = b1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!in[q]) continue;
+            const float wq = 0.5f * (ps_p + psq[q]);
+            sw += wq;
+            r1 = fmaf(wq, (Uq[q].x + duq[q]) - Up.x, r1);
+        }
+        const float m11 = a11 + sw;
+        if (m11 > 0.0f) du = (1.0f - omega) * du + omega * (r1 * __frcp_rn(m11));
+        return;
+    }
     float sw = 0.0f, r1 = b1, r2 = b2;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -223,7 +238,7 @@ __device__ __forceinline__ void refine_sor_update(float a11, float a12, float a2
 
 // One colour of one red-black sweep: the pixels with (x + y) % 2 == colour.
 __global__ void __launch_bounds__(256) refine_sor_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
-                                                         int colour, float omega)
+                                                         int colour, float omega, int dof)
 {
     for (long long g = gtid(); g < total; g += gstride()) {
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::half_base));
@@ -255,7 +270,7 @@ __global__ void __launch_bounds__(256) refine_sor_kernel(const __grid_constant__
         }
         float du = du_p[o], dv = dv_p[o];
         refine_sor_update(S[o], S[pl + o], S[2 * pl + o], S[3 * pl + o], S[4 * pl + o], S[5 * pl + o], in, psq, Uq,
-                          duq, dvq, J.U[f], omega, du, dv);
+                          duq, dvq, J.U[f], omega, dof, du, dv);
         du_p[o] = du;
         dv_p[o] = dv;
     }
@@ -287,7 +302,7 @@ template <int K, int PHASE>
 __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __grid_constant__ Jobs<LevelJob> js,
                                                                         long long total_tiles, int src, int dst,
                                                                         int j0, float delta, float gamma,
-                                                                        float alpha, float omega)
+                                                                        float alpha, float omega, int dof)
 {
     extern __shared__ float4 sm4[];
     constexpr int T = kRefineTile;
@@ -407,7 +422,7 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
                     const float2 s01 = r0[i0], s23 = r0[E0 + i0], s45 = r0[2 * E0 + i0];
                     float du = me.z, dv = me.w;
                     refine_sor_update(s01.x, s01.y, s23.x, s23.y, s45.x, s45.y, in, psq, Uq, duq, dvq,
-                                      make_float2(me.x, me.y), omega, du, dv);
+                                      make_float2(me.x, me.y), omega, dof, du, dv);
                     me.z = du;
                     me.w = dv;
                     r1[i1] = me;
@@ -464,7 +479,7 @@ static cudaError_t outer_launch(const Jobs<LevelJob>& js, long long total_tiles,
     }
     const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * occ);
     refine_outer_kernel<K, PHASE><<<gt, kOuterThreads, smem, s>>>(js, total_tiles, src, dst, j0, a.delta, a.gamma,
-                                                                   a.alpha, a.omega);
+                                                                   a.alpha, a.omega, a.dof);
     return cudaGetLastError();
 }
 
@@ -514,8 +529,8 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
         for (int ot = 0; ot < a.outer; ++ot) {
             refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);
             for (int it = 0; it < a.inner; ++it) {
-                refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 0, a.omega);
-                refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 1, a.omega);
+                refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 0, a.omega, a.dof);
+                refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 1, a.omega, a.dof);
             }
         }
         refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, du_plane);

@@ -1,0 +1,33 @@
+// Stereo (one degree of freedom) and robust-norm modes of the patch search, in the grouped form
+// of k_search_grouped.cuh (see its header for the arithmetic of each mode).
+#include "k_search_grouped.cuh"
+
+namespace dis {
+
+template <int DOF, bool ROBUST>
+static cudaError_t launch_mode(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int norm,
+                               float huber_b, const LaunchCfg& lc, cudaStream_t s)
+{
+    // the robust form keeps four coefficients per pixel in registers: fewer resident blocks
+    // (chosen so that nothing spills)
+    constexpr int MB8 = ROBUST ? (DOF == 1 ? 3 : 4) : 6, MB12 = ROBUST ? (DOF == 1 ? 2 : 3) : 5;
+    if (ps == 8) return launch_lp<8, 8, 8, MB8, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
+    if (ps == 12)
+        return launch_lp<16, 9, 12, MB12, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
+    if (ps < 8) return launch_lp<8, 7, 0, 4, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
+    return launch_lp<16, 16, 0, 2, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
+}
+
+cudaError_t launch_search_mode(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int dof,
+                               int norm, float huber_b, const LaunchCfg& lc, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    if (norm == 0) {
+        if (dof == 1) return launch_mode<1, false>(js, total, ps, stride, iters, 0, 0.0f, lc, s);
+        return cudaErrorInvalidValue;  // the flow search with the L2 norm is launch_search
+    }
+    if (dof == 1) return launch_mode<1, true>(js, total, ps, stride, iters, norm, huber_b, lc, s);
+    return launch_mode<2, true>(js, total, ps, stride, iters, norm, huber_b, lc, s);
+}
+
+}  // namespace dis

@@ -19,7 +19,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 DIS_OK, DIS_ERR_INVALID_ARG, DIS_ERR_OUT_OF_MEMORY, DIS_ERR_CUDA = 0, 1, 2, 3
 DIS_ERR_TOO_SMALL, DIS_ERR_TIMEOUT, DIS_ERR_NOT_SUPPORTED = 4, 5, 6
-PRESETS = {"default": 0, "op1": 1, "op2": 2, "op3": 3, "op4": 4, "fast": 5, "medium": 6, "dense": 7}
+PRESETS = {"default": 0, "op1": 1, "op2": 2, "op3": 3, "op4": 4, "fast": 5, "medium": 6, "dense": 7,
+           "stereo_op1": 8, "stereo_op2": 9, "stereo_op3": 10, "stereo_op4": 11, "stereo_dense": 12}
+NORMS = {"l2": 0, "l1": 1, "huber": 2}
 
 
 class DisError(RuntimeError):
@@ -46,6 +48,9 @@ class dis_params(ctypes.Structure):
         ("sor_omega", ctypes.c_float),
         ("intensity_scale", ctypes.c_float),
         ("channels", ctypes.c_int32),
+        ("dof", ctypes.c_int32),
+        ("norm", ctypes.c_int32),
+        ("huber_b", ctypes.c_float),
     ]
 
 
@@ -86,6 +91,9 @@ _SIGS = {
     "dis_sobel": (_i, [_vp, _i, _i, _i64, _vp, _vp, _i64, _vp]),
     "dis_search_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dis_search_level_ex": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "dis_search_level_ex2": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _i, _f, _vp, _vp, _vp,
+                                  _vp]),
+    "dis_refine_level_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _i, _vp]),
     "dis_densify_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _vp, _i, _i, _f, _vp, _vp]),
     "dis_refine_level": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
     "dis_upsample_flow": (_i, [_vp, _i, _i, _f, _vp, _i, _i, _vp]),
@@ -131,7 +139,7 @@ def dis_default_params(preset="default", **overrides):
     p = dis_params()
     _lib.dis_default_params(ctypes.byref(p), PRESETS[preset] if isinstance(preset, str) else int(preset))
     for k, v in overrides.items():
-        setattr(p, k, v)
+        setattr(p, k, NORMS[v] if k == "norm" and isinstance(v, str) else v)
     return p
 
 
@@ -279,6 +287,22 @@ def dis_search_level_ex(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, ite
 def dis_densify_level(I0, I1, w, h, pitch, u, ps, stride, Uc, wc, hc, cscale, U_out, stream=None):
     _check(_lib.dis_densify_level(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(u), ps, stride, _ptr(Uc), wc, hc, cscale,
                                   _ptr(U_out), _stream(stream)))
+
+
+def dis_search_level_ex2(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, variant, dof, norm, huber_b,
+                         u_out, uinit_out=None, status_out=None, stream=None):
+    """dis_search_level_ex with the degrees of freedom (1 stereo, 2 flow) and the error norm
+    (0 L2, 1 L1, 2 Huber with threshold huber_b)."""
+    _check(_lib.dis_search_level_ex2(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(Uc), wc, hc, cscale, ps, stride, iters,
+                                     variant, dof, NORMS.get(norm, norm), huber_b, _ptr(u_out), _ptr(uinit_out),
+                                     _ptr(status_out), _stream(stream)))
+
+
+def dis_refine_level_ex(handle, I0, I1, w, h, pitch, channels, U, outer, inner, delta=5.0, gamma=10.0, alpha=10.0,
+                        omega=1.6, dof=2, stream=None):
+    """dis_refine_level with the degrees of freedom (1: stereo, v kept)."""
+    _check(_lib.dis_refine_level_ex(handle, _ptr(I0), _ptr(I1), w, h, pitch, channels, _ptr(U), outer, inner, delta,
+                                    gamma, alpha, omega, dof, _stream(stream)), handle)
 
 
 def dis_refine_level(handle, I0, I1, w, h, pitch, channels, U, outer, inner, delta=5.0, gamma=10.0, alpha=10.0,

@@ -51,7 +51,8 @@ def translation_pair(seed, width=128, height=96, t=(2.3, -1.7), sigma=2.0):
     return I0.astype(np.float32), I1.astype(np.float32), gt
 
 
-def layered_pair(seed, width=1024, height=436, n_ellipses=20, max_disp=40.0, channels=1, rotation_deg=0.0):
+def layered_pair(seed, width=1024, height=436, n_ellipses=20, max_disp=40.0, channels=1, rotation_deg=0.0,
+                 horizontal=False):
     """Layered scene: a multi-octave noise background under `n_ellipses` textured ellipses.
 
     Motion: background affine about the image centre (|A - I| <= 0.02, translation up to
@@ -61,7 +62,10 @@ def layered_pair(seed, width=1024, height=436, n_ellipses=20, max_disp=40.0, cha
     motion uncovers show the background texture that frame 0 hid, i.e. fresh noise of the
     same spectrum.  Sizes scale with width / 1024.  Ground truth: the motion of the layer
     visible in frame 0.  channels = 3 draws an independent texture per channel over the
-    shared geometry.  Returns (I0, I1, gt)."""
+    shared geometry.  horizontal = True: a rectified stereo pair, every motion horizontal (the
+    vertical components of the affine map, the background translation and the ellipse
+    translations are zeroed after the same draws; no rotation), so gt[..., 1] == 0.
+    Returns (I0, I1, gt)."""
     g = rng(seed)
     scale = width / 1024.0
     cx, cy = 0.5 * (width - 1), 0.5 * (height - 1)
@@ -69,6 +73,12 @@ def layered_pair(seed, width=1024, height=436, n_ellipses=20, max_disp=40.0, cha
     A = np.eye(2) + E
     r_bg, a_bg = (max_disp / 4.0) * math.sqrt(g.uniform()), g.uniform(0, 2 * math.pi)
     t_bg = np.array([r_bg * math.cos(a_bg), r_bg * math.sin(a_bg)])
+    if horizontal:
+        if rotation_deg:
+            raise ValueError("a stereo pair has no rotation")
+        E[1] = 0.0
+        A = np.eye(2) + E
+        t_bg[1] = 0.0
     ell = []
     for _ in range(n_ellipses):
         ax = g.uniform(20, 150) * scale
@@ -76,7 +86,7 @@ def layered_pair(seed, width=1024, height=436, n_ellipses=20, max_disp=40.0, cha
         ang = g.uniform(0, math.pi)
         ex, ey = g.uniform(0, width), g.uniform(0, height)
         r, a = max_disp * math.sqrt(g.uniform()), g.uniform(0, 2 * math.pi)
-        ell.append((ex, ey, ax, bx, ang, r * math.cos(a), r * math.sin(a)))
+        ell.append((ex, ey, ax, bx, ang, r * math.cos(a), 0.0 if horizontal else r * math.sin(a)))
     th = math.radians(rotation_deg)
     R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
     Rinv = R.T
@@ -146,7 +156,8 @@ def mixed_resolutions(seed, n):
 
 
 _WORKLOADS = {"translate128x96": (0, 1), "layered1024x436": (1000, 1), "mixed": (2000, 64),
-              "layered512x256": (3000, 8), "rgb3840x2160": (4000, 4)}
+              "layered512x256": (3000, 8), "rgb3840x2160": (4000, 4), "stereo320x240": (5000, 4),
+              "stereo1440x960": (6000, 8)}
 
 
 def workload_pair(name, i, n=None, base_seed=None):
@@ -166,6 +177,10 @@ def workload_pair(name, i, n=None, base_seed=None):
         return layered_pair(s, width=512, height=256, max_disp=20.0)
     if name == "rgb3840x2160":
         return layered_pair(s, width=3840, height=2160, max_disp=100.0, channels=3, rotation_deg=2.0)
+    if name == "stereo320x240":
+        return layered_pair(s, width=320, height=240, n_ellipses=8, max_disp=12.0, horizontal=True)
+    if name == "stereo1440x960":
+        return layered_pair(s, width=1440, height=960, max_disp=96.0, horizontal=True)
     raise KeyError(name)
 
 
@@ -177,6 +192,9 @@ def workload_pairs(name, n=None, base_seed=None):
     'mixed'                : layered_pair at mixed resolutions, displacements 4 % of width
     'layered512x256'       : layered_pair 512x256 (displacements scaled with width)
     'rgb3840x2160'         : layered_pair RGB 3840x2160, 2 degree rotation, up to 200 px total
+    'stereo320x240'        : horizontal layered_pair 320x240, 8 ellipses, disparities up to 12 px
+    'stereo1440x960'       : horizontal layered_pair 1440x960, disparities up to 96 px (the size
+                             and disparity range of half-resolution Middlebury pairs)
     """
     n = _WORKLOADS[name][1] if n is None else n
     return [workload_pair(name, i, n, base_seed) for i in range(n)]
