@@ -12,6 +12,12 @@ write) between timed steps, outside the timed events.
 --impl reference times the FP64 CPU oracle (the correctness reference of this repository)
 on the host cores instead, on a bounded sample of the same workload.
 
+--workload stereo measures depth from stereo instead (supplementary, depth from stereo):
+rectified synthetic pairs of 1440x960 (half-resolution Middlebury size, disparities up to
+96 px), the dense preset with one degree of freedom and theta_it halved, batches of 8.
+--norm l1 / huber runs the patch search with that robust error norm (supplementary, robust
+error norms).
+
 Multi-GPU (torchrun): frame pairs are independent, so each rank runs its own batch
 (replicas, weak scaling, no collective on the data path); value = all ranks' pairs / max time.
 """
@@ -29,14 +35,33 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "DIS flow frame-pairs/s at 1024x436 (batched)"
 UNIT = "frame-pairs/s"
-W, H = 1024, 436
+# name -> (metric, width, height, default preset, default batch, theta_ss, workload text)
+WORKLOADS = {
+    "flow": ("DIS flow frame-pairs/s at 1024x436 (batched)", 1024, 436, "dense", 32, 4, "layered 1024x436"),
+    "stereo": ("DIS stereo frame-pairs/s at 1440x960 (batched)", 1440, 960, "stereo_dense", 8, 5,
+               "rectified stereo 1440x960 (horizontal layered scenes, disparities up to 96 px)"),
+}
+NORM_CODES = {"l2": 0, "l1": 1, "huber": 2}
 
 
-def preset_params(dis, name):
-    # five pyramid levels (theta_ss = 4) as in the 1024x436 workload
-    return dis.dis_default_params(name, coarsest_scale=4)
+def workload_pair(workload, k):
+    from paper_1603_03590_gb300 import synth
+    if workload == "stereo":
+        return synth.workload_pair("stereo1440x960", k)
+    return synth.layered_pair(1000 + k)
+
+
+def preset_params(dis, name, workload="flow", norm="l2"):
+    # theta_ss fixed per workload (five levels at 1024x436, six at 1440x960: the automatic value)
+    return dis.dis_default_params(name, coarsest_scale=WORKLOADS[workload][5], norm=NORM_CODES[norm])
+
+
+def search_form(p, lanes):
+    if p.dof == 1 or p.norm != 0:
+        return "grouped search, %s%s" % ("one degree of freedom" if p.dof == 1 else "flow",
+                                         "" if p.norm == 0 else ", %s norm" % ["l2", "l1", "huber"][p.norm])
+    return "search variant %d" % lanes
 
 
 def launches_per_call(dis, p, width, height, lanes, batch, refine_form=1):
@@ -83,7 +108,9 @@ def algorithmic_bytes(dis, p, width, height):
 
 def search_flops(dis, p, width, height):
     """Algorithmic FP32 operations of the inverse search of level theta_sf: 12 per bilinear
-    sample (3 lerps as sub+FMA, mean accumulation, residual, two FMA accumulations)."""
+    sample (3 lerps as sub+FMA, mean accumulation, residual, two FMA accumulations), 11 with one
+    degree of freedom (one accumulation); the robust norms' error transform (a square root) is
+    not counted."""
     ss, sf, _ = dis.dis_levels(width, height, p)
     w, h = width, height
     for _ in range(sf):
@@ -91,7 +118,7 @@ def search_flops(dis, p, width, height):
     ps = p.patch_size
     stride = p.stride_override or max(1, ps - int(np.floor(p.overlap * ps + 1e-4)))
     n = ((w - ps + stride - 1) // stride + 1) * ((h - ps + stride - 1) // stride + 1)
-    return n * p.grad_iters * ps * ps * 12, (w, h), n
+    return n * p.grad_iters * ps * ps * (12 if p.dof == 2 else 11), (w, h), n
 
 
 class Clocks:
@@ -124,48 +151,63 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(preset, seconds_hint=True):
-    """FP64 oracle on one pair of the workload cropped to 512x218 (a quarter of the area; the
-    method's cost is linear in area), scaled to pairs/s at 1024x436."""
+def cpu_baseline(preset, workload="flow", norm="l2"):
+    """FP64 oracle on one pair of the workload at half width and height (a quarter of the area,
+    one level fewer; the method's cost is linear in area), scaled to pairs/s at full size."""
     import oracle
     from paper_1603_03590_gb300 import synth
-    I0, I1, _ = synth.layered_pair(1000, width=512, height=218, max_disp=20.0)
+    _, W, H, _, _, ss, _ = WORKLOADS[workload]
+    w, h = W // 2, H // 2
+    I0, I1, _ = synth.layered_pair(1000, width=w, height=h, max_disp=20.0 if workload == "flow" else 48.0,
+                                   horizontal=workload == "stereo")
     from paper_1603_03590_gb300 import dis
-    p = preset_params(dis, preset)
+    p = preset_params(dis, preset, workload, norm)
     q = oracle.params(patch_size=p.patch_size, overlap=round(float(p.overlap), 6), grad_iters=p.grad_iters,
-                      coarsest_scale=3, finest_scale=p.finest_scale, refine=p.refine)
+                      coarsest_scale=ss - 1, finest_scale=p.finest_scale, refine=p.refine, dof=p.dof, norm=p.norm,
+                      huber_b=round(float(p.huber_b), 6))
     oracle.build()
     t = time.perf_counter()
     oracle.dis_flow(I0, I1, q)
     dt = time.perf_counter() - t
     return {"value": 0.25 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one 512x218 pair (1/4 of the 1024x436 area, one level fewer), %s preset, %.1f s; "
-                      "scaled by area to pairs/s at 1024x436" % (preset, dt)}
+            "sample": "one %dx%d pair (1/4 of the %dx%d area, one level fewer), %s preset, %.1f s; "
+                      "scaled by area to pairs/s at %dx%d" % (w, h, W, H, preset, dt, W, H)}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     steps, warmup = args.steps, args.warmup
+    metric, W, H, _, _, ss, wtext = WORKLOADS[args.workload]
     times = []
     for k in range(warmup + steps):
-        r = cpu_baseline(args.preset)
+        r = cpu_baseline(args.preset, args.workload, args.norm)
         if k >= warmup:
             times.append(0.25 / r["value"])
     dt = sum(times)
     value = steps * 0.25 / dt
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": warmup, "ms_per_step": 1000.0 * args.batch / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "layered 1024x436, %s preset, 5 levels, batch %d per GPU" % (args.preset, args.batch),
-                       "batch_per_gpu": args.batch, "preset": args.preset,
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": workload_config(args, args.batch, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step one 512x218 pair of the workload (1/4 of the area, one level "
-                                       "fewer), scaled by area to pairs/s at 1024x436; the batch's other pairs "
-                                       "would cost the same each"},
+                             "sample": "per step one %dx%d pair of the workload (1/4 of the area, one level "
+                                       "fewer), scaled by area to pairs/s at %dx%d; the batch's other pairs "
+                                       "would cost the same each" % (W // 2, H // 2, W, H)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def workload_config(args, batch, world):
+    _, W, H, _, _, ss, wtext = WORKLOADS[args.workload]
+    text = "%s, %s preset, %d levels, batch %d per GPU" % (wtext, args.preset, ss + 1, batch)
+    if args.norm != "l2":
+        text += ", %s search norm" % args.norm
+    c = {"workload": text, "batch_per_gpu": batch, "preset": args.preset,
+         "parallelism": "replicas" if world > 1 else "single"}
+    if args.norm != "l2":
+        c["norm"] = args.norm
+    return c
 
 
 def main():
@@ -174,8 +216,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--preset", default="dense")
-    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--workload", default="flow", choices=sorted(WORKLOADS))
+    ap.add_argument("--norm", default="l2", choices=sorted(NORM_CODES))
+    ap.add_argument("--preset", default=None, help="default: dense (flow), stereo_dense (stereo)")
+    ap.add_argument("--batch", type=int, default=None, help="default: 32 (flow), 8 (stereo)")
     ap.add_argument("--unique", type=int, default=4, help="distinct synthetic pairs cycled through the batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=None,
@@ -183,6 +227,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    metric, W, H, dpreset, dbatch, _, _ = WORKLOADS[args.workload]
+    args.preset = args.preset or dpreset
+    args.batch = args.batch or dbatch
 
     from paper_1603_03590_gb300 import replicas
     rank, local, world = replicas.env_rank_world()
@@ -200,8 +247,8 @@ def main():
     barrier = replicas.barrier
 
     B = args.batch
-    uniq = [synth.layered_pair(1000 + k) for k in range(args.unique)]
-    p = preset_params(dis, args.preset)
+    uniq = [workload_pair(args.workload, k) for k in range(args.unique)]
+    p = preset_params(dis, args.preset, args.workload, args.norm)
     h = dis.dis_create(W, H, B, 1)
     I0d = [torch.from_numpy(uniq[k % len(uniq)][0]).to(dev) for k in range(B)]
     I1d = [torch.from_numpy(uniq[k % len(uniq)][1]).to(dev) for k in range(B)]
@@ -323,38 +370,41 @@ def main():
     e2e = replicas.aggregate_rate(B * e2e_steps, world, ms_e / 1000.0)
     abytes = algorithmic_bytes(dis, p, W, H)
     achieved = flops * B / (k_ms / 1000.0) / 1e12
+    config = workload_config(args, B, world)
+    config.update({"l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                   "search_variant": lanes, "refine_launch_form": refine_form,
+                   "tuning": "pinned search variant" if args.variant is not None else "autotuned"})
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "layered 1024x436, %s preset, 5 levels, batch %d per GPU" % (args.preset, B),
-                   "batch_per_gpu": B, "preset": args.preset, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed steps (256 MB write, outside the timed events)",
-                   "search_variant": lanes, "refine_launch_form": refine_form,
-                   "tuning": "pinned search variant" if args.variant is not None else "autotuned"},
+        "config": config,
         "plain": {"value": plain, "unit": UNIT, "ms_per_pair": ms_p / (B * plain_steps)},
         "hbm_roofline": {"algorithmic_bytes_per_pair": abytes,
                          "achieved_gbs": abytes * value / world / 1e9, "peak_gbs": hbm,
                          "frac": abytes * value / world / 1e9 / hbm},
         "roofline": {"kernel": "inverse search of level %d over the batch (%d pairs x %d patches x %d iterations, "
-                               "search variant %d), timed inside the timed steps" % (sf, B, npatch, p.grad_iters, lanes),
+                               "%s), timed inside the timed steps"
+                               % (sf, B, npatch, p.grad_iters, search_form(p, lanes)),
                      "ms_per_launch": k_ms, "launches_timed": len(probe),
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak,
                      # DRAM bytes of the same launch at 4 pairs (ncu dram__bytes_read.sum +
                      # dram__bytes_write.sum, 17.82 MB: the level images and the coarser flow,
                      # each read once), scaled by the pairs a launch processes
-                     "traffic": 17.82e6 * B / 4 if args.preset == "dense" and lanes == 16 else None,
+                     "traffic": (17.82e6 * B / 4 if args.workload == "flow" and args.preset == "dense" and lanes == 16
+                                 and p.norm == 0 else None),
                      "traffic_source": "ncu capture of the 4-pair launch, scaled by pairs (profiles/)",
                      "algorithmic_flops_per_launch": flops * B,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max},
         "stages_ms_per_step": {k: round(v, 4) for k, v in stages.items()},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_call(dis, p, W, H, lanes, B, refine_form) * args.steps,
+        "gpu_launches": launches_per_call(dis, p, W, H, lanes if p.dof == 2 and p.norm == 0 else 0, B,
+                                          refine_form) * args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.preset)
+        line["cpu_baseline"] = cpu_baseline(args.preset, args.workload, args.norm)
     print(json.dumps(line))
 
 

@@ -240,8 +240,16 @@ dis_status dis_get_tuning(const dis_handle* h, int patch_size, int* search_varia
  * a patch size outside [2, 16]. */
 int dis_search_variants(int patch_size, int* out, int cap);
 
+/* The variants of the stereo and robust-norm searches (dis_params.dof 1 or norm != 0): group
+ * widths of the grouped form (lanes per patch; 8 and 16 at 8x8, 16 and 32 at 12x12, one
+ * otherwise), the first being their default.  A handle whose variant for ps is not one of them
+ * runs these searches with the default; dis_autotune chooses among them for such params.  Same
+ * conventions as dis_search_variants. */
+int dis_search_mode_variants(int patch_size, int* out, int cap);
+
 /* Pins the search variant of handle h for patch size ps to `lanes` (one of
- * dis_search_variants(ps)), as dis_autotune would; DIS_ERR_INVALID_ARG otherwise. */
+ * dis_search_variants(ps) or dis_search_mode_variants(ps)), as dis_autotune would;
+ * DIS_ERR_INVALID_ARG otherwise. */
 dis_status dis_set_search_variant(dis_handle* h, int patch_size, int lanes);
 
 /* ---- per-stage entry points (one pyramid level; used for per-stage parity tests and by
@@ -277,8 +285,8 @@ dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, i
 
 /* dis_search_level_ex with the search's degrees of freedom and error norm (dis_params.dof, norm
  * and huber_b).  dof 1 leaves the v component of u_out at u_init; status 2 (flat) then means
- * sum S'_x^2 <= 1e-6 tr(H') / 2.  The stereo and robust-norm searches run in the grouped form
- * whatever the variant; dof 2 with norm 0 is dis_search_level_ex.  DIS_ERR_INVALID_ARG for a
+ * sum S'_x^2 <= 1e-6 tr(H') / 2.  For dof 1 or norm != 0 the variant is 0 (the default) or one
+ * of dis_search_mode_variants(ps); dof 2 with norm 0 is dis_search_level_ex.  DIS_ERR_INVALID_ARG for a
  * dof outside {1, 2}, a norm outside {0, 1, 2} or huber_b <= 0. */
 dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc,
                                 int wc, int hc, float cscale, int ps, int stride, int iters, int variant, int dof,

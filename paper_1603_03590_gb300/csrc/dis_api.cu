@@ -422,7 +422,7 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                     e = traced(DIS_LAUNCH_SEARCH, ph.s, [&] {
                         if (p.dof != 2 || p.norm != 0)
                             return dis::launch_search_mode(js, ph.total, ps, stride, p.grad_iters, p.dof, p.norm,
-                                                           p.huber_b, hd->lc, s);
+                                                           p.huber_b, lanes, hd->lc, s);
                         return dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s, lanes, lanes == 1);
                     });
                 if (e == cudaSuccess)
@@ -938,6 +938,17 @@ static bool level_args_ok(int w, int h, int64_t pitch, int ps, int stride, const
     return true;
 }
 
+// A search variant of patch size ps: one of the flow search's forms, or (mode) one of the group
+// widths of the stereo and robust-norm searches.
+static bool variant_ok(int ps, int v, bool mode)
+{
+    int opts[8];
+    const int n = mode ? dis::search_mode_options(ps, opts) : dis::search_lane_options(ps, opts);
+    for (int k = 0; k < n; ++k)
+        if (opts[k] == v) return true;
+    return false;
+}
+
 dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc,
                                 int wc, int hc, float cscale, int ps, int stride, int iters, int variant, int dof,
                                 int norm, float huber_b, float* u_out, float* uinit_out, int* status_out,
@@ -947,13 +958,8 @@ dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, 
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: bad pointer, size, pitch or grid");
     if ((dof != 1 && dof != 2) || norm < 0 || norm > 2 || !finite(huber_b) || !(huber_b > 0.0f))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: dof, norm or huber_b out of range");
-    if (variant != 0) {
-        int opts[8];
-        const int n = dis_search_variants(ps, opts, 8);
-        bool ok = false;
-        for (int k = 0; k < n; ++k) ok = ok || opts[k] == variant;
-        if (!ok) return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: not a search variant of this patch size");
-    }
+    if (variant != 0 && !variant_ok(ps, variant, dof != 2 || norm != 0))
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: not a search variant of this patch size");
     LevelJob J;
     std::memset(&J, 0, sizeof(J));
     J.S0 = I0;
@@ -974,7 +980,7 @@ dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, 
     const long long np = (long long)J.nx * J.ny;
     cudaError_t e = (dof != 2 || norm != 0)
                         ? dis::launch_search_mode(dis::single_job(J), np, ps, stride, iters, dof, norm, huber_b,
-                                                  stage_lc(), (cudaStream_t)stream)
+                                                  variant, stage_lc(), (cudaStream_t)stream)
                         : dis::launch_search(dis::single_job(J), np, ps, stride, iters, stage_lc(),
                                              (cudaStream_t)stream, variant, false);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_search_level");
@@ -1096,9 +1102,10 @@ extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n,
     dis_status vst = validate(p, verr);
     if (vst != DIS_OK) return fail(hd, vst, verr);
     int opts[8];
-    // the stereo and robust-norm searches have one form: only the refinement is tuned for them
+    // the stereo and robust-norm searches have their own (grouped) forms
     const bool flow_l2 = p->dof == 2 && p->norm == 0;
-    const int nopt = flow_l2 ? dis::search_lane_options(p->patch_size, opts) : 0;
+    const int nopt = flow_l2 ? dis::search_lane_options(p->patch_size, opts)
+                             : dis::search_mode_options(p->patch_size, opts);
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1180,17 +1187,22 @@ extern "C" int dis_search_variants(int patch_size, int* out, int cap)
     return n;
 }
 
+extern "C" int dis_search_mode_variants(int patch_size, int* out, int cap)
+{
+    if (patch_size < 2 || patch_size > kMaxPatch) return 0;
+    int opts[8];
+    const int n = dis::search_mode_options(patch_size, opts);
+    for (int k = 0; out && k < n && k < cap; ++k) out[k] = opts[k];
+    return n;
+}
+
 extern "C" dis_status dis_set_search_variant(dis_handle* hd, int patch_size, int lanes)
 {
     if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
-    int opts[8];
-    const int n = dis_search_variants(patch_size, opts, 8);
-    for (int k = 0; k < n; ++k)
-        if (opts[k] == lanes) {
-            hd->search_lanes[patch_size] = lanes;
-            return DIS_OK;
-        }
-    return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_search_variant: not a variant of this patch size");
+    if (patch_size < 2 || patch_size > kMaxPatch || !(variant_ok(patch_size, lanes, false) || variant_ok(patch_size, lanes, true)))
+        return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_search_variant: not a variant of this patch size");
+    hd->search_lanes[patch_size] = lanes;
+    return DIS_OK;
 }
 
 // ---- host helpers shared with the backward pass (dis_backward.cu) ------------------------

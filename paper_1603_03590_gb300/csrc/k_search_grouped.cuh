@@ -278,6 +278,9 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                         if (k < n) {
                             const float r = fmaf(ay, fmaf(ax, c3[m], c2[m]), fmaf(ax, c1[m], c0[m])) - mw;
                             const float ar = fabsf(r);
+                            // correctly rounded square roots: the L1 transform's slope is unbounded
+                            // at e = 0, and an approximate root's few ulp measurably move the
+                            // search of weakly textured patches
                             const float e = norm == 1 ? copysignf(sqrtf(ar), r)
                                                       : (ar < huber_b ? r : copysignf(sqrtf(fmaf(twob, ar, -b2)), r));
                             bq[0] = fmaf(GSM ? gxs[k] : gxr[GSM ? 0 : m], e, bq[0]);

@@ -6,28 +6,47 @@ namespace dis {
 
 template <int DOF, bool ROBUST>
 static cudaError_t launch_mode(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int norm,
-                               float huber_b, const LaunchCfg& lc, cudaStream_t s)
+                               float huber_b, int lanes, const LaunchCfg& lc, cudaStream_t s)
 {
     // the robust form keeps four coefficients per pixel in registers: fewer resident blocks
-    // (chosen so that nothing spills)
+    // (chosen so that nothing spills); wider groups hold fewer pixels per lane
     constexpr int MB8 = ROBUST ? (DOF == 1 ? 3 : 4) : 6, MB12 = ROBUST ? (DOF == 1 ? 2 : 3) : 5;
-    if (ps == 8) return launch_lp<8, 8, 8, MB8, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
-    if (ps == 12)
+    constexpr int MBW = ROBUST ? (DOF == 1 ? 4 : 5) : 6;
+    if (ps == 8) {
+        if (lanes == 16)
+            return launch_lp<16, 4, 8, MBW, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
+        return launch_lp<8, 8, 8, MB8, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
+    }
+    if (ps == 12) {
+        if (lanes == 32)
+            return launch_lp<32, 5, 12, MBW, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
         return launch_lp<16, 9, 12, MB12, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
+    }
     if (ps < 8) return launch_lp<8, 7, 0, 4, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
     return launch_lp<16, 16, 0, 2, true, DOF, ROBUST>(js, total, ps, stride, iters, lc, s, norm, huber_b);
 }
 
 cudaError_t launch_search_mode(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int dof,
-                               int norm, float huber_b, const LaunchCfg& lc, cudaStream_t s)
+                               int norm, float huber_b, int lanes, const LaunchCfg& lc, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
     if (norm == 0) {
-        if (dof == 1) return launch_mode<1, false>(js, total, ps, stride, iters, 0, 0.0f, lc, s);
+        if (dof == 1) return launch_mode<1, false>(js, total, ps, stride, iters, 0, 0.0f, lanes, lc, s);
         return cudaErrorInvalidValue;  // the flow search with the L2 norm is launch_search
     }
-    if (dof == 1) return launch_mode<1, true>(js, total, ps, stride, iters, norm, huber_b, lc, s);
-    return launch_mode<2, true>(js, total, ps, stride, iters, norm, huber_b, lc, s);
+    if (dof == 1) return launch_mode<1, true>(js, total, ps, stride, iters, norm, huber_b, lanes, lc, s);
+    return launch_mode<2, true>(js, total, ps, stride, iters, norm, huber_b, lanes, lc, s);
+}
+
+int search_mode_options(int ps, int* out)
+{
+    if (ps == 8 || ps == 12) {
+        out[0] = ps == 8 ? 8 : 16;
+        out[1] = ps == 8 ? 16 : 32;
+        return 2;
+    }
+    out[0] = ps < 8 ? 8 : 16;
+    return 1;
 }
 
 }  // namespace dis

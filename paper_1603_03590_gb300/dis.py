@@ -91,6 +91,7 @@ _SIGS = {
     "dis_sobel": (_i, [_vp, _i, _i, _i64, _vp, _vp, _i64, _vp]),
     "dis_search_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dis_search_level_ex": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "dis_search_mode_variants": (_i, [_i, _vp, _i]),
     "dis_search_level_ex2": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _i, _f, _vp, _vp, _vp,
                                   _vp]),
     "dis_refine_level_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _i, _vp]),
@@ -256,6 +257,13 @@ def dis_search_variants(patch_size):
     """Lanes-per-patch variants of the search for this patch size (the default first)."""
     out = (_i * 8)()
     n = _lib.dis_search_variants(patch_size, out, 8)
+    return [out[k] for k in range(n)]
+
+
+def dis_search_mode_variants(patch_size):
+    """Group widths of the stereo and robust-norm searches for this patch size (default first)."""
+    out = (_i * 8)()
+    n = _lib.dis_search_mode_variants(patch_size, out, 8)
     return [out[k] for k in range(n)]
 
 

@@ -81,36 +81,42 @@ def test_search_modes_stage(env, case):
     Uc = torch.from_numpy(Uc_h).to(dev)
     nx, ny = oracle.grid_n(W, ps, stride), oracle.grid_n(H, ps, stride)
     A, B = host(a, W), host(b, W)
+    widths = dis.dis_search_mode_variants(ps)
+    assert widths
     for dof, norm, hb in MODES:
         refs = None
-        # the variant is ignored by these searches: every value gives the same result
-        outs = []
-        for variant in [0] + dis.dis_search_variants(ps)[:1]:
+        outs = {}
+        # variant 0 is the first width; every width is compared with the oracle
+        for variant in [0] + widths:
             u = torch.zeros((ny * nx, 2), device=dev)
             ui = torch.zeros((ny * nx, 2), device=dev)
             st = torch.zeros(ny * nx, dtype=torch.int32, device=dev)
             dis.dis_search_level_ex2(a, b, W, H, pitch, Uc, wc, hc, 2.0, ps, stride, iters, variant, dof, norm, hb,
                                      u, ui, st)
             torch.cuda.synchronize()
-            outs.append((host(u), host(ui), st.cpu().numpy()))
-        for o in outs[1:]:
-            assert all(np.array_equal(x, y) for x, y in zip(o, outs[0]))
-        u_g, ui_g, st_g = outs[0]
-        if dof == 1:
-            assert np.array_equal(u_g[:, 1], ui_g[:, 1])
-        mode = dict(dof=dof, norm=norm, huber_b=hb)
-        e, ndiff, refs = compare_search(A, B, Uc_h.astype(np.float64), 2.0, ps, stride, iters, u_g, ui_g, st_g,
-                                        refs, mode=mode)
-        nflat = int((st_g == 2).sum())
-        print("search %s dof %d norm %d b %.1f: %d patches (%d flat), max |du| %.2e, %s"
-              % (case, dof, norm, hb, nx * ny, nflat, e, ndiff))
-        assert e <= STAGE_TOL
-        if case == "stripes":
-            assert nflat > 0  # the right half is flat
+            outs[variant] = (host(u), host(ui), st.cpu().numpy())
+        assert all(np.array_equal(x, y) for x, y in zip(outs[0], outs[widths[0]]))
+        for variant in widths:
+            u_g, ui_g, st_g = outs[variant]
+            if dof == 1:
+                assert np.array_equal(u_g[:, 1], ui_g[:, 1])
+            mode = dict(dof=dof, norm=norm, huber_b=hb)
+            e, ndiff, refs = compare_search(A, B, Uc_h.astype(np.float64), 2.0, ps, stride, iters, u_g, ui_g, st_g,
+                                            refs, mode=mode)
+            nflat = int((st_g == 2).sum())
+            print("search %s dof %d norm %d b %.1f width %d: %d patches (%d flat), max |du| %.2e, %s"
+                  % (case, dof, norm, hb, variant, nx * ny, nflat, e, ndiff))
+            assert e <= STAGE_TOL
+            if case == "stripes":
+                assert nflat > 0  # the right half is flat
     u = torch.zeros((ny * nx, 2), device=dev)
     for bad in [(3, 0, 5.0), (0, 0, 5.0), (2, 3, 5.0), (2, 2, 0.0), (2, 2, float("nan"))]:
         with pytest.raises(dis.DisError):
             dis.dis_search_level_ex2(a, b, W, H, pitch, Uc, wc, hc, 2.0, ps, stride, iters, 0, *bad, u)
+    not_mode = [v for v in dis.dis_search_variants(ps) if v not in widths]
+    if not_mode:  # a flow-only form (lane per patch, cooperative) is not a variant of these searches
+        with pytest.raises(dis.DisError):
+            dis.dis_search_level_ex2(a, b, W, H, pitch, Uc, wc, hc, 2.0, ps, stride, iters, not_mode[0], 1, 0, 5.0, u)
 
 
 @pytest.mark.parametrize("case", ["stereo", "ragged", "tiny"])
@@ -155,7 +161,9 @@ def test_refine_stereo_stage(env, case):
 
 
 def run_batched(torch, dis, dev, pairs, p):
-    """One batched call over `pairs` ((I0, I1) host arrays); returns host flows."""
+    """One autotuned batched call over `pairs` ((I0, I1) host arrays), then single-pair calls of
+    the same pairs on the same handle (the same tuned forms); returns both lists of host flows
+    and the tuned search variant."""
     W = max(a.shape[-1] for a, _ in pairs)
     H = max(a.shape[-2] for a, _ in pairs)
     C = 1 if pairs[0][0].ndim == 2 else 3
@@ -164,10 +172,19 @@ def run_batched(torch, dis, dev, pairs, p):
         dp = [(to_dev(torch, a, dev), to_dev(torch, b, dev)) for a, b in pairs]
         flows = [torch.full((a.shape[-2], a.shape[-1], 2), float("nan"), device=dev) for a, _ in pairs]
         items = [(x, y, a.shape[-1], a.shape[-2], a.shape[-1], f) for (x, y), (a, _), f in zip(dp, pairs, flows)]
-        dis.dis_autotune(h, dis.make_pairs(items), len(items), p)
-        dis.dis_compute_flow_batched(h, dis.make_pairs(items), len(items), p)
+        arr = dis.make_pairs(items)
+        variant = dis.dis_autotune(h, arr, len(items), p)
+        assert variant in dis.dis_search_mode_variants(p.patch_size)
+        dis.dis_compute_flow_batched(h, arr, len(items), p)
         torch.cuda.synchronize()
-        return [host(f) for f in flows]
+        batched = [host(f) for f in flows]
+        single = []
+        for (x, y), (a, _) in zip(dp, pairs):
+            f = torch.full((a.shape[-2], a.shape[-1], 2), float("nan"), device=dev)
+            dis.dis_compute_flow(h, x, y, a.shape[-1], a.shape[-2], a.shape[-1], p, f)
+            torch.cuda.synchronize()
+            single.append(host(f))
+        return batched, single, variant
     finally:
         dis.dis_destroy(h)
 
@@ -179,13 +196,14 @@ def test_e2e_stereo(env, preset):
     base = dis.dis_default_params(preset.replace("stereo_", ""))
     assert p.dof == 1 and p.grad_iters == base.grad_iters // 2
     pairs = [synth.workload_pair("stereo320x240", i) for i in range(3)]
-    batched = run_batched(torch, dis, dev, [(a, b) for a, b, _ in pairs], p)
+    batched, single, variant = run_batched(torch, dis, dev, [(a, b) for a, b, _ in pairs], p)
     for k, (I0, I1, gt) in enumerate(pairs):
-        got, _ = run_gpu(torch, dis, dev, I0, I1, p)
-        assert np.array_equal(got, batched[k])
+        got = batched[k]
+        assert np.array_equal(got, single[k])
         assert (got[..., 1] == 0.0).all()
         if k == 0:
-            check_e2e("stereo320x240-%s" % preset, got, oracle_e2e(I0, I1, oracle_params(p)), gt)
+            check_e2e("stereo320x240-%s (width %d)" % (preset, variant), got,
+                      oracle_e2e(I0, I1, oracle_params(p)), gt)
 
 
 def test_differentiable_form_refuses_stereo(env):
@@ -216,12 +234,12 @@ def test_e2e_robust_norms(env, norm, hb):
     torch, dis, dev = env
     p = dis.dis_default_params("medium", norm=norm, huber_b=hb)
     pairs = [synth.layered_pair(2100 + i, width=320, height=240, max_disp=12.8) for i in range(2)]
-    batched = run_batched(torch, dis, dev, [(a, b) for a, b, _ in pairs], p)
-    for k, (I0, I1, gt) in enumerate(pairs):
-        got, _ = run_gpu(torch, dis, dev, I0, I1, p)
-        assert np.array_equal(got, batched[k])
+    batched, single, variant = run_batched(torch, dis, dev, [(a, b) for a, b, _ in pairs], p)
+    for k in range(len(pairs)):
+        assert np.array_equal(single[k], batched[k])
     I0, I1, gt = pairs[0]
-    check_e2e("layered320x240-medium-%s-b%g" % (norm, hb), batched[0], oracle_e2e(I0, I1, oracle_params(p)), gt)
+    check_e2e("layered320x240-medium-%s-b%g (width %d)" % (norm, hb, variant), batched[0],
+              oracle_e2e(I0, I1, oracle_params(p)), gt)
     # the L2 flow differs: the norm reached the search
     l2, _ = run_gpu(torch, dis, dev, I0, I1, dis.dis_default_params("medium"))
     assert not np.array_equal(l2, batched[0])
