@@ -49,6 +49,7 @@ class OrParams(ctypes.Structure):
         ("dof", ctypes.c_int),
         ("norm", ctypes.c_int),
         ("huber_b", ctypes.c_double),
+        ("fb", ctypes.c_int),
     ]
 
 
@@ -56,7 +57,8 @@ def params(**kw):
     """Parameter set with the paper's defaults (Sec. 3.1) overridden by keyword."""
     d = dict(patch_size=8, overlap=0.3, stride_override=0, grad_iters=16, coarsest_scale=-1,
              finest_scale=0, refine=1, var_outer=-1, var_inner=5, delta=5.0, gamma=10.0,
-             alpha=10.0, sor_omega=1.6, intensity_scale=255.0, channels=1, dof=2, norm=0, huber_b=5.0)
+             alpha=10.0, sor_omega=1.6, intensity_scale=255.0, channels=1, dof=2, norm=0, huber_b=5.0,
+             fb=0)
     d.update(kw)
     return OrParams(**d)
 
@@ -87,6 +89,8 @@ def _load():
             "or_upsample_flow": (None, [_D, i, i, d, _D, i, i]),
             "or_total_patches": (i, [i, i, P]),
             "or_dis_flow": (i, [_D, _D, i, i, P, _D, _D, _D, _D, u64p]),
+            "or_dis_flow_fb": (i, [_D, _D, i, i, P, _D, _D, _D, _D, _D, u64p]),
+            "or_densify_level_fb": (None, [_D, _D, i, i, _D, _D, i, i, _D, i, i, d, _D]),
             "or_charbonnier_loss": (d, [_D, _D, i, i, i, _D, d, u64p]),
         }
         for name, (res, args) in sig.items():
@@ -169,6 +173,36 @@ def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen
                             iters, _p(fz), _p(u), _p(ui), st.ctypes.data_as(_I), int(dof), int(norm),
                             float(huber_b))
     return u, ui, st
+
+
+def densify_level_fb(I0, I1, u, ub, ps, stride_, Uc=None, cscale=2.0):
+    """Densification with forward-backward consistency: this direction's patch flows u (grid on
+    I0) merged with the other direction's ub (grid on I1, displacements into I0).  Returns the
+    dense field on I0's grid; the other direction's is densify_level_fb(I1, I0, ub, u, ...)."""
+    I0, I1, u, ub = _f64(I0), _f64(I1), _f64(u), _f64(ub)
+    h, w = I0.shape
+    U = np.zeros((h, w, 2))
+    wc = hc = 0
+    if Uc is not None:
+        Uc = _f64(Uc)
+        hc, wc = Uc.shape[:2]
+    _load().or_densify_level_fb(_p(I0), _p(I1), w, h, _p(u), _p(ub), ps, stride_, _p(Uc), wc, hc, float(cscale),
+                                _p(U))
+    return U
+
+
+def dis_flow_fb(I0, I1, prm):
+    """Whole method with forward-backward consistency (prm.fb is set here): returns the forward
+    and the backward flow, both (H, W, 2)."""
+    I0, I1 = _f64(I0), _f64(I1)
+    H, W = I0.shape[-2:]
+    prm.fb = 1
+    flow = np.zeros((H, W, 2))
+    flow_b = np.zeros((H, W, 2))
+    rc = _load().or_dis_flow_fb(_p(I0), _p(I1), W, H, ctypes.byref(prm), None, None, None, _p(flow), _p(flow_b), None)
+    if rc != 0:
+        raise ValueError("oracle error %d" % rc)
+    return flow, flow_b
 
 
 def densify_level(I0, I1, u, ps, stride_, Uc=None, cscale=2.0):

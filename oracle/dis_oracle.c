@@ -45,6 +45,7 @@ typedef struct or_params {
     int dof;               /* 2: optical flow; 1: horizontal displacement only (supp. depth from stereo) [R20] */
     int norm;              /* search error norm (supp. robust error norms): 0 L2, 1 L1, 2 Huber [R21] */
     double huber_b;        /* Huber threshold b on the intensity scale [R21] */
+    int fb;                /* 1: forward-backward consistency (supp. Sec. B (ii)) [R22] */
 } or_params;
 
 enum { OR_NORM_L2 = 0, OR_NORM_L1 = 1, OR_NORM_HUBER = 2 };
@@ -383,6 +384,67 @@ void or_densify_level(const double* I0, const double* I1, int w, int h, const do
         }
 }
 
+/* ---- densification with forward-backward consistency (supp. Sec. B (ii)) -----------
+ * Both directions are searched; each direction's dense field merges its own patches with the
+ * other direction's:
+ *   U(x) = (1/Z) [ sum_i lambda_i,x / max(1, |d_i(x)|) u_i  -  sum_j mu_j,x / max(1, |e_j(x)|) u'_j ],
+ *   Z = sum_i lambda_i,x / max(1, |d_i(x)|) + sum_j mu_j,x / max(1, |e_j(x)|),
+ * the first sum as in Eq. 3 over the patches i of this direction (grid on I0, displacement u_i),
+ * the second over the patches j of the other direction (grid on I1, displacement u'_j into I0).
+ * [R22] mu_j,x = 1 iff x lies in patch j moved by u'_j, i.e. p_j <= x - u'_j <= p_j + ps - 1
+ * in both coordinates (pixel centres; evaluated as x - p_j >= u'_j and x - p_j - (ps - 1) <= u'_j,
+ * the same inequalities with exact integer left sides); e_j(x) = I0(x) - I1(x - u'_j), the
+ * template of patch j sampled bilinearly at the non-integer x - u'_j (inside the patch, so no
+ * clamping is needed).  Contributions are summed patch by patch in row-major order of each grid,
+ * this direction's first.  The other direction's field is this function with the roles of
+ * (I0, u) and (I1, u') exchanged. */
+void or_densify_level_fb(const double* I0, const double* I1, int w, int h, const double* u, const double* ub,
+                         int ps, int stride, const double* Uc, int wc, int hc, double cscale, double* U)
+{
+    int nx = or_grid_n(w, ps, stride), ny = or_grid_n(h, ps, stride);
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            double nu = 0.0, nv = 0.0, Z = 0.0;
+            for (int j = 0; j < ny; j++) {
+                int py = or_grid_pos(j, h, ps, stride);
+                if (y < py || y >= py + ps) continue;
+                for (int i = 0; i < nx; i++) {
+                    int px = or_grid_pos(i, w, ps, stride);
+                    if (x < px || x >= px + ps) continue;
+                    const double* ui = u + 2 * (j * nx + i);
+                    double d = or_bilinear(I1, w, h, x + ui[0], y + ui[1]) - I0[(size_t)y * w + x];
+                    double ad = fabs(d);
+                    double wt = 1.0 / (ad > 1.0 ? ad : 1.0);
+                    nu += wt * ui[0];
+                    nv += wt * ui[1];
+                    Z += wt;
+                }
+            }
+            for (int j = 0; j < ny; j++) {
+                int py = or_grid_pos(j, h, ps, stride);
+                for (int i = 0; i < nx; i++) {
+                    int px = or_grid_pos(i, w, ps, stride);
+                    const double* uj = ub + 2 * (j * nx + i);
+                    int kx = x - px, ky = y - py;
+                    if (!(kx >= uj[0] && kx - (ps - 1) <= uj[0] && ky >= uj[1] && ky - (ps - 1) <= uj[1])) continue;
+                    double e = I0[(size_t)y * w + x] - or_bilinear(I1, w, h, x - uj[0], y - uj[1]);
+                    double ae = fabs(e);
+                    double wt = 1.0 / (ae > 1.0 ? ae : 1.0);
+                    nu -= wt * uj[0];
+                    nv -= wt * uj[1];
+                    Z += wt;
+                }
+            }
+            double* o = U + 2 * ((size_t)y * w + x);
+            if (Z > 0.0) {
+                o[0] = nu / Z;
+                o[1] = nv / Z;
+            } else {
+                init_at(Uc, wc, hc, cscale, x, y, o);
+            }
+        }
+}
+
 /* ---- variational refinement (Alg. 1 step 5, Sec. 2.3) ------------------------------
  * E(U) = int delta Psi(E_I) + gamma Psi(E_G) + alpha Psi(E_S),  Psi(a^2) = sqrt(a^2 + eps^2).
  * [R12] Discretisation: warp I1 once by U (bilinear, clamped); Ibar = (I0 + I1w)/2;
@@ -564,12 +626,15 @@ int or_total_patches(int W, int H, const or_params* p)
  * hash (optional): decision trace, see note().
  * [R1] intensities are scaled by intensity_scale; for C = 3 the search and the
  * densification use the channel mean, the refinement all channels (supp. Sec. B (i)). */
-int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_params* p, const double* init_flow,
-                const double* frozen, double* record, double* flow_out, uint64_t* hash)
+int or_dis_flow_fb(const double* I0, const double* I1, int W, int H, const or_params* p, const double* init_flow,
+                   const double* frozen, double* record, double* flow_out, double* flow_b_out, uint64_t* hash)
 {
     int C = p->channels, ss, sf;
     if (C != 1 && C != 3) return OR_ERR_INVALID;
     if ((p->dof != 1 && p->dof != 2) || p->norm < 0 || p->norm > 2 || !(p->huber_b > 0.0)) return OR_ERR_INVALID;
+    /* [R22] forward-backward consistency starts both directions from zero and replays nothing */
+    if (p->fb != 0 && p->fb != 1) return OR_ERR_INVALID;
+    if (p->fb && (init_flow || frozen || record)) return OR_ERR_INVALID;
     int rc = or_levels(W, H, p, &ss, &sf);
     if (rc != OR_OK) return rc;
     int ps = p->patch_size, stride = or_stride(ps, p->overlap, p->stride_override);
@@ -619,58 +684,77 @@ int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_param
                 or_pyr_down(P1[(s - 1) * C + c], lw[s - 1], lh[s - 1], P1[s * C + c]);
             }
     }
-    double* Uprev = NULL;
+    /* direction 0: I0 -> I1; direction 1 (forward-backward consistency): I1 -> I0 */
+    const int ndir = p->fb ? 2 : 1;
+    double* Uprev[2] = {NULL, NULL};
     int wprev = 0, hprev = 0, off = 0;
     for (int s = ss; s >= sf; s--) {
         int w = lw[s], h = lh[s];
         size_t ns = (size_t)w * h;
-        double* Ix = (double*)malloc(sizeof(double) * ns);
-        double* Iy = (double*)malloc(sizeof(double) * ns);
-        or_sobel(S0[s], w, h, Ix, Iy);
         int nx = or_grid_n(w, ps, stride), ny = or_grid_n(h, ps, stride), np = nx * ny;
-        double* u = (double*)malloc(sizeof(double) * 2 * np);
-        double* ui = (double*)malloc(sizeof(double) * 2 * np);
-        const double* Uc = Uprev;
+        const double* A[2] = {S0[s], S1[s]};
+        const double* B[2] = {S1[s], S0[s]};
+        double* u[2] = {NULL, NULL};
+        double* U[2] = {NULL, NULL};
+        const double* Uc[2] = {Uprev[0], Uprev[1]};
         int wc = wprev, hc = hprev;
         double cs = 2.0;
         if (s == ss) {
-            Uc = init_flow;
+            Uc[0] = init_flow;
+            Uc[1] = NULL;
             wc = w;
             hc = h;
             cs = 1.0;
         }
-        or_search_level(S0[s], Ix, Iy, S1[s], w, h, Uc, wc, hc, cs, ps, stride, p->grad_iters,
-                        frozen ? frozen + 2 * off : NULL, u, ui, NULL, p->dof, p->norm, p->huber_b);
-        if (record)
-            for (int k = 0; k < 2 * np; k++) record[2 * off + k] = u[k] - ui[k];
-        double* U = (double*)malloc(sizeof(double) * 2 * ns);
-        or_densify_level(S0[s], S1[s], w, h, u, ps, stride, Uc, wc, hc, cs, U);
-        if (p->refine) {
-            /* channel planes of level s, contiguous */
-            double* Q0 = (double*)malloc(sizeof(double) * ns * C);
-            double* Q1 = (double*)malloc(sizeof(double) * ns * C);
-            for (int c = 0; c < C; c++) {
-                memcpy(Q0 + ns * c, P0[s * C + c], sizeof(double) * ns);
-                memcpy(Q1 + ns * c, P1[s * C + c], sizeof(double) * ns);
-            }
-            int outer = p->var_outer < 0 ? s + 1 : p->var_outer;
-            or_refine_level(Q0, Q1, w, h, C, U, outer, p->var_inner, p->delta, p->gamma, p->alpha, p->sor_omega,
-                            p->dof);
-            free(Q0);
-            free(Q1);
+        for (int d = 0; d < ndir; d++) {
+            double* Ix = (double*)malloc(sizeof(double) * ns);
+            double* Iy = (double*)malloc(sizeof(double) * ns);
+            double* ui = (double*)malloc(sizeof(double) * 2 * np);
+            u[d] = (double*)malloc(sizeof(double) * 2 * np);
+            or_sobel(A[d], w, h, Ix, Iy);
+            or_search_level(A[d], Ix, Iy, B[d], w, h, Uc[d], wc, hc, cs, ps, stride, p->grad_iters,
+                            frozen ? frozen + 2 * off : NULL, u[d], ui, NULL, p->dof, p->norm, p->huber_b);
+            if (record && d == 0)
+                for (int k = 0; k < 2 * np; k++) record[2 * off + k] = u[d][k] - ui[k];
+            free(Ix);
+            free(Iy);
+            free(ui);
         }
-        free(Ix);
-        free(Iy);
-        free(u);
-        free(ui);
-        free(Uprev);
-        Uprev = U;
+        for (int d = 0; d < ndir; d++) {
+            U[d] = (double*)malloc(sizeof(double) * 2 * ns);
+            if (p->fb)
+                or_densify_level_fb(A[d], B[d], w, h, u[d], u[1 - d], ps, stride, Uc[d], wc, hc, cs, U[d]);
+            else
+                or_densify_level(A[d], B[d], w, h, u[d], ps, stride, Uc[d], wc, hc, cs, U[d]);
+        }
+        if (p->refine)
+            for (int d = 0; d < ndir; d++) {
+                /* channel planes of level s, contiguous; direction 1 swaps the frames */
+                double* Q0 = (double*)malloc(sizeof(double) * ns * C);
+                double* Q1 = (double*)malloc(sizeof(double) * ns * C);
+                for (int c = 0; c < C; c++) {
+                    memcpy(Q0 + ns * c, (d ? P1 : P0)[s * C + c], sizeof(double) * ns);
+                    memcpy(Q1 + ns * c, (d ? P0 : P1)[s * C + c], sizeof(double) * ns);
+                }
+                int outer = p->var_outer < 0 ? s + 1 : p->var_outer;
+                or_refine_level(Q0, Q1, w, h, C, U[d], outer, p->var_inner, p->delta, p->gamma, p->alpha,
+                                p->sor_omega, p->dof);
+                free(Q0);
+                free(Q1);
+            }
+        for (int d = 0; d < ndir; d++) {
+            free(u[d]);
+            free(Uprev[d]);
+            Uprev[d] = U[d];
+        }
         wprev = w;
         hprev = h;
         off += np;
     }
-    or_upsample_flow(Uprev, wprev, hprev, (double)(1 << sf), flow_out, W, H);
-    free(Uprev);
+    if (flow_b_out && p->fb) or_upsample_flow(Uprev[1], wprev, hprev, (double)(1 << sf), flow_b_out, W, H);
+    free(Uprev[1]);
+    or_upsample_flow(Uprev[0], wprev, hprev, (double)(1 << sf), flow_out, W, H);
+    free(Uprev[0]);
     for (int s = 0; s < L; s++) {
         free(S0[s]);
         free(S1[s]);
@@ -687,6 +771,13 @@ int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_param
     free(lh);
     t_hash = NULL;
     return OR_OK;
+}
+
+/* Alg. 1 on one pair; with p->fb the backward flow is computed alongside and dropped. */
+int or_dis_flow(const double* I0, const double* I1, int W, int H, const or_params* p, const double* init_flow,
+                const double* frozen, double* record, double* flow_out, uint64_t* hash)
+{
+    return or_dis_flow_fb(I0, I1, W, H, p, init_flow, frozen, record, flow_out, NULL, hash);
 }
 
 /* Photometric loss of the differentiable form: mean over channels and pixels of the

@@ -658,3 +658,113 @@ def test_robust_search_one_step_on_centred_saddle(norm, b):
     u, _, _ = oracle.search_level(I0, gx, gy, I1, ps, 16, 1, norm=norm, huber_b=b)
     got = u.reshape(-1, 2)[_patch_index(w, ps, 16, px, py)]
     assert np.abs(got - ref).max() < 1e-12 and np.abs(got - t).max() > 1e-3
+
+
+# ---- forward-backward consistency (supplementary Sec. B (ii)) ----
+
+def _fb_brute(I0, I1, uf, ub, ps, st_):
+    """Merged forward field by the definition, pixel by pixel in Python: the forward patches
+    containing x with weight 1/max(1, |I1(x + u) - I0(x)|), the backward patches whose moved box
+    contains x with weight 1/max(1, |I0(x) - I1(x - u')|) and displacement -u'; bilinear samples
+    from scipy (edge values replicated, i.e. coordinates clamped)."""
+    h, w = I0.shape
+    nx, ny = oracle.grid_n(w, ps, st_), oracle.grid_n(h, ps, st_)
+    pos = [(oracle.grid_pos(i, w, ps, st_), oracle.grid_pos(j, h, ps, st_), j * nx + i)
+           for j in range(ny) for i in range(nx)]
+
+    def sample(img, x, y):
+        return float(ndimage.map_coordinates(img, [[y], [x]], order=1, mode="nearest")[0])
+
+    U = np.zeros((h, w, 2))
+    for y in range(h):
+        for x in range(w):
+            num, Z = np.zeros(2), 0.0
+            for px, py, k in pos:
+                if px <= x < px + ps and py <= y < py + ps:
+                    wt = 1.0 / max(1.0, abs(sample(I1, x + uf[k, 0], y + uf[k, 1]) - I0[y, x]))
+                    num += wt * uf[k]
+                    Z += wt
+            for px, py, k in pos:
+                a, b = x - ub[k, 0], y - ub[k, 1]
+                if px <= a <= px + ps - 1 and py <= b <= py + ps - 1:
+                    wt = 1.0 / max(1.0, abs(I0[y, x] - sample(I1, a, b)))
+                    num -= wt * ub[k]
+                    Z += wt
+            U[y, x] = num / Z
+    return U
+
+
+def test_fb_densify_consistent_translation_is_exact():
+    g = np.random.default_rng(41)
+    h, w, t = 30, 34, (2, -1)
+    I0 = ndimage.gaussian_filter(g.standard_normal((h, w)), 1.5) * 40 + 120
+    I1 = np.roll(np.roll(I0, t[1], axis=0), t[0], axis=1)
+    ps, st_ = 6, 3
+    n = oracle.grid_n(w, ps, st_) * oracle.grid_n(h, ps, st_)
+    uf = np.tile(np.array(t, float), (n, 1))
+    U = oracle.densify_level_fb(I0, I1, uf, -uf, ps, st_)
+    assert np.abs(U - np.array(t)).max() < 1e-12
+    Ub = oracle.densify_level_fb(I1, I0, -uf, uf, ps, st_)
+    assert np.abs(Ub + np.array(t)).max() < 1e-12
+
+
+def test_fb_densify_counts_moved_boxes_by_brute_force():
+    # equal constant frames: every weight is 1, so U(x) is the plain mean of the forward patch
+    # flows containing x and the negated backward flows whose moved box contains x; integer
+    # backward displacements (inclusive box edges) and fractional ones are mixed
+    g = np.random.default_rng(42)
+    h, w, ps, st_ = 17, 19, 5, 3
+    I0 = np.full((h, w), 80.0)
+    n = oracle.grid_n(w, ps, st_) * oracle.grid_n(h, ps, st_)
+    uf = g.uniform(-3, 3, (n, 2))
+    ub = g.uniform(-3, 3, (n, 2))
+    ub[::3] = np.round(ub[::3])
+    U = oracle.densify_level_fb(I0, I0, uf, ub, ps, st_)
+    ref = _fb_brute(I0, I0, uf, ub, ps, st_)
+    assert np.abs(U - ref).max() < 1e-12
+    # a backward patch moved by an integer covers ps x ps pixels, by a fractional amount (ps-1)^2
+    single = np.zeros((n, 2))
+    for d, cov in [((1.0, -2.0), ps * ps), ((0.5, 1.25), (ps - 1) ** 2)]:
+        ubs = single.copy()
+        k = n // 2
+        ubs[k] = d
+        ufz = np.zeros((n, 2))
+        Us = oracle.densify_level_fb(I0, I0, ufz, ubs, ps, st_)
+        assert int((Us[..., 0] != 0).sum()) == cov
+
+
+def test_fb_densify_weights_by_brute_force():
+    g = np.random.default_rng(43)
+    h, w, ps, st_ = 15, 18, 4, 2
+    I0 = ndimage.gaussian_filter(g.standard_normal((h, w)), 1.0) * 30 + 100
+    I1 = ndimage.shift(I0, (0.4, -0.7), order=3, mode="nearest") + g.normal(0, 2.0, (h, w))
+    n = oracle.grid_n(w, ps, st_) * oracle.grid_n(h, ps, st_)
+    uf = g.uniform(-2, 2, (n, 2))
+    ub = g.uniform(-2, 2, (n, 2))
+    U = oracle.densify_level_fb(I0, I1, uf, ub, ps, st_)
+    ref = _fb_brute(I0, I1, uf, ub, ps, st_)
+    assert np.abs(U - ref).max() < 1e-10
+
+
+def test_fb_pipeline_recovers_translation_both_ways_and_is_symmetric():
+    h = w = 48
+    y, x = np.mgrid[0:h, 0:w].astype(float)
+    t = (1.3, -0.7)
+    f = lambda X, Y: 0.5 * (X - 23.5) * (Y - 23.5) + 100.0  # noqa: E731
+    I0, I1 = f(x, y), f(x - t[0], y - t[1])
+    q = oracle.params(patch_size=8, stride_override=4, grad_iters=5000, coarsest_scale=1, refine=0,
+                      intensity_scale=1.0)
+    fw, bw = oracle.dis_flow_fb(I0, I1, q)
+    assert np.abs(fw[14:34, 14:34] - np.array(t)).max() < 1e-6
+    assert np.abs(bw[14:34, 14:34] + np.array(t)).max() < 1e-6
+    # the directions are interchangeable: swapping the frames swaps the two results exactly
+    g = np.random.default_rng(44)
+    A = ndimage.gaussian_filter(g.standard_normal((40, 56)), 1.5) * 0.15 + 0.5
+    B = ndimage.shift(A, (0.6, -1.2), order=3, mode="nearest")
+    q = oracle.params(patch_size=8, stride_override=4, grad_iters=12, coarsest_scale=2)
+    f1, b1 = oracle.dis_flow_fb(A, B, q)
+    f2, b2 = oracle.dis_flow_fb(B, A, q)
+    assert np.array_equal(f1, b2) and np.array_equal(b1, f2)
+    # and the consistency changes the forward flow (the backward patches entered it)
+    plain = oracle.dis_flow(A, B, oracle.params(patch_size=8, stride_override=4, grad_iters=12, coarsest_scale=2))
+    assert not np.array_equal(plain, f1) and np.abs(plain - f1).max() < 1.0
