@@ -16,7 +16,8 @@ on the host cores instead, on a bounded sample of the same workload.
 rectified synthetic pairs of 1440x960 (half-resolution Middlebury size, disparities up to
 96 px), the dense preset with one degree of freedom and theta_it halved, batches of 8.
 --norm l1 / huber runs the patch search with that robust error norm (supplementary, robust
-error norms).
+error norms).  --fb adds forward-backward consistency (supplementary Sec. B (ii)): both
+directions per pair, merged in the densification; the forward flows are the output.
 
 Multi-GPU (torchrun): frame pairs are independent, so each rank runs its own batch
 (replicas, weak scaling, no collective on the data path); value = all ranks' pairs / max time.
@@ -52,9 +53,10 @@ def workload_pair(workload, k):
     return synth.layered_pair(1000 + k)
 
 
-def preset_params(dis, name, workload="flow", norm="l2"):
+def preset_params(dis, name, workload="flow", norm="l2", fb=False):
     # theta_ss fixed per workload (five levels at 1024x436, six at 1440x960: the automatic value)
-    return dis.dis_default_params(name, coarsest_scale=WORKLOADS[workload][5], norm=NORM_CODES[norm])
+    return dis.dis_default_params(name, coarsest_scale=WORKLOADS[workload][5], norm=NORM_CODES[norm],
+                                  fb=1 if fb else 0)
 
 
 def search_form(p, lanes):
@@ -65,6 +67,7 @@ def search_form(p, lanes):
 
 
 def launches_per_call(dis, p, width, height, lanes, batch, refine_form=1):
+    # (forward-backward consistency: the densification of each level is five launches)
     """Kernels one batched call launches (mirrors the host plan: prep, pyramid, per level search
     planes (lane-per-patch search variant only) + search + densify (+ refinement: 3 setup, then
     per outer pass one fused launch, two when the level has more than 128 Ki pixels over the batch,
@@ -76,11 +79,12 @@ def launches_per_call(dis, p, width, height, lanes, batch, refine_form=1):
         w, h = (w + 1) // 2, (h + 1) // 2
         dims.append((w, h))
     n = 1 + ss
+    dirs = 2 if p.fb else 1
     for s in range(ss, sf - 1, -1):
-        n += 2 + (1 if lanes == 1 else 0)
+        n += 2 + (1 if lanes == 1 else 0) + (4 if p.fb else 0)
         if p.refine:
             outer = s + 1 if p.var_outer < 0 else p.var_outer
-            npx = batch * dims[s][0] * dims[s][1]
+            npx = dirs * batch * dims[s][0] * dims[s][1]
             fused = 0 < p.var_inner <= 5 and refine_form != 0
             chunks = 2 if refine_form == 3 or (refine_form == 1 and npx > (1 << 17)) else 1
             n += 3 + (outer * chunks if fused else outer * (1 + 2 * p.var_inner)) + 1
@@ -151,7 +155,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(preset, workload="flow", norm="l2"):
+def cpu_baseline(preset, workload="flow", norm="l2", fb=False):
     """FP64 oracle on one pair of the workload at half width and height (a quarter of the area,
     one level fewer; the method's cost is linear in area), scaled to pairs/s at full size."""
     import oracle
@@ -161,10 +165,10 @@ def cpu_baseline(preset, workload="flow", norm="l2"):
     I0, I1, _ = synth.layered_pair(1000, width=w, height=h, max_disp=20.0 if workload == "flow" else 48.0,
                                    horizontal=workload == "stereo")
     from paper_1603_03590_gb300 import dis
-    p = preset_params(dis, preset, workload, norm)
+    p = preset_params(dis, preset, workload, norm, fb)
     q = oracle.params(patch_size=p.patch_size, overlap=round(float(p.overlap), 6), grad_iters=p.grad_iters,
                       coarsest_scale=ss - 1, finest_scale=p.finest_scale, refine=p.refine, dof=p.dof, norm=p.norm,
-                      huber_b=round(float(p.huber_b), 6))
+                      huber_b=round(float(p.huber_b), 6), fb=p.fb)
     oracle.build()
     t = time.perf_counter()
     oracle.dis_flow(I0, I1, q)
@@ -181,7 +185,7 @@ def run_reference(args, rank, world):
     metric, W, H, _, _, ss, wtext = WORKLOADS[args.workload]
     times = []
     for k in range(warmup + steps):
-        r = cpu_baseline(args.preset, args.workload, args.norm)
+        r = cpu_baseline(args.preset, args.workload, args.norm, args.fb)
         if k >= warmup:
             times.append(0.25 / r["value"])
     dt = sum(times)
@@ -203,10 +207,14 @@ def workload_config(args, batch, world):
     text = "%s, %s preset, %d levels, batch %d per GPU" % (wtext, args.preset, ss + 1, batch)
     if args.norm != "l2":
         text += ", %s search norm" % args.norm
+    if args.fb:
+        text += ", forward-backward consistency"
     c = {"workload": text, "batch_per_gpu": batch, "preset": args.preset,
          "parallelism": "replicas" if world > 1 else "single"}
     if args.norm != "l2":
         c["norm"] = args.norm
+    if args.fb:
+        c["fb"] = True
     return c
 
 
@@ -218,6 +226,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="flow", choices=sorted(WORKLOADS))
     ap.add_argument("--norm", default="l2", choices=sorted(NORM_CODES))
+    ap.add_argument("--fb", action="store_true", help="forward-backward consistency")
     ap.add_argument("--preset", default=None, help="default: dense (flow), stereo_dense (stereo)")
     ap.add_argument("--batch", type=int, default=None, help="default: 32 (flow), 8 (stereo)")
     ap.add_argument("--unique", type=int, default=4, help="distinct synthetic pairs cycled through the batch")
@@ -248,8 +257,8 @@ def main():
 
     B = args.batch
     uniq = [workload_pair(args.workload, k) for k in range(args.unique)]
-    p = preset_params(dis, args.preset, args.workload, args.norm)
-    h = dis.dis_create(W, H, B, 1)
+    p = preset_params(dis, args.preset, args.workload, args.norm, args.fb)
+    h = dis.dis_create(W, H, 2 * B if args.fb else B, 1)
     I0d = [torch.from_numpy(uniq[k % len(uniq)][0]).to(dev) for k in range(B)]
     I1d = [torch.from_numpy(uniq[k % len(uniq)][1]).to(dev) for k in range(B)]
     flows = [torch.empty((H, W, 2), device=dev) for _ in range(B)]
@@ -404,7 +413,7 @@ def main():
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.preset, args.workload, args.norm)
+        line["cpu_baseline"] = cpu_baseline(args.preset, args.workload, args.norm, args.fb)
     print(json.dumps(line))
 
 

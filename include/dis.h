@@ -67,6 +67,11 @@ typedef struct dis_params {
                               * (e <- sign(e) sqrt|e|), 2 Huber (e <- e if |e| < huber_b, else
                               * sign(e) sqrt(2 huber_b |e| - huber_b^2)); e = I1(x + u) - mean - T */
     float huber_b;           /* Huber threshold on the intensity_scale scale, > 0 (5) */
+    int32_t fb;              /* 1: forward-backward consistency (supplementary Sec. B (ii)): both
+                              * directions are searched and refined, each densification merges the
+                              * other direction's patches (dis_densify_level_fb); n pairs take 2 n of
+                              * the handle's max_batch slots; no initial flow, recorded / frozen
+                              * increments or checkpoints (DIS_ERR_NOT_SUPPORTED); 0: off */
 } dis_params;
 
 /* Presets for dis_default_params.  OP1..OP4 are the paper's operating points
@@ -136,6 +141,12 @@ int64_t dis_arena_bytes(const dis_handle* h);
  * Requires w <= max_w, hgt <= max_h of the handle and p->channels == handle channels. */
 dis_status dis_compute_flow(dis_handle* h, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
                             const dis_params* p, float* flow_out, void* stream);
+
+/* dis_compute_flow with forward-backward consistency (supplementary Sec. B (ii); p->fb is
+ * taken as 1): flow_out receives the forward flow (I0 -> I1), flow_b_out (nullable) the
+ * backward flow (I1 -> I0), same layout.  Needs a handle with max_batch >= 2. */
+dis_status dis_compute_flow_fb(dis_handle* h, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                               const dis_params* p, float* flow_out, float* flow_b_out, void* stream);
 
 /* Same as dis_compute_flow, with the differentiable form's extras (not in the paper):
  *  init_flow   (nullable): replaces the zero flow above the coarsest level (Alg. 1 line 1);
@@ -298,6 +309,20 @@ dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, 
  * Uc / cscale give the fallback for uncovered pixels as in dis_search_level. */
 dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* u, int ps,
                              int stride, const float* Uc, int wc, int hc, float cscale, float* U_out, void* stream);
+
+/* Step 4 with forward-backward consistency (supplementary Sec. B (ii)): both directions' dense
+ * fields at once.  U_out (on I0's grid) merges the forward patches u (grid on I0, displacements
+ * into I1; Eq. 3) with the backward patches ub (grid on I1, displacements into I0): backward
+ * patch j gives pixel x the weight mu_j(x) / max(1, |I0(x) - I1(x - ub_j)|) (I1 bilinear) and
+ * the displacement -ub_j, mu_j(x) being its bilinear footprint moved by ub_j (the sum over its
+ * template pixels q of the bilinear weight that q + ub_j gives x: 1 inside the moved box, fading
+ * to 0 over one pixel around it).  Ub_out is the same with the roles of (I0, u) and (I1, ub) exchanged.  u, ub: nx*ny*2;
+ * U_out, Ub_out: w*h*2.  The per-tile patch lists live in the scratch of the handle's first two
+ * pair slots (max_batch >= 2, w x h within its size).  Deterministic: the other direction's
+ * contributions are summed in 64-bit fixed point. */
+dis_status dis_densify_level_fb(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
+                                const float* u, const float* ub, int ps, int stride, float* U_out, float* Ub_out,
+                                void* stream);
 
 /* Step 5 of Alg. 1 (Sec. 2.3): `outer` lagged-nonlinearity iterations of `inner` red-black
  * SOR sweeps on the intensity + gradient + smoothness energy; U (w*h*2) is refined in place.

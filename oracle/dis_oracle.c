@@ -391,20 +391,27 @@ void or_densify_level(const double* I0, const double* I1, int w, int h, const do
  *   Z = sum_i lambda_i,x / max(1, |d_i(x)|) + sum_j mu_j,x / max(1, |e_j(x)|),
  * the first sum as in Eq. 3 over the patches i of this direction (grid on I0, displacement u_i),
  * the second over the patches j of the other direction (grid on I1, displacement u'_j into I0).
- * [R22] mu_j,x = 1 iff x lies in patch j moved by u'_j, i.e. p_j <= x - u'_j <= p_j + ps - 1
- * in both coordinates (pixel centres; evaluated as x - p_j >= u'_j and x - p_j - (ps - 1) <= u'_j,
- * the same inequalities with exact integer left sides); e_j(x) = I0(x) - I1(x - u'_j), the
- * template of patch j sampled bilinearly at the non-integer x - u'_j (inside the patch, so no
- * clamping is needed).  Contributions are summed patch by patch in row-major order of each grid,
- * this direction's first.  The other direction's field is this function with the roles of
- * (I0, u) and (I1, u') exchanged. */
+ * [R22] mu_j,x is the bilinear footprint of patch j moved by u'_j ("bilinear interpolation for
+ * the second term"): every template pixel q of the patch lands at q + u'_j in I0 and spreads
+ * over its four neighbours with bilinear weights,
+ *   mu_j,x = sum_q max(0, 1 - |x - q_x - u'_x|) max(0, 1 - |y - q_y - u'_y|)
+ *          = (sum_qx max(0, 1 - |x - q_x - u'_x|)) (sum_qy max(0, 1 - |y - q_y - u'_y|)),
+ * 1 inside the moved box, fading to 0 over one pixel beyond it (an integer move covers exactly
+ * ps x ps pixels with weight 1; the weights of one patch always sum to ps^2).
+ * e_j(x) = I0(x) - I1(x - u'_j), I1 being the template's frame, sampled bilinearly (clamped).
+ * Contributions are summed patch by patch in row-major order of each grid, this direction's
+ * first.  The other direction's field is this function with the roles of (I0, u) and (I1, u')
+ * exchanged. */
 void or_densify_level_fb(const double* I0, const double* I1, int w, int h, const double* u, const double* ub,
                          int ps, int stride, const double* Uc, int wc, int hc, double cscale, double* U)
 {
     int nx = or_grid_n(w, ps, stride), ny = or_grid_n(h, ps, stride);
+    size_t n = (size_t)w * h;
+    double* acc = (double*)calloc(3 * n, sizeof(double)); /* per pixel: nu, nv, Z */
+    /* this direction's patches containing x, in row-major patch order */
     for (int y = 0; y < h; y++)
         for (int x = 0; x < w; x++) {
-            double nu = 0.0, nv = 0.0, Z = 0.0;
+            double* a = acc + 3 * ((size_t)y * w + x);
             for (int j = 0; j < ny; j++) {
                 int py = or_grid_pos(j, h, ps, stride);
                 if (y < py || y >= py + ps) continue;
@@ -415,34 +422,60 @@ void or_densify_level_fb(const double* I0, const double* I1, int w, int h, const
                     double d = or_bilinear(I1, w, h, x + ui[0], y + ui[1]) - I0[(size_t)y * w + x];
                     double ad = fabs(d);
                     double wt = 1.0 / (ad > 1.0 ? ad : 1.0);
-                    nu += wt * ui[0];
-                    nv += wt * ui[1];
-                    Z += wt;
+                    a[0] += wt * ui[0];
+                    a[1] += wt * ui[1];
+                    a[2] += wt;
                 }
             }
-            for (int j = 0; j < ny; j++) {
-                int py = or_grid_pos(j, h, ps, stride);
-                for (int i = 0; i < nx; i++) {
-                    int px = or_grid_pos(i, w, ps, stride);
-                    const double* uj = ub + 2 * (j * nx + i);
-                    int kx = x - px, ky = y - py;
-                    if (!(kx >= uj[0] && kx - (ps - 1) <= uj[0] && ky >= uj[1] && ky - (ps - 1) <= uj[1])) continue;
+        }
+    /* then the other direction's patches, in row-major patch order: each visits the pixels its
+     * footprint can reach (so every pixel still receives these contributions in patch order) */
+    for (int j = 0; j < ny; j++) {
+        int py = or_grid_pos(j, h, ps, stride);
+        for (int i = 0; i < nx; i++) {
+            int px = or_grid_pos(i, w, ps, stride);
+            const double* uj = ub + 2 * (j * nx + i);
+            if (!(fabs(uj[0]) < 1e6 && fabs(uj[1]) < 1e6)) continue; /* no frame reaches that far */
+            int cx = px + (int)floor(uj[0]), cy = py + (int)floor(uj[1]);
+            for (int y = cy - 1; y <= cy + ps + 1; y++) {
+                if (y < 0 || y >= h) continue;
+                double ly = 0.0;
+                for (int qy = py; qy < py + ps; qy++) {
+                    double t = 1.0 - fabs(y - qy - uj[1]);
+                    if (t > 0.0) ly += t;
+                }
+                if (ly <= 0.0) continue;
+                for (int x = cx - 1; x <= cx + ps + 1; x++) {
+                    if (x < 0 || x >= w) continue;
+                    double lx = 0.0;
+                    for (int qx = px; qx < px + ps; qx++) {
+                        double t = 1.0 - fabs(x - qx - uj[0]);
+                        if (t > 0.0) lx += t;
+                    }
+                    if (lx <= 0.0) continue;
                     double e = I0[(size_t)y * w + x] - or_bilinear(I1, w, h, x - uj[0], y - uj[1]);
                     double ae = fabs(e);
-                    double wt = 1.0 / (ae > 1.0 ? ae : 1.0);
-                    nu -= wt * uj[0];
-                    nv -= wt * uj[1];
-                    Z += wt;
+                    double wt = lx * ly / (ae > 1.0 ? ae : 1.0);
+                    double* a = acc + 3 * ((size_t)y * w + x);
+                    a[0] -= wt * uj[0];
+                    a[1] -= wt * uj[1];
+                    a[2] += wt;
                 }
             }
+        }
+    }
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            const double* a = acc + 3 * ((size_t)y * w + x);
             double* o = U + 2 * ((size_t)y * w + x);
-            if (Z > 0.0) {
-                o[0] = nu / Z;
-                o[1] = nv / Z;
+            if (a[2] > 0.0) {
+                o[0] = a[0] / a[2];
+                o[1] = a[1] / a[2];
             } else {
                 init_at(Uc, wc, hc, cscale, x, y, o);
             }
         }
+    free(acc);
 }
 
 /* ---- variational refinement (Alg. 1 step 5, Sec. 2.3) ------------------------------

@@ -95,6 +95,10 @@ dis_status validate(const dis_params* p, std::string& err)
         err = "norm must be 0 (L2), 1 (L1) or 2 (Huber), huber_b finite and > 0";
         return DIS_ERR_INVALID_ARG;
     }
+    if (p->fb != 0 && p->fb != 1) {
+        err = "fb must be 0 or 1";
+        return DIS_ERR_INVALID_ARG;
+    }
     return DIS_OK;
 }
 
@@ -151,6 +155,7 @@ struct PairIn {
     const float* frozen;
     float* record;
     float* ckpt;
+    float* flow_b = nullptr;  // forward-backward consistency: the backward flow (nullable)
 };
 
 struct Phase {
@@ -202,6 +207,17 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     }
     const bool colour_planes = (C == 3) && refine;
     const int nplanes = colour_planes ? 2 + 2 * C : 2;
+    // forward-backward consistency: pair i's backward direction uses slot n + i (its flows,
+    // patches and scratch) and reads the forward direction's pyramid with the frames exchanged
+    const bool fb = p.fb != 0;
+    if (fb) {
+        if (2 * n > hd->max_batch)
+            return fail(hd, DIS_ERR_INVALID_ARG, "forward-backward consistency takes two pair slots per pair (2 n > max_batch)");
+        for (int i = 0; i < n; ++i)
+            if (pairs[i].init || pairs[i].frozen || pairs[i].record || pairs[i].ckpt)
+                return fail(hd, DIS_ERR_NOT_SUPPORTED,
+                            "forward-backward consistency: no initial flow, recorded or frozen increments, checkpoints");
+    }
     plan.blob.clear();
     plan.phases.clear();
     plan.copies.clear();
@@ -222,6 +238,10 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     auto Uof = [&](int i, int s) -> float2* {
         if (s == 0 && sf[i] == 0) return reinterpret_cast<float2*>(pairs[i].flow);
         return reinterpret_cast<float2*>(slot(i) + hd->off_U[s]);
+    };
+    auto Ubof = [&](int i, int s) -> float2* {  // the backward direction's flows
+        if (s == 0 && sf[i] == 0 && pairs[i].flow_b) return reinterpret_cast<float2*>(pairs[i].flow_b);
+        return reinterpret_cast<float2*>(slot(n + i) + hd->off_U[s]);
     };
 
     // level 0 preparation
@@ -251,7 +271,8 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             plan.key.push_back(w);
             plan.key.push_back(h);
             plan.key.push_back(pairs[i].pitch);
-            plan.key.push_back((pairs[i].init ? 1 : 0) | (pairs[i].frozen ? 2 : 0) | (pairs[i].record ? 4 : 0));
+            plan.key.push_back((pairs[i].init ? 1 : 0) | (pairs[i].frozen ? 2 : 0) | (pairs[i].record ? 4 : 0) |
+                               (pairs[i].flow_b ? 8 : 0));
         }
         plan.phases.push_back({Phase::PREP, push_table(plan.blob, t), n, base, 0, 0, 0});
     }
@@ -330,9 +351,48 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.pix_base = xb;
             J.half_base = hb;
             dis::set_refine_tiles(J, tb);
+            J.partner = -1;
             pb += (long long)J.nx * J.ny;
             xb += (long long)w * h;
             hb += (long long)h * ((w + 1) / 2);
+            if (fb) {
+                // the lists of this direction's tiles, in its refinement scratch (free between
+                // the search and the refinement)
+                const long long tiles = dis::refine_tiles(w, h);
+                J.fb_cnt = reinterpret_cast<int*>(J.rs);
+                J.fb_cur = J.fb_cnt + tiles;
+                J.fb_list = J.fb_cur + tiles;
+                LevelJob B = J;
+                B.S0 = J.S1;
+                B.S1 = J.S0;
+                B.P0 = J.P1;
+                B.P1 = J.P0;
+                if (s == ss[i]) {
+                    B.Uc = nullptr;
+                } else {
+                    B.Uc = Ubof(i, s + 1);
+                }
+                B.U = Ubof(i, s);
+                B.pu = reinterpret_cast<float2*>(slot(n + i) + hd->off_pu[s]);
+                B.rs = reinterpret_cast<float*>(slot(n + i) + hd->off_rs);
+                B.tpl = reinterpret_cast<const float4*>(B.rs);
+                B.tap = B.tpl + B.plane;
+                B.fb_cnt = reinterpret_cast<int*>(B.rs);
+                B.fb_cur = B.fb_cnt + tiles;
+                B.fb_list = B.fb_cur + tiles;
+                B.patch_base = pb;
+                B.pix_base = xb;
+                B.half_base = hb;
+                dis::set_refine_tiles(B, tb);
+                pb += (long long)B.nx * B.ny;
+                xb += (long long)w * h;
+                hb += (long long)h * ((w + 1) / 2);
+                J.partner = (int)t.size() + 1;
+                B.partner = (int)t.size();
+                t.push_back(J);
+                t.push_back(B);
+                continue;
+            }
             t.push_back(J);
             if (pairs[i].ckpt) {
                 long long cb = 0;
@@ -360,7 +420,22 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.base = base;
             base += (long long)J.wo * J.ho;
         }
-        plan.phases.push_back({Phase::UP, push_table(plan.blob, t), n, base, 0, 0, fsf});
+        for (int i = 0; fb && i < n; ++i) {
+            if (!pairs[i].flow_b) continue;
+            UpJob J;
+            std::memset(&J, 0, sizeof(J));
+            J.in = Ubof(i, fsf);
+            J.wi = lw(i, fsf);
+            J.hi = lh(i, fsf);
+            J.out = reinterpret_cast<float2*>(pairs[i].flow_b);
+            J.wo = pairs[i].w;
+            J.ho = pairs[i].h;
+            J.factor = (float)(1 << fsf);
+            J.base = base;
+            base += (long long)J.wo * J.ho;
+            t.push_back(J);
+        }
+        plan.phases.push_back({Phase::UP, push_table(plan.blob, t), (int)t.size(), base, 0, 0, fsf});
     }
     if (plan.blob.size() > hd->jobs_bytes) return fail(hd, DIS_ERR_INVALID_ARG, "job tables exceed the handle's job region");
     return DIS_OK;
@@ -426,8 +501,11 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                         return dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s, lanes, lanes == 1);
                     });
                 if (e == cudaSuccess)
-                    e = traced(DIS_LAUNCH_DENSIFY, ph.s,
-                               [&] { return dis::launch_densify(js, ph.total2, ps, stride, hd->lc, s); });
+                    e = traced(DIS_LAUNCH_DENSIFY, ph.s, [&] {
+                        if (p.fb)
+                            return dis::launch_densify_fb(js, ph.total, ph.total4, ph.n, ps, stride, hd->lc, s);
+                        return dis::launch_densify(js, ph.total2, ps, stride, hd->lc, s);
+                    });
                 for (const auto& c : plan.copies)
                     if (e == cudaSuccess && c.s == ph.s) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s);
                 if (e == cudaSuccess && p.refine) {
@@ -700,6 +778,23 @@ dis_status dis_compute_flow(dis_handle* hd, const float* I0, const float* I1, in
                             const dis_params* p, float* flow_out, void* stream)
 {
     return dis_compute_flow_ex(hd, I0, I1, w, hgt, pitch, p, nullptr, nullptr, nullptr, nullptr, flow_out, stream);
+}
+
+dis_status dis_compute_flow_fb(dis_handle* hd, const float* I0, const float* I1, int w, int hgt, int64_t pitch,
+                               const dis_params* p, float* flow_out, float* flow_b_out, void* stream)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    std::string e;
+    dis_status st = validate(p, e);
+    if (st != DIS_OK) return fail(hd, st, e);
+    if (p->channels != hd->C) return fail(hd, DIS_ERR_INVALID_ARG, "params.channels differs from the handle's");
+    dis_params q = *p;
+    q.fb = 1;
+    PairIn in{I0, I1, w, hgt, pitch, flow_out, nullptr, nullptr, nullptr, nullptr, flow_b_out};
+    if ((st = check_pair(hd, in, 0)) != DIS_OK) return st;
+    Plan plan;
+    if ((st = build_plan(hd, {in}, q, plan)) != DIS_OK) return st;
+    return run_plan(hd, plan, q, (cudaStream_t)stream);
 }
 
 dis_status dis_compute_flow_batched(dis_handle* hd, const dis_pair* pairs, int n, const dis_params* p, void* stream)
@@ -1000,6 +1095,58 @@ dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int6
 {
     return dis_search_level_ex(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, 0, u_out, uinit_out,
                                status_out, stream);
+}
+
+dis_status dis_densify_level_fb(dis_handle* hd, const float* I0, const float* I1, int w, int h, int64_t pitch,
+                                const float* u, const float* ub, int ps, int stride, float* U_out, float* Ub_out,
+                                void* stream)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    if (!I0 || !I1 || !u || !ub || !U_out || !Ub_out || !level_args_ok(w, h, pitch, ps, stride, nullptr, 0, 0, 1.0f))
+        return fail(hd, DIS_ERR_INVALID_ARG, "dis_densify_level_fb: bad pointer, size, pitch or grid");
+    if (hd->max_batch < 2 || w > hd->max_w || h > hd->max_h ||
+        (size_t)dis::fb_scratch_ints(w, h, ps, stride) > hd->rs_floats)
+        return fail(hd, DIS_ERR_INVALID_ARG, "dis_densify_level_fb: needs a handle of two pairs of at least w x h");
+    // two jobs, each the other's partner: the forward one on (I0, I1) with patch flows u, the
+    // backward one on (I1, I0) with ub; the lists live in the scratch of slots 0 and 1
+    LevelJob J[2];
+    for (int k = 0; k < 2; ++k) {
+        LevelJob& A = J[k];
+        std::memset(&A, 0, sizeof(A));
+        A.S0 = k ? I1 : I0;
+        A.S1 = k ? I0 : I1;
+        A.w = w;
+        A.h = h;
+        A.pitch = (int)pitch;
+        A.wc = w;
+        A.hc = h;
+        A.cscale = 1.0f;
+        A.pu = reinterpret_cast<float2*>(const_cast<float*>(k ? ub : u));
+        A.U = reinterpret_cast<float2*>(k ? Ub_out : U_out);
+        A.nx = grid_n(w, ps, stride);
+        A.ny = grid_n(h, ps, stride);
+        A.C = 1;
+        A.patch_base = (long long)k * A.nx * A.ny;
+        A.pix_base = (long long)k * w * h;
+        long long tb = (long long)k * dis::refine_tiles(w, h);
+        dis::set_refine_tiles(A, tb);
+        A.rs = reinterpret_cast<float*>(hd->arena + (size_t)k * hd->slot_bytes + hd->off_rs);
+        const long long tiles = dis::refine_tiles(w, h);
+        A.fb_cnt = reinterpret_cast<int*>(A.rs);
+        A.fb_cur = A.fb_cnt + tiles;
+        A.fb_list = A.fb_cur + tiles;
+        A.partner = 1 - k;
+    }
+    Plan plan;
+    plan.blob.resize(sizeof(J));
+    std::memcpy(plan.blob.data(), J, sizeof(J));
+    cudaStream_t s = (cudaStream_t)stream;
+    dis_status st = upload_jobs(hd, plan, s);
+    if (st != DIS_OK) return st;
+    const long long np = (long long)J[0].nx * J[0].ny;
+    cudaError_t e = dis::launch_densify_fb(dis::device_jobs(reinterpret_cast<const LevelJob*>(hd->jobs_dev), 2), 2 * np,
+                                           2 * dis::refine_tiles(w, h), 2, ps, stride, hd->lc, s);
+    return e == cudaSuccess ? DIS_OK : cuda_fail(hd, e, "dis_densify_level_fb");
 }
 
 dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* u, int ps,

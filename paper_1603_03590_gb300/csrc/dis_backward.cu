@@ -196,6 +196,7 @@ dis_status check_common(dis_handle* hd, const float* I0, const float* I1, int W,
     if (p->channels != 1) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: grayscale (channels = 1) only");
     if (p->finest_scale != 0) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: finest_scale must be 0");
     if (p->dof != 2) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: dof must be 2 (optical flow)");
+    if (p->fb) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: no forward-backward consistency");
     if (!I0 || !I1 || !frozen || !workspace || W < 1 || H < 1 || pitch < W)
         return set_fail(hd, DIS_ERR_INVALID_ARG, "differentiable form: bad pointer, size or pitch");
     if ((st = layout(W, H, *p, L, err)) != DIS_OK) return set_fail(hd, st, err);

@@ -41,6 +41,14 @@ struct LevelJob {
     float cscale;
     int nx, ny;
     int C;
+    // forward-backward consistency: the job of the other direction of the same pair (same
+    // size and grid, frames exchanged) and, in this job's refinement scratch, the lists of the
+    // other direction's patches whose moved box meets each of this job's refinement tiles:
+    // fb_cnt (counts, then offsets), fb_cur (fill cursors, then list ends), fb_list.
+    int partner;
+    int* fb_cnt;
+    int* fb_cur;
+    int* fb_list;
 };
 
 // One pyramid step of `nplanes` consecutive planes.
@@ -144,6 +152,13 @@ cudaError_t launch_search_mode(const Jobs<LevelJob>& js, long long total, int ps
                                int norm, float huber_b, int lanes, const LaunchCfg& lc, cudaStream_t s);
 // Group widths of the stereo and robust-norm searches for patch size ps (the first is the default).
 int search_mode_options(int ps, int* out);
+// Densification with forward-backward consistency over jobs that come in partner pairs: lists
+// the patches of each job by the tiles of its partner that their moved boxes meet (four
+// launches), then merges, per tile, the job's own patches with the partner's listed ones.
+cudaError_t launch_densify_fb(const Jobs<LevelJob>& js, long long total_patches, long long total_tiles, int njobs,
+                              int ps, int stride, const LaunchCfg& lc, cudaStream_t s);
+// Ints of refinement scratch the lists of one job take (at most), for a w x h level.
+long long fb_scratch_ints(int w, int h, int ps, int stride);
 cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, int stride, const LaunchCfg& lc,
                            cudaStream_t s);
 struct RefineArgs {

@@ -51,6 +51,7 @@ class dis_params(ctypes.Structure):
         ("dof", ctypes.c_int32),
         ("norm", ctypes.c_int32),
         ("huber_b", ctypes.c_float),
+        ("fb", ctypes.c_int32),
     ]
 
 
@@ -92,6 +93,8 @@ _SIGS = {
     "dis_search_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dis_search_level_ex": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "dis_search_mode_variants": (_i, [_i, _vp, _i]),
+    "dis_compute_flow_fb": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp]),
+    "dis_densify_level_fb": (_i, [_vp, _vp, _vp, _i, _i, _i64, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "dis_search_level_ex2": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _i, _f, _vp, _vp, _vp,
                                   _vp]),
     "dis_refine_level_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _i, _vp]),
@@ -171,6 +174,12 @@ def dis_arena_bytes(handle):
 def dis_compute_flow(handle, I0, I1, w, h, pitch, params, flow_out, stream=None):
     _check(_lib.dis_compute_flow(handle, _ptr(I0), _ptr(I1), w, h, pitch, ctypes.byref(params), _ptr(flow_out),
                                  _stream(stream)), handle)
+
+
+def dis_compute_flow_fb(handle, I0, I1, w, h, pitch, params, flow_out, flow_b_out=None, stream=None):
+    """Forward-backward consistency: forward flow into flow_out, backward flow into flow_b_out."""
+    _check(_lib.dis_compute_flow_fb(handle, _ptr(I0), _ptr(I1), w, h, pitch, ctypes.byref(params), _ptr(flow_out),
+                                    _ptr(flow_b_out), _stream(stream)), handle)
 
 
 def dis_compute_flow_ex(handle, I0, I1, w, h, pitch, params, init_flow, frozen_in, record_out, checkpoints,
@@ -295,6 +304,12 @@ def dis_search_level_ex(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, ite
 def dis_densify_level(I0, I1, w, h, pitch, u, ps, stride, Uc, wc, hc, cscale, U_out, stream=None):
     _check(_lib.dis_densify_level(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(u), ps, stride, _ptr(Uc), wc, hc, cscale,
                                   _ptr(U_out), _stream(stream)))
+
+
+def dis_densify_level_fb(handle, I0, I1, w, h, pitch, u, ub, ps, stride, U_out, Ub_out, stream=None):
+    """Both directions' dense fields with forward-backward consistency (handle scratch)."""
+    _check(_lib.dis_densify_level_fb(handle, _ptr(I0), _ptr(I1), w, h, pitch, _ptr(u), _ptr(ub), ps, stride,
+                                     _ptr(U_out), _ptr(Ub_out), _stream(stream)), handle)
 
 
 def dis_search_level_ex2(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, variant, dof, norm, huber_b,

@@ -310,7 +310,7 @@ def oracle_params(p):
                          refine=p.refine, var_outer=p.var_outer, var_inner=p.var_inner, delta=p.delta,
                          gamma=p.gamma, alpha=p.alpha, sor_omega=round(float(p.sor_omega), 6),
                          intensity_scale=p.intensity_scale, channels=p.channels, dof=p.dof, norm=p.norm,
-                         huber_b=round(float(p.huber_b), 6))
+                         huber_b=round(float(p.huber_b), 6), fb=p.fb)
 
 
 def oracle_e2e(I0, I1, q, **kw):

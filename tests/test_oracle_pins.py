@@ -664,9 +664,10 @@ def test_robust_search_one_step_on_centred_saddle(norm, b):
 
 def _fb_brute(I0, I1, uf, ub, ps, st_):
     """Merged forward field by the definition, pixel by pixel in Python: the forward patches
-    containing x with weight 1/max(1, |I1(x + u) - I0(x)|), the backward patches whose moved box
-    contains x with weight 1/max(1, |I0(x) - I1(x - u')|) and displacement -u'; bilinear samples
-    from scipy (edge values replicated, i.e. coordinates clamped)."""
+    containing x with weight 1/max(1, |I1(x + u) - I0(x)|); every backward patch with weight
+    mu(x)/max(1, |I0(x) - I1(x - u')|) and displacement -u', mu(x) the sum over its template
+    pixels q of the bilinear weight that q + u' gives x; bilinear samples from scipy (edge
+    values replicated, i.e. coordinates clamped)."""
     h, w = I0.shape
     nx, ny = oracle.grid_n(w, ps, st_), oracle.grid_n(h, ps, st_)
     pos = [(oracle.grid_pos(i, w, ps, st_), oracle.grid_pos(j, h, ps, st_), j * nx + i)
@@ -685,9 +686,12 @@ def _fb_brute(I0, I1, uf, ub, ps, st_):
                     num += wt * uf[k]
                     Z += wt
             for px, py, k in pos:
-                a, b = x - ub[k, 0], y - ub[k, 1]
-                if px <= a <= px + ps - 1 and py <= b <= py + ps - 1:
-                    wt = 1.0 / max(1.0, abs(I0[y, x] - sample(I1, a, b)))
+                mu = 0.0
+                for qy in range(py, py + ps):
+                    for qx in range(px, px + ps):
+                        mu += max(0.0, 1 - abs(x - qx - ub[k, 0])) * max(0.0, 1 - abs(y - qy - ub[k, 1]))
+                if mu > 0.0:
+                    wt = mu / max(1.0, abs(I0[y, x] - sample(I1, x - ub[k, 0], y - ub[k, 1])))
                     num -= wt * ub[k]
                     Z += wt
             U[y, x] = num / Z
@@ -708,10 +712,10 @@ def test_fb_densify_consistent_translation_is_exact():
     assert np.abs(Ub + np.array(t)).max() < 1e-12
 
 
-def test_fb_densify_counts_moved_boxes_by_brute_force():
-    # equal constant frames: every weight is 1, so U(x) is the plain mean of the forward patch
-    # flows containing x and the negated backward flows whose moved box contains x; integer
-    # backward displacements (inclusive box edges) and fractional ones are mixed
+def test_fb_densify_footprints_by_brute_force():
+    # equal constant frames: the error weights are 1, so U(x) is the footprint-weighted mean of
+    # the forward patch flows containing x and the negated backward flows; integer backward
+    # displacements (footprint edges on pixel centres) and fractional ones are mixed
     g = np.random.default_rng(42)
     h, w, ps, st_ = 17, 19, 5, 3
     I0 = np.full((h, w), 80.0)
@@ -722,15 +726,28 @@ def test_fb_densify_counts_moved_boxes_by_brute_force():
     U = oracle.densify_level_fb(I0, I0, uf, ub, ps, st_)
     ref = _fb_brute(I0, I0, uf, ub, ps, st_)
     assert np.abs(U - ref).max() < 1e-12
-    # a backward patch moved by an integer covers ps x ps pixels, by a fractional amount (ps-1)^2
-    single = np.zeros((n, 2))
-    for d, cov in [((1.0, -2.0), ps * ps), ((0.5, 1.25), (ps - 1) ** 2)]:
-        ubs = single.copy()
+    # a backward patch moved by an integer reaches ps x ps pixels, by a fractional amount in both
+    # coordinates (ps + 1)^2; its footprint weights sum to ps^2.  With every other patch at 0,
+    # U(x) = -d mu(x) / (n(x) + mu(x)), n(x) the number of other contributions, so mu follows.
+    for d, cov in [((1.0, -2.0), ps * ps), ((0.5, 1.25), (ps + 1) ** 2)]:
+        ubs = np.zeros((n, 2))
         k = n // 2
         ubs[k] = d
         ufz = np.zeros((n, 2))
         Us = oracle.densify_level_fb(I0, I0, ufz, ubs, ps, st_)
         assert int((Us[..., 0] != 0).sum()) == cov
+        ones = np.ones((n, 2))
+        cnt = oracle.densify_level_fb(I0, I0, ones, np.full((n, 2), -1.0), ps, st_)  # all contributions equal 1
+        assert np.abs(cnt - 1.0).max() < 1e-12
+        # n(x): forward patches containing x plus the other backward patches (moved by 0)
+        nx_, ny_ = oracle.grid_n(w, ps, st_), oracle.grid_n(h, ps, st_)
+        N = np.zeros((h, w))
+        for j in range(ny_):
+            for i in range(nx_):
+                px_, py_ = oracle.grid_pos(i, w, ps, st_), oracle.grid_pos(j, h, ps, st_)
+                N[py_:py_ + ps, px_:px_ + ps] += 2 if j * nx_ + i != k else 1
+        mu = -Us[..., 0] * N / (Us[..., 0] + d[0])
+        assert abs(mu.sum() - ps * ps) < 1e-9
 
 
 def test_fb_densify_weights_by_brute_force():
