@@ -192,32 +192,34 @@ __global__ void __launch_bounds__(1024) fb_scan_kernel(const __grid_constant__ J
     }
 }
 
-constexpr int kFbThreads = 512;  // one warp per bin
-constexpr int kFbChunk = 512;    // listed patches staged in shared memory at a time
-constexpr int kFbBin = 8;        // 8 x 8 pixel bins: 16 per tile
-constexpr int kFbStrip = kFbBin * kFbBin / (kFbThreads / 16);  // pixels per thread (a row strip)
+constexpr int kFbBin = 16;       // 16 x 16 pixel bins: 4 per tile
+constexpr int kFbThreads = 32 * (kFbTile / kFbBin) * (kFbTile / kFbBin);  // one warp per bin
+constexpr int kFbChunk = kFbThreads;  // listed patches staged in shared memory at a time
 
-// One block (512 threads) per tile of a job.  Warp b owns bin b; its lane l the 1 x 2 pixel
-// strip (2 (l & 3), l / 4) of the bin.  The partner's listed patches are staged in chunks;
-// each is entered in the bins its (tile-clipped) footprint meets, and each thread then visits
-// only its bin's patches, accumulating its pixels' contributions in 64-bit fixed point in
-// registers (the order in which patches enter a bin does not matter).
+// One block (a warp per bin) per tile of a job; warp b owns the 16 x 16 pixel bin b and its
+// accumulators.  The partner's listed patches are staged in chunks and entered in the bins their
+// (tile-clipped) footprints meet; each warp then takes its bin's patches one after another and
+// spreads the lanes over the rectangle the footprint covers in the bin, so that a lane adds to
+// one pixel's shared-memory accumulators with a plain read-modify-write (no other lane or warp
+// touches that pixel meanwhile).  Sums are 64-bit fixed point: the order in which the patches
+// enter a bin (atomic) does not change them.
 template <int SC>
-__global__ void __launch_bounds__(kFbThreads, 2) densify_fb_kernel(const __grid_constant__ Jobs<LevelJob> js,
+__global__ void __launch_bounds__(kFbThreads, 6) densify_fb_kernel(const __grid_constant__ Jobs<LevelJob> js,
                                                                    long long total, int ps, int stride)
 {
     constexpr int NB = (kFbTile / kFbBin) * (kFbTile / kFbBin);
-    constexpr int SPR = kFbBin / kFbStrip;  // strips per bin row
-    static_assert(kFbThreads / 32 == NB && SPR * kFbStrip == kFbBin, "one warp per bin, whole strips");
+    constexpr int NP = kFbTile * kFbTile;
+    static_assert(kFbThreads / 32 == NB, "one warp per bin");
     __shared__ float2 eu[kFbChunk];
     __shared__ int2 epos[kFbChunk];
     __shared__ int4 ebox[kFbChunk];  // footprint clipped to the tile, tile coordinates
     __shared__ short blist[NB][kFbChunk];
     __shared__ int bcnt[NB];
+    __shared__ long long acc[3][NP];  // fixed-point sums per tile pixel: -w u'_x, -w u'_y, w
+    __shared__ float s0[NP];          // the tile of I0
     __shared__ float red[kFbThreads / 32];
     const int bin = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx0 = (bin % (kFbTile / kFbBin)) * kFbBin, by0 = (bin / (kFbTile / kFbBin)) * kFbBin;
-    const int sx = bx0 + kFbStrip * (lane % SPR), sy = by0 + lane / SPR;  // the strip's first pixel (tile coordinates)
     for (long long g = blockIdx.x; g < total; g += gridDim.x) {
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::tile_base));
         const LevelJob& P = job_ref(js, J.partner);
@@ -226,6 +228,11 @@ __global__ void __launch_bounds__(kFbThreads, 2) densify_fb_kernel(const __grid_
         const int X0 = tx * kFbTile, Y0 = ty * kFbTile;
         const int tw = min(kFbTile, J.w - X0), th = min(kFbTile, J.h - Y0);
         const int beg = J.fb_cnt[t], L = J.fb_cur[t];  // after the fill the cursor holds the count
+        for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+            const int ly = q / kFbTile, lx = q - ly * kFbTile;
+            acc[0][q] = acc[1][q] = acc[2][q] = 0;
+            s0[q] = (lx < tw && ly < th) ? __ldg(J.S0 + (long long)(Y0 + ly) * J.pitch + X0 + lx) : 0.0f;
+        }
         // the largest |u'| of the listed patches bounds every term
         float m = 0.0f;
         for (int e = threadIdx.x; e < L; e += blockDim.x) {
@@ -234,25 +241,15 @@ __global__ void __launch_bounds__(kFbThreads, 2) densify_fb_kernel(const __grid_
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        if (lane == 0) red[bin] = m;
         __syncthreads();
         m = 0.0f;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k]);
+        for (int k = 0; k < NB; ++k) m = fmaxf(m, red[k]);
         // |w u'| <= m < 2^ex: terms scaled by 2^kn stay below 2^30 (w <= 1: 2^kz = 2^30 too), so
         // each converts to a 32-bit integer and a sum of fewer than 2^33 of them fits 64 bits
         const int ex = ((__float_as_int(m + 1.0f) >> 23) & 0xff) - 126;  // m + 1 < 2^ex (m + 1 >= 1 is normal)
         const int kn = 30 - ex, kz = 30;
         const float sn = ldexpf(1.0f, kn), sz = ldexpf(1.0f, kz);
-        // this thread's pixels
-        const int y = Y0 + sy;
-        const bool row_in = sy < th;
-        float i0[kFbStrip];
-        long long au[kFbStrip], av[kFbStrip], az[kFbStrip];
-#pragma unroll
-        for (int k = 0; k < kFbStrip; ++k) {
-            i0[k] = (row_in && sx + k < tw) ? __ldg(J.S0 + (long long)y * J.pitch + X0 + sx + k) : 0.0f;
-            au[k] = av[k] = az[k] = 0;
-        }
         for (int c0 = 0; c0 < L; c0 += kFbChunk) {
             const int nc = min(kFbChunk, L - c0);
             __syncthreads();  // the previous chunk is consumed
@@ -280,40 +277,54 @@ __global__ void __launch_bounds__(kFbThreads, 2) densify_fb_kernel(const __grid_
             for (int k = 0; k < nb; ++k) {
                 const int e = blist[bin][k];
                 const int4 b = ebox[e];
-                if (!row_in || sy < b.z || sy > b.w) continue;
+                const int rx0 = max(b.x, bx0), rx1 = min(b.y, bx0 + kFbBin - 1);
+                const int ry0 = max(b.z, by0), ry1 = min(b.w, by0 + kFbBin - 1);
+                const int rw = rx1 - rx0 + 1, n = rw * (ry1 - ry0 + 1);
+                const unsigned inv_rw = (65536u + (unsigned)rw - 1u) / (unsigned)rw;  // r / rw = (r inv_rw) >> 16 for r < 256
                 const float2 u = eu[e];
                 const int2 pc = epos[e];
-                const float ly = footprint_1d(y - pc.y, u.y, ps);
-#pragma unroll
-                for (int q = 0; q < kFbStrip; ++q) {
-                    const int lx = sx + q;
-                    if (lx < b.x || lx > b.y) continue;
-                    const int x = X0 + lx;
-                    const float d = i0[q] - sample_shift(J.S1, J.w, J.h, J.pitch, x, y, -u.x, -u.y);
-                    const float wt = footprint_1d(x - pc.x, u.x, ps) * ly * __frcp_rn(fmaxf(1.0f, fabsf(d)));
-                    au[q] += __float2int_rn((-wt * u.x) * sn);
-                    av[q] += __float2int_rn((-wt * u.y) * sn);
-                    az[q] += __float2int_rn(wt * sz);
+                // the sample I1(x - u'): the same cell offset and weights for every pixel of the patch
+                const float fu = floorf(-u.x), fv = floorf(-u.y);
+                const float ax = -u.x - fu, ay = -u.y - fv;
+                const int ox = (int)fu, oy = (int)fv;
+                const float su = (-u.x) * sn, sv = (-u.y) * sn;
+                for (int r = lane; r < n; r += 32) {
+                    const int dy = (int)(((unsigned)r * inv_rw) >> 16);
+                    const int lx = rx0 + (r - dy * rw), ly = ry0 + dy;
+                    const int x = X0 + lx, y = Y0 + ly, a = ly * kFbTile + lx;
+                    const int xi = x + ox, yi = y + oy;
+                    const int x0 = clampi(xi, 0, J.w - 1), x1 = clampi(xi + 1, 0, J.w - 1);
+                    const float* r0 = J.S1 + (long long)clampi(yi, 0, J.h - 1) * J.pitch;
+                    const float* r1 = J.S1 + (long long)clampi(yi + 1, 0, J.h - 1) * J.pitch;
+                    const float p00 = __ldg(r0 + x0), p01 = __ldg(r0 + x1), p10 = __ldg(r1 + x0), p11 = __ldg(r1 + x1);
+                    const float top = fmaf(ax, p01 - p00, p00), bot = fmaf(ax, p11 - p10, p10);
+                    const float d = s0[a] - fmaf(ay, bot - top, top);
+                    const float wt = footprint_1d(x - pc.x, u.x, ps) * footprint_1d(y - pc.y, u.y, ps) *
+                                     __frcp_rn(fmaxf(1.0f, fabsf(d)));
+                    acc[0][a] += __float2int_rn(wt * su);
+                    acc[1][a] += __float2int_rn(wt * sv);
+                    acc[2][a] += __float2int_rn(wt * sz);
                 }
+                __syncwarp();  // the next patch's rectangle may overlap this one's pixels
             }
         }
+        __syncthreads();
         const float in_ = ldexpf(1.0f, -kn), iz = ldexpf(1.0f, -kz);
-#pragma unroll
-        for (int q = 0; q < kFbStrip; ++q) {
-            if (!row_in || sx + q >= tw) continue;
-            const int x = X0 + sx + q;
+        for (int q = threadIdx.x; q < tw * th; q += blockDim.x) {
+            const int ly = q / tw, lx = q - ly * tw;
+            const int x = X0 + lx, y = Y0 + ly, a = ly * kFbTile + lx;
             float nu, nv, Z;
             own_sums<SC>(J, x, y, ps, stride, nu, nv, Z);
-            const float Zt = Z + __ll2float_rn(az[q]) * iz;
+            const float Zt = Z + __ll2float_rn(acc[2][a]) * iz;
             float2 r;
             if (Zt > 0.0f) {
-                r = make_float2((nu + __ll2float_rn(au[q]) * in_) / Zt, (nv + __ll2float_rn(av[q]) * in_) / Zt);
+                r = make_float2((nu + __ll2float_rn(acc[0][a]) * in_) / Zt, (nv + __ll2float_rn(acc[1][a]) * in_) / Zt);
             } else {
                 r = init_flow_at(J.Uc, J.wc, J.hc, J.cscale, (float)x, (float)y);
             }
             J.U[(long long)y * J.w + x] = r;
         }
-        __syncthreads();  // red and bcnt are rewritten for the next tile
+        __syncthreads();  // the accumulators, red and bcnt are rewritten for the next tile
     }
 }
 
@@ -338,7 +349,7 @@ cudaError_t launch_densify_fb(const Jobs<LevelJob>& js, long long total_patches,
     if (total_patches > 0) fb_list_kernel<false><<<grid(total_patches, lc.max_blocks_256), 256, 0, s>>>(js, total_patches, ps, stride);
     fb_scan_kernel<<<std::min(njobs, lc.sm_count * 2), 1024, 0, s>>>(js, njobs);
     if (total_patches > 0) fb_list_kernel<true><<<grid(total_patches, lc.max_blocks_256), 256, 0, s>>>(js, total_patches, ps, stride);
-    const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * 4);
+    const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * 12);
     switch (stride) {
         case 3: densify_fb_kernel<3><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride); break;
         case 4: densify_fb_kernel<4><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride); break;
