@@ -50,6 +50,7 @@ class OrParams(ctypes.Structure):
         ("norm", ctypes.c_int),
         ("huber_b", ctypes.c_double),
         ("fb", ctypes.c_int),
+        ("term_eps", ctypes.c_double),
     ]
 
 
@@ -58,7 +59,7 @@ def params(**kw):
     d = dict(patch_size=8, overlap=0.3, stride_override=0, grad_iters=16, coarsest_scale=-1,
              finest_scale=0, refine=1, var_outer=-1, var_inner=5, delta=5.0, gamma=10.0,
              alpha=10.0, sor_omega=1.6, intensity_scale=255.0, channels=1, dof=2, norm=0, huber_b=5.0,
-             fb=0)
+             fb=0, term_eps=0.0)
     d.update(kw)
     return OrParams(**d)
 
@@ -83,7 +84,7 @@ def _load():
             "or_grid_n": (i, [i, i, i]),
             "or_grid_pos": (i, [i, i, i, i]),
             "or_levels": (i, [i, i, P, _I, _I]),
-            "or_search_level": (None, [_D, _D, _D, _D, i, i, _D, i, i, d, i, i, i, _D, _D, _D, _I, i, i, d]),
+            "or_search_level": (None, [_D, _D, _D, _D, i, i, _D, i, i, d, i, i, i, _D, _D, _D, _I, i, i, d, d]),
             "or_densify_level": (None, [_D, _D, i, i, _D, i, i, _D, i, i, d, _D]),
             "or_refine_level": (None, [_D, _D, i, i, i, _D, i, i, d, d, d, d, i]),
             "or_upsample_flow": (None, [_D, i, i, d, _D, i, i]),
@@ -154,10 +155,12 @@ def robust_error(e, norm, huber_b=5.0):
     return _load().or_robust_error(float(e), int(norm), float(huber_b))
 
 
-def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen=None, dof=2, norm=0, huber_b=5.0):
+def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen=None, dof=2, norm=0, huber_b=5.0,
+                 term_eps=0.0):
     """Inverse search of one level.  Returns (u, u_init, status) with u, u_init of shape
     (ny, nx, 2) and status (ny, nx) in {0 ok, 1 reset, 2 flat}.  dof = 1: horizontal only;
-    norm: 0 L2, 1 L1, 2 Huber with threshold huber_b."""
+    norm: 0 L2, 1 L1, 2 Huber with threshold huber_b; term_eps > 0: a patch stops after the
+    first step of length <= term_eps."""
     I0, Ix, Iy, I1 = _f64(I0), _f64(Ix), _f64(Iy), _f64(I1)
     h, w = I0.shape
     nx, ny = grid_n(w, ps, stride_), grid_n(h, ps, stride_)
@@ -171,7 +174,7 @@ def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen
     fz = None if frozen is None else _f64(frozen)
     _load().or_search_level(_p(I0), _p(Ix), _p(Iy), _p(I1), w, h, _p(Uc), wc, hc, float(cscale), ps, stride_,
                             iters, _p(fz), _p(u), _p(ui), st.ctypes.data_as(_I), int(dof), int(norm),
-                            float(huber_b))
+                            float(huber_b), float(term_eps))
     return u, ui, st
 
 

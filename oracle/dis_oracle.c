@@ -46,6 +46,7 @@ typedef struct or_params {
     int norm;              /* search error norm (supp. robust error norms): 0 L2, 1 L1, 2 Huber [R21] */
     double huber_b;        /* Huber threshold b on the intensity scale [R21] */
     int fb;                /* 1: forward-backward consistency (supp. Sec. B (ii)) [R22] */
+    double term_eps;       /* > 0: a patch stops once its update step is at most this long (supp. Sec. C) [R23] */
 } or_params;
 
 enum { OR_NORM_L2 = 0, OR_NORM_L1 = 1, OR_NORM_HUBER = 2 };
@@ -252,11 +253,14 @@ static void init_at(const double* Uc, int wc, int hc, double cscale, double x, d
  * v stays at its initial value and u takes the scalar step du = sum S'_x e / sum S'_x^2; the
  * patch is flat when sum S'_x^2 <= 1e-6 tr(H') / 2.
  * [R21] norm / huber_b: the per-pixel error e = (w - mean w) - T is transformed by
- * or_robust_error before it enters sum S'^T e. */
+ * or_robust_error before it enters sum S'^T e.
+ * [R23] term_eps > 0 (supplementary Sec. C: iterations end early "for small residuals"): a patch
+ * stops after the first update whose step |(du, dv)|_2 is at most term_eps (0: the fixed count
+ * of R8). */
 void or_search_level(const double* I0, const double* Ix, const double* Iy, const double* I1, int w, int h,
                      const double* Uc, int wc, int hc, double cscale, int ps, int stride, int iters,
                      const double* frozen, double* u_out, double* uinit_out, int* status_out, int dof, int norm,
-                     double huber_b)
+                     double huber_b, double term_eps)
 {
     int nx = or_grid_n(w, ps, stride), ny = or_grid_n(h, ps, stride), n = ps * ps;
     double* T = (double*)malloc(sizeof(double) * n);
@@ -319,14 +323,16 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
                         b0 += gx[q] * r;
                         b1 += gy[q] * r;
                     }
+                    double du, dv = 0.0;
                     if (dof == 1) {
-                        u -= b0 / h00;
+                        du = b0 / h00;
                     } else {
-                        double du = (h11 * b0 - h01 * b1) / det;
-                        double dv = (h00 * b1 - h01 * b0) / det;
-                        u -= du;
-                        v -= dv;
+                        du = (h11 * b0 - h01 * b1) / det;
+                        dv = (h00 * b1 - h01 * b0) / det;
                     }
+                    u -= du;
+                    v -= dv;
+                    if (term_eps > 0.0 && du * du + dv * dv <= term_eps * term_eps) break;
                 }
                 double ex = u - ui[0], ey = v - ui[1];
                 if (sqrt(ex * ex + ey * ey) > (double)ps) {
@@ -667,6 +673,7 @@ int or_dis_flow_fb(const double* I0, const double* I1, int W, int H, const or_pa
     if ((p->dof != 1 && p->dof != 2) || p->norm < 0 || p->norm > 2 || !(p->huber_b > 0.0)) return OR_ERR_INVALID;
     /* [R22] forward-backward consistency starts both directions from zero and replays nothing */
     if (p->fb != 0 && p->fb != 1) return OR_ERR_INVALID;
+    if (!(p->term_eps >= 0.0)) return OR_ERR_INVALID;
     if (p->fb && (init_flow || frozen || record)) return OR_ERR_INVALID;
     int rc = or_levels(W, H, p, &ss, &sf);
     if (rc != OR_OK) return rc;
@@ -746,7 +753,8 @@ int or_dis_flow_fb(const double* I0, const double* I1, int W, int H, const or_pa
             u[d] = (double*)malloc(sizeof(double) * 2 * np);
             or_sobel(A[d], w, h, Ix, Iy);
             or_search_level(A[d], Ix, Iy, B[d], w, h, Uc[d], wc, hc, cs, ps, stride, p->grad_iters,
-                            frozen ? frozen + 2 * off : NULL, u[d], ui, NULL, p->dof, p->norm, p->huber_b);
+                            frozen ? frozen + 2 * off : NULL, u[d], ui, NULL, p->dof, p->norm, p->huber_b,
+                            p->term_eps);
             if (record && d == 0)
                 for (int k = 0; k < 2 * np; k++) record[2 * off + k] = u[d][k] - ui[k];
             free(Ix);

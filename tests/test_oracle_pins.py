@@ -785,3 +785,40 @@ def test_fb_pipeline_recovers_translation_both_ways_and_is_symmetric():
     # and the consistency changes the forward flow (the backward patches entered it)
     plain = oracle.dis_flow(A, B, oracle.params(patch_size=8, stride_override=4, grad_iters=12, coarsest_scale=2))
     assert not np.array_equal(plain, f1) and np.abs(plain - f1).max() < 1.0
+
+
+# ---- early termination on a small step (supplementary Sec. C) ----
+
+def test_early_termination_stops_at_the_closed_form_iteration():
+    # bilinear scene, off-centre patch: the error after k steps is M^k (-t) (see the closed-form
+    # pin above), so the step of iteration k is M^(k-1) (-t) - M^k (-t); the search must stop at
+    # the first k whose step is at most term_eps and return M^k (-t) + t
+    h = w = 64
+    ps, st_, px, py = 8, 8, 24, 32
+    c3 = 0.3
+    x0, y0 = px + 3.5 + 2, py + 3.5 + 2  # saddle 2 px off the patch centre: contraction 0.60
+    c = (5.0 + c3 * x0 * y0, -c3 * y0, -c3 * x0, c3)
+    t = np.array([0.8, 0.45])
+    I0, I1, gx, gy = _bilinear_scene(h, w, c, t)
+    Y, X = np.mgrid[py:py + ps, px:px + ps].astype(float)
+    G = np.stack([(c[1] + c[3] * Y).ravel(), (c[2] + c[3] * X).ravel()], 1)
+    M = ps * ps * np.linalg.solve(G.T @ G, np.outer(G.mean(0), G.mean(0)))
+    assert 0.5 < max(abs(np.linalg.eigvals(M))) < 0.7
+    k_idx = _patch_index(w, ps, st_, px, py)
+    errs = [-t]
+    for _ in range(60):
+        errs.append(M @ errs[-1])
+    steps = [np.linalg.norm(errs[k - 1] - errs[k]) for k in range(1, 61)]
+    for kwant in (1, 2, 5, 12):
+        eps = float(np.sqrt(steps[kwant - 1] * steps[kwant]))  # between the steps of k and k + 1
+        kstop = next(k for k in range(1, 61) if steps[k - 1] <= eps)
+        assert kstop == kwant + 1
+        u, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 60, term_eps=eps)
+        assert np.abs(u.reshape(-1, 2)[k_idx] - t - errs[kstop]).max() < 1e-11, (eps, kstop)
+    # off: the fixed count; a huge threshold: exactly one step
+    a, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 7)
+    b, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 7, term_eps=0.0)
+    assert np.array_equal(a, b)
+    one, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 1)
+    big, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 50, term_eps=1e9)
+    assert np.array_equal(one, big)
