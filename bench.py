@@ -18,6 +18,8 @@ rectified synthetic pairs of 1440x960 (half-resolution Middlebury size, disparit
 --norm l1 / huber runs the patch search with that robust error norm (supplementary, robust
 error norms).  --fb adds forward-backward consistency (supplementary Sec. B (ii)): both
 directions per pair, merged in the densification; the forward flows are the output.
+--term-eps E stops each patch's search after its first step of at most E px (early termination
+for small residuals, supplementary Sec. C).
 
 Multi-GPU (torchrun): frame pairs are independent, so each rank runs its own batch
 (replicas, weak scaling, no collective on the data path); value = all ranks' pairs / max time.
@@ -53,14 +55,14 @@ def workload_pair(workload, k):
     return synth.layered_pair(1000 + k)
 
 
-def preset_params(dis, name, workload="flow", norm="l2", fb=False):
+def preset_params(dis, name, workload="flow", norm="l2", fb=False, term_eps=0.0):
     # theta_ss fixed per workload (five levels at 1024x436, six at 1440x960: the automatic value)
     return dis.dis_default_params(name, coarsest_scale=WORKLOADS[workload][5], norm=NORM_CODES[norm],
-                                  fb=1 if fb else 0)
+                                  fb=1 if fb else 0, term_eps=term_eps)
 
 
 def search_form(p, lanes):
-    if p.dof == 1 or p.norm != 0:
+    if p.dof == 1 or p.norm != 0 or p.term_eps > 0:
         return "grouped search, %s%s" % ("one degree of freedom" if p.dof == 1 else "flow",
                                          "" if p.norm == 0 else ", %s norm" % ["l2", "l1", "huber"][p.norm])
     return "search variant %d" % lanes
@@ -155,7 +157,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(preset, workload="flow", norm="l2", fb=False):
+def cpu_baseline(preset, workload="flow", norm="l2", fb=False, term_eps=0.0):
     """FP64 oracle on one pair of the workload at half width and height (a quarter of the area,
     one level fewer; the method's cost is linear in area), scaled to pairs/s at full size."""
     import oracle
@@ -165,10 +167,10 @@ def cpu_baseline(preset, workload="flow", norm="l2", fb=False):
     I0, I1, _ = synth.layered_pair(1000, width=w, height=h, max_disp=20.0 if workload == "flow" else 48.0,
                                    horizontal=workload == "stereo")
     from paper_1603_03590_gb300 import dis
-    p = preset_params(dis, preset, workload, norm, fb)
+    p = preset_params(dis, preset, workload, norm, fb, term_eps)
     q = oracle.params(patch_size=p.patch_size, overlap=round(float(p.overlap), 6), grad_iters=p.grad_iters,
                       coarsest_scale=ss - 1, finest_scale=p.finest_scale, refine=p.refine, dof=p.dof, norm=p.norm,
-                      huber_b=round(float(p.huber_b), 6), fb=p.fb)
+                      huber_b=round(float(p.huber_b), 6), fb=p.fb, term_eps=float(p.term_eps))
     oracle.build()
     t = time.perf_counter()
     oracle.dis_flow(I0, I1, q)
@@ -185,7 +187,7 @@ def run_reference(args, rank, world):
     metric, W, H, _, _, ss, wtext = WORKLOADS[args.workload]
     times = []
     for k in range(warmup + steps):
-        r = cpu_baseline(args.preset, args.workload, args.norm, args.fb)
+        r = cpu_baseline(args.preset, args.workload, args.norm, args.fb, args.term_eps)
         if k >= warmup:
             times.append(0.25 / r["value"])
     dt = sum(times)
@@ -209,12 +211,16 @@ def workload_config(args, batch, world):
         text += ", %s search norm" % args.norm
     if args.fb:
         text += ", forward-backward consistency"
+    if args.term_eps > 0:
+        text += ", search ends at a step <= %g px" % args.term_eps
     c = {"workload": text, "batch_per_gpu": batch, "preset": args.preset,
          "parallelism": "replicas" if world > 1 else "single"}
     if args.norm != "l2":
         c["norm"] = args.norm
     if args.fb:
         c["fb"] = True
+    if args.term_eps > 0:
+        c["term_eps"] = args.term_eps
     return c
 
 
@@ -227,6 +233,7 @@ def main():
     ap.add_argument("--workload", default="flow", choices=sorted(WORKLOADS))
     ap.add_argument("--norm", default="l2", choices=sorted(NORM_CODES))
     ap.add_argument("--fb", action="store_true", help="forward-backward consistency")
+    ap.add_argument("--term-eps", type=float, default=0.0, help="early termination of the patch search (px)")
     ap.add_argument("--preset", default=None, help="default: dense (flow), stereo_dense (stereo)")
     ap.add_argument("--batch", type=int, default=None, help="default: 32 (flow), 8 (stereo)")
     ap.add_argument("--unique", type=int, default=4, help="distinct synthetic pairs cycled through the batch")
@@ -257,7 +264,7 @@ def main():
 
     B = args.batch
     uniq = [workload_pair(args.workload, k) for k in range(args.unique)]
-    p = preset_params(dis, args.preset, args.workload, args.norm, args.fb)
+    p = preset_params(dis, args.preset, args.workload, args.norm, args.fb, args.term_eps)
     h = dis.dis_create(W, H, 2 * B if args.fb else B, 1)
     I0d = [torch.from_numpy(uniq[k % len(uniq)][0]).to(dev) for k in range(B)]
     I1d = [torch.from_numpy(uniq[k % len(uniq)][1]).to(dev) for k in range(B)]
@@ -408,12 +415,12 @@ def main():
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max},
         "stages_ms_per_step": {k: round(v, 4) for k, v in stages.items()},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_call(dis, p, W, H, lanes if p.dof == 2 and p.norm == 0 else 0, B,
+        "gpu_launches": launches_per_call(dis, p, W, H, lanes if p.dof == 2 and p.norm == 0 and p.term_eps == 0 else 0, B,
                                           refine_form) * args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.preset, args.workload, args.norm, args.fb)
+        line["cpu_baseline"] = cpu_baseline(args.preset, args.workload, args.norm, args.fb, args.term_eps)
     print(json.dumps(line))
 
 

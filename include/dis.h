@@ -67,6 +67,11 @@ typedef struct dis_params {
                               * (e <- sign(e) sqrt|e|), 2 Huber (e <- e if |e| < huber_b, else
                               * sign(e) sqrt(2 huber_b |e| - huber_b^2)); e = I1(x + u) - mean - T */
     float huber_b;           /* Huber threshold on the intensity_scale scale, > 0 (5) */
+    float term_eps;          /* > 0: a patch's search stops after the first update whose step length
+                              * is at most term_eps px (early termination for small residuals,
+                              * supplementary Sec. C; runs in the grouped search forms); 0: theta_it
+                              * iterations (the search still ends early where that result is already
+                              * known exactly) */
     int32_t fb;              /* 1: forward-backward consistency (supplementary Sec. B (ii)): both
                               * directions are searched and refined, each densification merges the
                               * other direction's patches (dis_densify_level_fb); n pairs take 2 n of
@@ -294,15 +299,16 @@ dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, i
                                int hc, float cscale, int ps, int stride, int iters, int variant, float* u_out,
                                float* uinit_out, int* status_out, void* stream);
 
-/* dis_search_level_ex with the search's degrees of freedom and error norm (dis_params.dof, norm
- * and huber_b).  dof 1 leaves the v component of u_out at u_init; status 2 (flat) then means
- * sum S'_x^2 <= 1e-6 tr(H') / 2.  For dof 1 or norm != 0 the variant is 0 (the default) or one
- * of dis_search_mode_variants(ps); dof 2 with norm 0 is dis_search_level_ex.  DIS_ERR_INVALID_ARG for a
- * dof outside {1, 2}, a norm outside {0, 1, 2} or huber_b <= 0. */
+/* dis_search_level_ex with the search's degrees of freedom, error norm and early termination
+ * (dis_params.dof, norm, huber_b and term_eps).  dof 1 leaves the v component of u_out at
+ * u_init; status 2 (flat) then means sum S'_x^2 <= 1e-6 tr(H') / 2.  For dof 1, norm != 0 or
+ * term_eps > 0 the variant is 0 (the default) or one of dis_search_mode_variants(ps); dof 2 with
+ * norm 0 and term_eps 0 is dis_search_level_ex.  DIS_ERR_INVALID_ARG for a dof outside {1, 2}, a
+ * norm outside {0, 1, 2}, huber_b <= 0 or term_eps < 0. */
 dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc,
                                 int wc, int hc, float cscale, int ps, int stride, int iters, int variant, int dof,
-                                int norm, float huber_b, float* u_out, float* uinit_out, int* status_out,
-                                void* stream);
+                                int norm, float huber_b, float term_eps, float* u_out, float* uinit_out,
+                                int* status_out, void* stream);
 
 /* Step 4 of Alg. 1 (Eq. 3): U(x) = sum_i w_i(x) u_i / sum_i w_i(x) over the patches covering
  * x, w_i(x) = 1 / max(1, |I1(x + u_i) - I0(x)|).  u: nx*ny*2 patch flows; U_out: w*h*2.

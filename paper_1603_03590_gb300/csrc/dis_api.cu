@@ -99,6 +99,10 @@ dis_status validate(const dis_params* p, std::string& err)
         err = "fb must be 0 or 1";
         return DIS_ERR_INVALID_ARG;
     }
+    if (!finite(p->term_eps) || p->term_eps < 0.0f) {
+        err = "term_eps must be finite and >= 0";
+        return DIS_ERR_INVALID_ARG;
+    }
     return DIS_OK;
 }
 
@@ -490,14 +494,14 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
             case Phase::LEVEL: {
                 auto js = dis::device_jobs(reinterpret_cast<const LevelJob*>(tab), ph.n);
                 const int lanes = hd->search_lanes[ps];
-                if (lanes == 1 && p.dof == 2 && p.norm == 0)
+                if (lanes == 1 && p.dof == 2 && p.norm == 0 && p.term_eps == 0.0f)
                     e = traced(DIS_LAUNCH_SEARCH_PLANES, ph.s,
                                [&] { return dis::launch_search_planes(js, ph.total2, hd->lc, s); });
                 if (e == cudaSuccess)
                     e = traced(DIS_LAUNCH_SEARCH, ph.s, [&] {
-                        if (p.dof != 2 || p.norm != 0)
+                        if (p.dof != 2 || p.norm != 0 || p.term_eps > 0.0f)
                             return dis::launch_search_mode(js, ph.total, ps, stride, p.grad_iters, p.dof, p.norm,
-                                                           p.huber_b, lanes, hd->lc, s);
+                                                           p.huber_b, p.term_eps, lanes, hd->lc, s);
                         return dis::launch_search(js, ph.total, ps, stride, p.grad_iters, hd->lc, s, lanes, lanes == 1);
                     });
                 if (e == cudaSuccess)
@@ -1046,14 +1050,16 @@ static bool variant_ok(int ps, int v, bool mode)
 
 dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc,
                                 int wc, int hc, float cscale, int ps, int stride, int iters, int variant, int dof,
-                                int norm, float huber_b, float* u_out, float* uinit_out, int* status_out,
-                                void* stream)
+                                int norm, float huber_b, float term_eps, float* u_out, float* uinit_out,
+                                int* status_out, void* stream)
 {
     if (!I0 || !I1 || !u_out || iters < 0 || !level_args_ok(w, h, pitch, ps, stride, Uc, wc, hc, cscale))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: bad pointer, size, pitch or grid");
-    if ((dof != 1 && dof != 2) || norm < 0 || norm > 2 || !finite(huber_b) || !(huber_b > 0.0f))
-        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: dof, norm or huber_b out of range");
-    if (variant != 0 && !variant_ok(ps, variant, dof != 2 || norm != 0))
+    if ((dof != 1 && dof != 2) || norm < 0 || norm > 2 || !finite(huber_b) || !(huber_b > 0.0f) ||
+        !finite(term_eps) || term_eps < 0.0f)
+        return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: dof, norm, huber_b or term_eps out of range");
+    const bool mode = dof != 2 || norm != 0 || term_eps > 0.0f;
+    if (variant != 0 && !variant_ok(ps, variant, mode))
         return fail(nullptr, DIS_ERR_INVALID_ARG, "dis_search_level: not a search variant of this patch size");
     LevelJob J;
     std::memset(&J, 0, sizeof(J));
@@ -1073,9 +1079,8 @@ dis_status dis_search_level_ex2(const float* I0, const float* I1, int w, int h, 
     J.ny = grid_n(h, ps, stride);
     J.C = 1;
     const long long np = (long long)J.nx * J.ny;
-    cudaError_t e = (dof != 2 || norm != 0)
-                        ? dis::launch_search_mode(dis::single_job(J), np, ps, stride, iters, dof, norm, huber_b,
-                                                  variant, stage_lc(), (cudaStream_t)stream)
+    cudaError_t e = mode ? dis::launch_search_mode(dis::single_job(J), np, ps, stride, iters, dof, norm, huber_b,
+                                                   term_eps, variant, stage_lc(), (cudaStream_t)stream)
                         : dis::launch_search(dis::single_job(J), np, ps, stride, iters, stage_lc(),
                                              (cudaStream_t)stream, variant, false);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_search_level");
@@ -1086,7 +1091,7 @@ dis_status dis_search_level_ex(const float* I0, const float* I1, int w, int h, i
                                float* uinit_out, int* status_out, void* stream)
 {
     return dis_search_level_ex2(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, variant, 2, 0, 5.0f,
-                                u_out, uinit_out, status_out, stream);
+                                0.0f, u_out, uinit_out, status_out, stream);
 }
 
 dis_status dis_search_level(const float* I0, const float* I1, int w, int h, int64_t pitch, const float* Uc, int wc,
@@ -1250,7 +1255,7 @@ extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n,
     if (vst != DIS_OK) return fail(hd, vst, verr);
     int opts[8];
     // the stereo and robust-norm searches have their own (grouped) forms
-    const bool flow_l2 = p->dof == 2 && p->norm == 0;
+    const bool flow_l2 = p->dof == 2 && p->norm == 0 && p->term_eps == 0.0f;
     const int nopt = flow_l2 ? dis::search_lane_options(p->patch_size, opts)
                              : dis::search_mode_options(p->patch_size, opts);
     cudaStream_t s = (cudaStream_t)stream;

@@ -145,11 +145,13 @@ cudaError_t launch_search_coop(const Jobs<LevelJob>& js, long long total, int ps
 cudaError_t launch_search_planes(const Jobs<LevelJob>& js, long long total_pix, const LaunchCfg& lc, cudaStream_t s);
 // Lanes-per-patch variants the search offers for patch size ps (first = default); returns the count.
 int search_lane_options(int ps, int* out);
-// The stereo (dof 1) and robust-norm (norm 1 L1, 2 Huber with threshold huber_b) searches, in the
-// grouped form with `lanes` lanes per patch when that is one of search_mode_options(ps), else the
-// first of them; dof 2 with norm 0 is launch_search.
+// The stereo (dof 1) and robust-norm (norm 1 L1, 2 Huber with threshold huber_b) searches, and
+// any search with early termination (term_eps > 0: stop after a step of length <= term_eps), in
+// the grouped form with `lanes` lanes per patch when that is one of search_mode_options(ps), else
+// the first of them.  The flow search with the L2 norm and no early termination is launch_search.
 cudaError_t launch_search_mode(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int dof,
-                               int norm, float huber_b, int lanes, const LaunchCfg& lc, cudaStream_t s);
+                               int norm, float huber_b, float term_eps, int lanes, const LaunchCfg& lc,
+                               cudaStream_t s);
 // Group widths of the stereo and robust-norm searches for patch size ps (the first is the default).
 int search_mode_options(int ps, int* out);
 // Densification with forward-backward consistency over jobs that come in partner pairs: lists

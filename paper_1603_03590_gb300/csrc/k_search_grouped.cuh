@@ -99,9 +99,12 @@ __device__ __forceinline__ void group_sum12(float (&Q)[12], unsigned gmask, int 
 // register allocation must allow (chosen per variant so that nothing spills).  GSM: template
 // gradients in shared memory (else in registers; measured per variant, see launch_search).
 // DOF / ROBUST: the modes above; `norm` (1 L1, 2 Huber) and `huber_b` are read by ROBUST only.
-template <int LPP, int PPL, int PSC, int MINB, bool GSM, int DOF = 2, bool ROBUST = false>
+// TERM: term2 > 0 makes a patch stop after the first update whose squared step length is at most
+// term2 (early termination on a small step; 0: the fixed count, ended early only where exact).
+template <int LPP, int PPL, int PSC, int MINB, bool GSM, int DOF = 2, bool ROBUST = false, bool TERM = false>
 __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
-                                                     int ps_rt, int stride, int iters, int norm, float huber_b)
+                                                     int ps_rt, int stride, int iters, int norm, float huber_b,
+                                                     float term2)
 {
     static_assert(DOF == 1 || DOF == 2, "one or two degrees of freedom");
     extern __shared__ float smem[];
@@ -295,6 +298,11 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                     } else {
                         un = u - k00 * bq[0];
                     }
+                    if (TERM && term2 > 0.0f && (un - u) * (un - u) + (vn - v) * (vn - v) <= term2) {
+                        u = un;
+                        v = vn;
+                        break;
+                    }
                     // the state is (u, v) alone: a repeat two iterates back is a 2-cycle
                     if (search_cycle_exit(u, v, un, vn, u1, v1, 2, iters - 1 - it)) break;
                 }
@@ -390,6 +398,11 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                     } else {
                         un = u - k00 * b0;
                     }
+                    if (TERM && term2 > 0.0f && (un - u) * (un - u) + (vn - v) * (vn - v) <= term2) {
+                        u = un;
+                        v = vn;
+                        break;
+                    }
                     ++quiet;
                     if (search_cycle_exit(u, v, un, vn, u1, v1, quiet, iters - 1 - it)) break;
                 }
@@ -412,15 +425,17 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
     }
 }
 
-template <int LPP, int PPL, int PSC, int MINB = 1, bool GSM = true, int DOF = 2, bool ROBUST = false>
+template <int LPP, int PPL, int PSC, int MINB = 1, bool GSM = true, int DOF = 2, bool ROBUST = false,
+          bool TERM = false>
 static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters,
-                             const LaunchCfg& lc, cudaStream_t s, int norm = 0, float huber_b = 0.0f)
+                             const LaunchCfg& lc, cudaStream_t s, int norm = 0, float huber_b = 0.0f,
+                             float term2 = 0.0f)
 {
     const int threads = 128, wpb = threads / 32, per_block = wpb * (32 / LPP);
     const size_t smem = (size_t)per_block * ((ps + 2) * (ps + 2) + (GSM ? 2 * ps * ps : 0)) * sizeof(float);
     static int occ = 0;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC, MINB, GSM, DOF, ROBUST>, threads,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC, MINB, GSM, DOF, ROBUST, TERM>, threads,
                                                           smem) !=
                 cudaSuccess ||
             occ < 1)
@@ -429,8 +444,8 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     long long blocks = (total + per_block - 1) / per_block;
     const long long cap = (long long)lc.sm_count * occ;
     if (blocks > cap) blocks = cap;
-    search_kernel<LPP, PPL, PSC, MINB, GSM, DOF, ROBUST>
-        <<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters, norm, huber_b);
+    search_kernel<LPP, PPL, PSC, MINB, GSM, DOF, ROBUST, TERM>
+        <<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters, norm, huber_b, term2);
     return cudaGetLastError();
 }
 

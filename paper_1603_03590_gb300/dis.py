@@ -51,6 +51,7 @@ class dis_params(ctypes.Structure):
         ("dof", ctypes.c_int32),
         ("norm", ctypes.c_int32),
         ("huber_b", ctypes.c_float),
+        ("term_eps", ctypes.c_float),
         ("fb", ctypes.c_int32),
     ]
 
@@ -95,8 +96,8 @@ _SIGS = {
     "dis_search_mode_variants": (_i, [_i, _vp, _i]),
     "dis_compute_flow_fb": (_i, [_vp, _vp, _vp, _i, _i, _i64, _P, _vp, _vp, _vp]),
     "dis_densify_level_fb": (_i, [_vp, _vp, _vp, _i, _i, _i64, _vp, _vp, _i, _i, _vp, _vp, _vp]),
-    "dis_search_level_ex2": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _i, _f, _vp, _vp, _vp,
-                                  _vp]),
+    "dis_search_level_ex2": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _i, _f, _f, _vp, _vp,
+                                  _vp, _vp]),
     "dis_refine_level_ex": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _i, _vp]),
     "dis_densify_level": (_i, [_vp, _vp, _i, _i, _i64, _vp, _i, _i, _vp, _i, _i, _f, _vp, _vp]),
     "dis_refine_level": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _vp, _i, _i, _f, _f, _f, _f, _vp]),
@@ -313,12 +314,12 @@ def dis_densify_level_fb(handle, I0, I1, w, h, pitch, u, ub, ps, stride, U_out, 
 
 
 def dis_search_level_ex2(I0, I1, w, h, pitch, Uc, wc, hc, cscale, ps, stride, iters, variant, dof, norm, huber_b,
-                         u_out, uinit_out=None, status_out=None, stream=None):
-    """dis_search_level_ex with the degrees of freedom (1 stereo, 2 flow) and the error norm
-    (0 L2, 1 L1, 2 Huber with threshold huber_b)."""
+                         u_out, uinit_out=None, status_out=None, stream=None, term_eps=0.0):
+    """dis_search_level_ex with the degrees of freedom (1 stereo, 2 flow), the error norm (0 L2,
+    1 L1, 2 Huber with threshold huber_b) and early termination (term_eps > 0)."""
     _check(_lib.dis_search_level_ex2(_ptr(I0), _ptr(I1), w, h, pitch, _ptr(Uc), wc, hc, cscale, ps, stride, iters,
-                                     variant, dof, NORMS.get(norm, norm), huber_b, _ptr(u_out), _ptr(uinit_out),
-                                     _ptr(status_out), _stream(stream)))
+                                     variant, dof, NORMS.get(norm, norm), huber_b, term_eps, _ptr(u_out),
+                                     _ptr(uinit_out), _ptr(status_out), _stream(stream)))
 
 
 def dis_refine_level_ex(handle, I0, I1, w, h, pitch, channels, U, outer, inner, delta=5.0, gamma=10.0, alpha=10.0,

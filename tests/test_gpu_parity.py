@@ -117,6 +117,14 @@ def compare_search(I0, I1, Uc, cscale, ps, stride, iters, u_g, ui_g, st_g, ref=N
             I1p = I1 + 1e-5 * np.random.default_rng(seed).standard_normal(I1.shape)
             u_p, _, st_p = oracle.search_level(I0, gx, gy, I1p, ps, stride, iters, Uc=Uc, cscale=cscale, **mode)
             unstable |= (np.abs(u_p.reshape(-1, 2) - u_o).max(1) > 1e-4) | (st_p.reshape(-1) != st_o)
+        if mode.get("term_eps", 0.0) > 0.0:
+            # early termination is a threshold decision on a step length: patches whose result
+            # changes when the threshold moves by 0.2 % (far more than FP32 moves a step) stop at
+            # an iteration that FP32 does not determine
+            for f in (1.0 - 2e-3, 1.0 + 2e-3):
+                m2 = dict(mode, term_eps=mode["term_eps"] * f)
+                u_p, _, st_p = oracle.search_level(I0, gx, gy, I1, ps, stride, iters, Uc=Uc, cscale=cscale, **m2)
+                unstable |= (np.abs(u_p.reshape(-1, 2) - u_o).max(1) > 1e-4) | (st_p.reshape(-1) != st_o)
         ref = (u_o, ui_o, st_o, unstable)
     u_o, ui_o, st_o, unstable = ref
     assert np.abs(ui_g - ui_o).max() <= 1e-4
@@ -310,7 +318,7 @@ def oracle_params(p):
                          refine=p.refine, var_outer=p.var_outer, var_inner=p.var_inner, delta=p.delta,
                          gamma=p.gamma, alpha=p.alpha, sor_omega=round(float(p.sor_omega), 6),
                          intensity_scale=p.intensity_scale, channels=p.channels, dof=p.dof, norm=p.norm,
-                         huber_b=round(float(p.huber_b), 6), fb=p.fb)
+                         huber_b=round(float(p.huber_b), 6), fb=p.fb, term_eps=float(p.term_eps))
 
 
 def oracle_e2e(I0, I1, q, **kw):
