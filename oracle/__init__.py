@@ -51,6 +51,7 @@ class OrParams(ctypes.Structure):
         ("huber_b", ctypes.c_double),
         ("fb", ctypes.c_int),
         ("term_eps", ctypes.c_double),
+        ("polish", ctypes.c_int),
     ]
 
 
@@ -59,7 +60,7 @@ def params(**kw):
     d = dict(patch_size=8, overlap=0.3, stride_override=0, grad_iters=16, coarsest_scale=-1,
              finest_scale=0, refine=1, var_outer=-1, var_inner=5, delta=5.0, gamma=10.0,
              alpha=10.0, sor_omega=1.6, intensity_scale=255.0, channels=1, dof=2, norm=0, huber_b=5.0,
-             fb=0, term_eps=0.0)
+             fb=0, term_eps=0.0, polish=0)
     d.update(kw)
     return OrParams(**d)
 
@@ -84,7 +85,7 @@ def _load():
             "or_grid_n": (i, [i, i, i]),
             "or_grid_pos": (i, [i, i, i, i]),
             "or_levels": (i, [i, i, P, _I, _I]),
-            "or_search_level": (None, [_D, _D, _D, _D, i, i, _D, i, i, d, i, i, i, _D, _D, _D, _I, i, i, d, d]),
+            "or_search_level": (None, [_D, _D, _D, _D, i, i, _D, i, i, d, i, i, i, _D, _D, _D, _I, i, i, d, d, i]),
             "or_densify_level": (None, [_D, _D, i, i, _D, i, i, _D, i, i, d, _D]),
             "or_refine_level": (None, [_D, _D, i, i, i, _D, i, i, d, d, d, d, i]),
             "or_upsample_flow": (None, [_D, i, i, d, _D, i, i]),
@@ -156,7 +157,7 @@ def robust_error(e, norm, huber_b=5.0):
 
 
 def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen=None, dof=2, norm=0, huber_b=5.0,
-                 term_eps=0.0):
+                 term_eps=0.0, polish=0):
     """Inverse search of one level.  Returns (u, u_init, status) with u, u_init of shape
     (ny, nx, 2) and status (ny, nx) in {0 ok, 1 reset, 2 flat}.  dof = 1: horizontal only;
     norm: 0 L2, 1 L1, 2 Huber with threshold huber_b; term_eps > 0: a patch stops after the
@@ -174,7 +175,7 @@ def search_level(I0, Ix, Iy, I1, ps, stride_, iters, Uc=None, cscale=2.0, frozen
     fz = None if frozen is None else _f64(frozen)
     _load().or_search_level(_p(I0), _p(Ix), _p(Iy), _p(I1), w, h, _p(Uc), wc, hc, float(cscale), ps, stride_,
                             iters, _p(fz), _p(u), _p(ui), st.ctypes.data_as(_I), int(dof), int(norm),
-                            float(huber_b), float(term_eps))
+                            float(huber_b), float(term_eps), int(polish))
     return u, ui, st
 
 

@@ -47,6 +47,9 @@ typedef struct or_params {
     double huber_b;        /* Huber threshold b on the intensity scale [R21] */
     int fb;                /* 1: forward-backward consistency (supp. Sec. B (ii)) [R22] */
     double term_eps;       /* > 0: a patch stops once its update step is at most this long (supp. Sec. C) [R23] */
+    int polish;            /* > 0 with frozen increments: each patch restarts at u_init + frozen and runs the
+                            * update to convergence (at most this many steps): the converged search whose
+                            * implicit-function gradient the differentiable form offers [R24] */
 } or_params;
 
 enum { OR_NORM_L2 = 0, OR_NORM_L1 = 1, OR_NORM_HUBER = 2 };
@@ -103,6 +106,27 @@ double or_bilinear(const double* I, int w, int h, double x, double y)
     note(((int64_t)y0 << 2) | cy);
     double top = (1.0 - fx) * I[(size_t)y0 * w + x0] + fx * I[(size_t)y0 * w + x1];
     double bot = (1.0 - fx) * I[(size_t)y1 * w + x0] + fx * I[(size_t)y1 * w + x1];
+    return (1.0 - fy) * top + fy * bot;
+}
+
+/* or_bilinear and its derivatives d/dx, d/dy at (x, y): the slopes of the interpolant inside
+ * its cell, 0 along a coordinate that is clamped (outside the image the value is constant). */
+static double bilinear_grad(const double* I, int w, int h, double x, double y, double* dx, double* dy)
+{
+    int cx = 0, cy = 0;
+    if (x < 0.0) { x = 0.0; cx = 1; }
+    if (x > (double)(w - 1)) { x = (double)(w - 1); cx = 1; }
+    if (y < 0.0) { y = 0.0; cy = 1; }
+    if (y > (double)(h - 1)) { y = (double)(h - 1); cy = 1; }
+    int x0 = (int)floor(x), y0 = (int)floor(y);
+    int x1 = x0 + 1 < w ? x0 + 1 : w - 1;
+    int y1 = y0 + 1 < h ? y0 + 1 : h - 1;
+    double fx = x - x0, fy = y - y0;
+    double a = I[(size_t)y0 * w + x0], b = I[(size_t)y0 * w + x1];
+    double c = I[(size_t)y1 * w + x0], d = I[(size_t)y1 * w + x1];
+    *dx = cx ? 0.0 : (1.0 - fy) * (b - a) + fy * (d - c);
+    *dy = cy ? 0.0 : (1.0 - fx) * (c - a) + fx * (d - b);
+    double top = (1.0 - fx) * a + fx * b, bot = (1.0 - fx) * c + fx * d;
     return (1.0 - fy) * top + fy * bot;
 }
 
@@ -256,17 +280,28 @@ static void init_at(const double* Uc, int wc, int hc, double cscale, double x, d
  * or_robust_error before it enters sum S'^T e.
  * [R23] term_eps > 0 (supplementary Sec. C: iterations end early "for small residuals"): a patch
  * stops after the first update whose step |(du, dv)|_2 is at most term_eps (0: the fixed count
- * of R8). */
+ * of R8).
+ * [R24] polish > 0 with frozen increments: every patch with a nonzero increment restarts at
+ * u_init + frozen and solves the search's stationarity condition
+ *   g(u) = sum_q S'_q (w~_q(u) - T_q) = 0,   w~ = w - mean w,  w_q(u) = I1(x_q + u) bilinear
+ * (the fixed point of the update: du = H'^-1 g) by Newton steps u <- u - J^-1 g with
+ * J = dg/du = sum_q S'_q (grad w_q - mean grad w)^T (the bilinear interpolant's derivative,
+ * 0 across a clamped coordinate), until a step is below 1e-13 px (at most `polish` steps;
+ * whether it got there joins the decision trace); then the reset test.  This is the converged
+ * search, whose solution depends on the frames and not on where it started; the
+ * differentiable form's implicit-function gradient is the derivative of this map. */
 void or_search_level(const double* I0, const double* Ix, const double* Iy, const double* I1, int w, int h,
                      const double* Uc, int wc, int hc, double cscale, int ps, int stride, int iters,
                      const double* frozen, double* u_out, double* uinit_out, int* status_out, int dof, int norm,
-                     double huber_b, double term_eps)
+                     double huber_b, double term_eps, int polish)
 {
     int nx = or_grid_n(w, ps, stride), ny = or_grid_n(h, ps, stride), n = ps * ps;
     double* T = (double*)malloc(sizeof(double) * n);
     double* gx = (double*)malloc(sizeof(double) * n);
     double* gy = (double*)malloc(sizeof(double) * n);
     double* wv = (double*)malloc(sizeof(double) * n);
+    double* T2x = (double*)malloc(sizeof(double) * n); /* polish: derivatives of w along x, y */
+    double* T2y = (double*)malloc(sizeof(double) * n);
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             int k = j * nx + i;
@@ -278,7 +313,10 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
                 uinit_out[2 * k] = ui[0];
                 uinit_out[2 * k + 1] = ui[1];
             }
-            if (frozen) {
+            /* [R24] a zero frozen increment stands for a patch that was reset, flat or never moved:
+             * it stays at u_init, polished or not */
+            const int polishing = frozen && polish > 0 && (frozen[2 * k] != 0.0 || frozen[2 * k + 1] != 0.0);
+            if (frozen && !polishing) {
                 u_out[2 * k] = ui[0] + frozen[2 * k];
                 u_out[2 * k + 1] = ui[1] + frozen[2 * k + 1];
                 if (status_out) status_out[k] = OR_PATCH_OK;
@@ -301,6 +339,11 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
                     h11 += gy[q] * gy[q];
                 }
             double u = ui[0], v = ui[1];
+            if (polishing) {
+                u += frozen[2 * k];
+                v += frozen[2 * k + 1];
+            }
+            const int n_it = polishing ? polish : iters;
             double det = h00 * h11 - h01 * h01, tr = h00 + h11;
             int st = OR_PATCH_OK;
             const int flat = dof == 1 ? h00 <= OR_DEGENERATE_REL * 0.5 * tr
@@ -308,7 +351,47 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
             if (flat) {
                 st = OR_PATCH_FLAT;
             } else {
-                for (int it = 0; it < iters; it++) {
+                int converged = 0;
+                for (int it = 0; polishing && it < n_it; it++) {
+                    /* Newton step on g(u) = 0 */
+                    double mw = 0.0, mgx = 0.0, mgy = 0.0;
+                    for (int b = 0; b < ps; b++)
+                        for (int a = 0; a < ps; a++) {
+                            double X = px + a + u, Y = py + b + v, dx, dy;
+                            double s = bilinear_grad(I1, w, h, X, Y, &dx, &dy);
+                            int q = b * ps + a;
+                            wv[q] = s;
+                            T2x[q] = dx;
+                            T2y[q] = dy;
+                            mw += s;
+                            mgx += dx;
+                            mgy += dy;
+                        }
+                    mw /= n;
+                    mgx /= n;
+                    mgy /= n;
+                    double g0 = 0.0, g1 = 0.0, j00 = 0.0, j01 = 0.0, j10 = 0.0, j11 = 0.0;
+                    for (int q = 0; q < n; q++) {
+                        double r = (wv[q] - mw) - T[q];
+                        g0 += gx[q] * r;
+                        g1 += gy[q] * r;
+                        j00 += gx[q] * (T2x[q] - mgx);
+                        j01 += gx[q] * (T2y[q] - mgy);
+                        j10 += gy[q] * (T2x[q] - mgx);
+                        j11 += gy[q] * (T2y[q] - mgy);
+                    }
+                    double dj = j00 * j11 - j01 * j10;
+                    if (!(fabs(dj) > 0.0)) break;
+                    double du = (j11 * g0 - j01 * g1) / dj;
+                    double dv = (j00 * g1 - j10 * g0) / dj;
+                    u -= du;
+                    v -= dv;
+                    if (du * du + dv * dv <= 1e-26) {
+                        converged = 1;
+                        break;
+                    }
+                }
+                for (int it = 0; !polishing && it < n_it; it++) {
                     double mw = 0.0;
                     for (int b = 0; b < ps; b++)
                         for (int a = 0; a < ps; a++) {
@@ -334,6 +417,7 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
                     v -= dv;
                     if (term_eps > 0.0 && du * du + dv * dv <= term_eps * term_eps) break;
                 }
+                if (polishing) note(converged);
                 double ex = u - ui[0], ey = v - ui[1];
                 if (sqrt(ex * ex + ey * ey) > (double)ps) {
                     st = OR_PATCH_RESET;
@@ -349,6 +433,8 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
     free(T);
     free(gx);
     free(gy);
+    free(T2x);
+    free(T2y);
     free(wv);
 }
 
@@ -754,7 +840,7 @@ int or_dis_flow_fb(const double* I0, const double* I1, int W, int H, const or_pa
             or_sobel(A[d], w, h, Ix, Iy);
             or_search_level(A[d], Ix, Iy, B[d], w, h, Uc[d], wc, hc, cs, ps, stride, p->grad_iters,
                             frozen ? frozen + 2 * off : NULL, u[d], ui, NULL, p->dof, p->norm, p->huber_b,
-                            p->term_eps);
+                            p->term_eps, p->polish);
             if (record && d == 0)
                 for (int k = 0; k < 2 * np; k++) record[2 * off + k] = u[d][k] - ui[k];
             free(Ix);

@@ -822,3 +822,45 @@ def test_early_termination_stops_at_the_closed_form_iteration():
     one, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 1)
     big, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 50, term_eps=1e9)
     assert np.array_equal(one, big)
+
+
+# ---- the converged search of the differentiable form's implicit gradient ----
+
+def test_polished_search_finds_the_exact_translation_of_a_bilinear_scene():
+    # g(u) = sum S' (w~ - T) vanishes exactly at u = t on a bilinear image; Newton from any
+    # nearby start lands there, wherever the frozen increment left the patch
+    h = w = 48
+    c3 = 0.3
+    c = (5.0 + c3 * 20 * 21, -c3 * 21, -c3 * 20, c3)
+    t = np.array([0.7, -0.4])
+    I0, I1, gx, gy = _bilinear_scene(h, w, c, t)
+    ps, st_ = 8, 8
+    n = oracle.grid_n(w, ps, st_) ** 2
+    g = np.random.default_rng(61)
+    frozen = t + g.uniform(-0.3, 0.3, (n, 2))
+    u, _, st = oracle.search_level(I0, gx, gy, I1, ps, st_, 0, frozen=frozen, polish=50)
+    inner = [_patch_index(w, ps, st_, px, py) for px in (8, 16, 24, 32) for py in (8, 16, 24, 32)]
+    assert np.abs(u.reshape(-1, 2)[inner] - t).max() < 1e-12
+    # a zero increment stands for a patch that did not move: it stays at u_init
+    z = frozen.copy()
+    z[inner[0]] = 0.0
+    u2, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 0, frozen=z, polish=50)
+    assert np.array_equal(u2.reshape(-1, 2)[inner[0]], [0.0, 0.0])
+
+
+def test_polished_search_equals_the_long_fixed_point_iteration():
+    # the root of g is the fixed point of the update: where 20000 plain iterations have settled,
+    # Newton from a 30-iteration start reaches the same flow
+    g = np.random.default_rng(62)
+    h, w = 40, 48
+    I0 = ndimage.gaussian_filter(g.standard_normal((h, w)), 2.0) * 40 + 120
+    I1 = ndimage.shift(I0, (0.35, -0.6), order=3, mode="nearest")
+    gx, gy = oracle.sobel(I0)
+    ps, st_ = 8, 4
+    long_a, _, sa = oracle.search_level(I0, gx, gy, I1, ps, st_, 20000)
+    long_b, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 20001)
+    short, ui, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 30)
+    pol, _, _ = oracle.search_level(I0, gx, gy, I1, ps, st_, 0, frozen=(short - ui).reshape(-1, 2), polish=100)
+    settled = (np.abs(long_a - long_b).max(-1) < 1e-12) & (sa == 0)
+    assert settled.mean() > 0.8
+    assert np.abs(pol - long_a)[settled].max() < 1e-9
