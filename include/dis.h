@@ -77,6 +77,10 @@ typedef struct dis_params {
                               * other direction's patches (dis_densify_level_fb); n pairs take 2 n of
                               * the handle's max_batch slots; no initial flow, recorded / frozen
                               * increments or checkpoints (DIS_ERR_NOT_SUPPORTED); 0: off */
+    int32_t search_grad;     /* differentiable form (dis_backward): 0 treats the recorded search
+                              * increments as constants (stop-gradient through the search); 1 takes
+                              * the implicit-function gradient of the converged search at every patch
+                              * with a nonzero increment (L2 norm only) */
 } dis_params;
 
 /* Presets for dis_default_params.  OP1..OP4 are the paper's operating points

@@ -20,7 +20,12 @@ def _level_dims(w, h, s):
 
 class DifferentiableDIS:
     """Grayscale DIS with gradients w.r.t. I0, I1 (H, W float32 CUDA, [0, 1]) and the initial
-    flow (level theta_ss resolution, (h_ss, w_ss, 2)).  finest_scale must be 0."""
+    flow (level theta_ss resolution, (h_ss, w_ss, 2)).  finest_scale must be 0.
+
+    The patch searches are replayed from their recorded increments (recorded by the FP32 search
+    of each call, or given as `frozen`, dis_levels' total_patches x 2).  search_grad=0 (default)
+    treats the increments as constants; search_grad=1 differentiates the converged search by the
+    implicit-function theorem (pass increments of converged searches)."""
 
     def __init__(self, max_w, max_h, preset="default", **overrides):
         self.params = dis.dis_default_params(preset, channels=1, **overrides)
@@ -42,22 +47,27 @@ class DifferentiableDIS:
         ws, hs = _level_dims(w, h, ss)
         return hs, ws
 
-    def __call__(self, I0, I1, init_flow=None):
-        return _DISFlow.apply(I0, I1, init_flow, self)
+    def __call__(self, I0, I1, init_flow=None, frozen=None):
+        return _DISFlow.apply(I0, I1, init_flow, self, frozen)
 
 
 class _DISFlow(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, I0, I1, init_flow, owner):
+    def forward(ctx, I0, I1, init_flow, owner, frozen=None):
         I0c, I1c = I0.detach().contiguous(), I1.detach().contiguous()
         H, W = I0c.shape
         p = owner.params
         n = dis.dis_levels(W, H, p)[2]
-        rec = torch.empty((n, 2), device=I0c.device, dtype=torch.float32)
-        tmp = torch.empty((H, W, 2), device=I0c.device, dtype=torch.float32)
         init = None if init_flow is None else init_flow.detach().contiguous()
-        # the FP32 search records every patch's increment ...
-        dis.dis_compute_flow_ex(owner.handle, I0c, I1c, W, H, W, p, init, None, rec, None, tmp)
+        if frozen is None:
+            # the FP32 search records every patch's increment ...
+            rec = torch.empty((n, 2), device=I0c.device, dtype=torch.float32)
+            tmp = torch.empty((H, W, 2), device=I0c.device, dtype=torch.float32)
+            dis.dis_compute_flow_ex(owner.handle, I0c, I1c, W, H, W, p, init, None, rec, None, tmp)
+        else:
+            rec = frozen.detach().to(device=I0c.device, dtype=torch.float32).contiguous()
+            if tuple(rec.shape) != (n, 2):
+                raise ValueError("frozen increments must be (%d, 2)" % n)
         # ... and the map with those increments frozen is evaluated in FP64
         nbytes = dis.dis_backward_workspace_bytes(W, H, p)
         ws = torch.empty(nbytes, device=I0c.device, dtype=torch.uint8)
@@ -80,7 +90,7 @@ class _DISFlow(torch.autograd.Function):
         gInit = torch.empty_like(init) if ctx.has_init else None
         dis.dis_backward(owner.handle, I0, I1, W, H, W, p, it, rec, grad_flow.contiguous(), gI0, gI1, W, gInit, ws,
                          nbytes)
-        return gI0, gI1, gInit, None
+        return gI0, gI1, gInit, None, None
 
 
 class _PhotometricLoss(torch.autograd.Function):

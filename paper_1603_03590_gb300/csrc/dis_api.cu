@@ -103,6 +103,10 @@ dis_status validate(const dis_params* p, std::string& err)
         err = "term_eps must be finite and >= 0";
         return DIS_ERR_INVALID_ARG;
     }
+    if (p->search_grad != 0 && p->search_grad != 1) {
+        err = "search_grad must be 0 or 1";
+        return DIS_ERR_INVALID_ARG;
+    }
     return DIS_OK;
 }
 

@@ -27,8 +27,8 @@ size_t al(size_t v) { return (v + kAl - 1) / kAl * kAl; }
 struct BwdLayout {
     int ss = 0, sf = 0;
     std::vector<int> w, h, pitch, outer, np;
-    // accumulators first (one memset): per level gS0, gS1acc, gUacc, then gInit
-    std::vector<size_t> gS0, gS1acc, gUacc;
+    // accumulators first (one memset): per level gS0, gS1acc, gUacc, gS0acc, then gInit
+    std::vector<size_t> gS0, gS1acc, gUacc, gS0acc;
     size_t gInit = 0, acc_end = 0;
     // per level state
     std::vector<size_t> S0, S1, Ud, U, pu, gS1f, gU;
@@ -61,6 +61,7 @@ dis_status layout(int W, int H, const dis_params& p, BwdLayout& L, std::string& 
         L.gS0.push_back(take(sizeof(double) * plane));
         L.gS1acc.push_back(take(sizeof(unsigned long long) * plane));
         L.gUacc.push_back(take(sizeof(unsigned long long) * 2 * pix));
+        L.gS0acc.push_back(take(sizeof(unsigned long long) * plane));
     }
     L.gInit = take(sizeof(unsigned long long) * 2 * L.w[L.ss] * L.h[L.ss]);
     L.acc_end = off;
@@ -197,6 +198,8 @@ dis_status check_common(dis_handle* hd, const float* I0, const float* I1, int W,
     if (p->finest_scale != 0) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: finest_scale must be 0");
     if (p->dof != 2) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: dof must be 2 (optical flow)");
     if (p->fb) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: no forward-backward consistency");
+    if (p->search_grad && p->norm != 0)
+        return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "implicit search gradient: L2 search norm only");
     if (!I0 || !I1 || !frozen || !workspace || W < 1 || H < 1 || pitch < W)
         return set_fail(hd, DIS_ERR_INVALID_ARG, "differentiable form: bad pointer, size or pitch");
     if ((st = layout(W, H, *p, L, err)) != DIS_OK) return set_fail(hd, st, err);
@@ -325,6 +328,12 @@ dis_status dis_backward(dis_handle* hd, const float* I0, const float* I1, int W,
         }
         const dis::Dens64 A = c.dens(sl);
         if (e == cudaSuccess) e = dis::launch_dens_bwd(lv, A, lc, s);
+        if (e == cudaSuccess && c.p.search_grad) {
+            long long off = 0;  // increments of coarser levels come first
+            for (int q = L.ss; q > sl; --q) off += L.np[q];
+            e = dis::launch_search_ift_bwd(lv, A, reinterpret_cast<const float2*>(frozen) + off, c.U64(L.gS0acc[sl]),
+                                           lc, s);
+        }
         if (e == cudaSuccess) {
             if (sl < L.ss)
                 e = dis::launch_uinit_bwd(A, w, h, c.U64(L.gUacc[sl + 1]), L.w[sl + 1], L.h[sl + 1], 2.0, lc, s);
@@ -333,9 +342,13 @@ dis_status dis_backward(dis_handle* hd, const float* I0, const float* I1, int W,
         }
     }
     // level images: fixed point -> double, then the pyramid transpose down to level 0
-    for (int sl = 0; sl <= L.ss && e == cudaSuccess; ++sl)
+    for (int sl = 0; sl <= L.ss && e == cudaSuccess; ++sl) {
         e = dis::launch_fx_to_double(c.U64(L.gS1acc[sl]), L.pitch[sl], c.D(L.gS1f[sl]), L.pitch[sl], L.w[sl], L.h[sl],
                                      1.0, false, lc, s);
+        if (e == cudaSuccess && c.p.search_grad)
+            e = dis::launch_fx_to_double(c.U64(L.gS0acc[sl]), L.pitch[sl], c.D(L.gS0[sl]), L.pitch[sl], L.w[sl],
+                                         L.h[sl], 1.0, true, lc, s);
+    }
     for (int sl = L.ss; sl >= 1 && e == cudaSuccess; --sl) {
         e = dis::launch_pyr_bwd(c.D(L.gS0[sl]), L.w[sl], L.h[sl], L.pitch[sl], c.D(L.gS0[sl - 1]), L.w[sl - 1],
                                 L.h[sl - 1], L.pitch[sl - 1], lc, s);

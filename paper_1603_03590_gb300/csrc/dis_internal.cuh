@@ -248,6 +248,11 @@ cudaError_t launch_start_flow(const Lvl64& L, const double2* g, const LaunchCfg&
 cudaError_t launch_dens_bwd(const Lvl64& L, const Dens64& A, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_uinit_bwd(const Dens64& A, int w, int h, unsigned long long* gUc, int wc, int hc, double cs,
                              const LaunchCfg& lc, cudaStream_t s);
+// Implicit-function gradient of the converged search at every patch with a nonzero frozen
+// increment (see k_adjoint.cu): scatters into L.gS1 and gS0acc (2^-40 fixed point, pitch) and
+// zeroes those patches' A.gpu.
+cudaError_t launch_search_ift_bwd(const Lvl64& L, const Dens64& A, const float2* frozen, unsigned long long* gS0acc,
+                                  const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_pyr_bwd(const double* gc, int wc, int hc, int pc, double* gf, int wf, int hf, int pf,
                            const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_f2_to_d2(const float2* in, double2* out, long long n, const LaunchCfg& lc, cudaStream_t s);

@@ -825,6 +825,85 @@ __global__ void __launch_bounds__(128) dens_bwd_patch_kernel(Lvl64 L, Dens64 A)
 
 // u_init,i = cscale * Uc(c_i / cscale): scatter cscale * weights * g u_i onto Uc (fixed point,
 // two components per pixel).
+// Implicit-function gradient of the converged patch search.  At a patch's solution u the search
+// is stationary: g(u) = sum_q S'_q (w~_q - T_q) = 0 with w~ = w - mean w, w_q = I1(x_q + u)
+// (bilinear), T = I0 patch - its mean, S' = Sobel/8 of I0.  Hence du/dtheta = -J^-1 dg/dtheta,
+// J = sum_q S'_q (grad w_q - mean grad w)^T, and for the patch's upstream gradient gu,
+// lambda = -J^-T gu gives dL/dtheta = lambda . dg/dtheta:
+//   I1 through w_q:      lambda . (S'_q - mean S')        (bilinear scatter at x_q + u)
+//   I0 through T_q:     -lambda . (S'_q - mean S')
+//   I0 through S'_q:     lambda_x r_q, lambda_y r_q       (Sobel transpose), r_q = w~_q - T_q.
+// The solution does not depend on u_init, so the patch's gradient is consumed here (gpu = 0).
+// A zero frozen increment marks a patch that was reset, flat or never moved: it stays at
+// u_init and keeps its gradient for the initial-displacement transpose.  One warp per patch.
+__global__ void __launch_bounds__(128) search_ift_bwd_kernel(Lvl64 L, Dens64 A, const float2* __restrict__ frozen,
+                                                             unsigned long long* __restrict__ gS0acc)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long np = (long long)A.nx * A.ny;
+    const int ps = A.ps, n = ps * ps, w = L.w, h = L.h, pitch = L.pitch;
+    for (long long k = warp; k < np; k += nwarps) {
+        const float2 dz = frozen[k];
+        if (dz.x == 0.0f && dz.y == 0.0f) continue;
+        const int j = (int)(k / A.nx), i = (int)(k - (long long)j * A.nx);
+        const int px = min(i * A.stride, w - ps), py = min(j * A.stride, h - ps);
+        const double2 u = A.pu[k];
+        // sums over the patch: I0, w, grad w, S', S' grad w^T
+        double s[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int q = lane; q < n; q += 32) {
+            const int x = px + q % ps, y = py + q / ps;
+            const double gx = sobel_fwd(L.S0, pitch, w, h, x, y, true), gy = sobel_fwd(L.S0, pitch, w, h, x, y, false);
+            const Taps t = taps_at(L.S1, w, h, pitch, x, y, u.x, u.y);
+            s[0] += L.S0[(long long)y * pitch + x];
+            s[1] += t.val;
+            s[2] += t.du;
+            s[3] += t.dv;
+            s[4] += gx;
+            s[5] += gy;
+            s[6] += gx * t.du;
+            s[7] += gx * t.dv;
+            s[8] += gy * t.du;
+            s[9] += gy * t.dv;
+        }
+#pragma unroll
+        for (int m = 0; m < 10; ++m)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[m] += __shfl_xor_sync(0xffffffffu, s[m], o);
+        const double inv_n = 1.0 / n;
+        const double mean0 = s[0] * inv_n, mw = s[1] * inv_n, mdu = s[2] * inv_n, mdv = s[3] * inv_n;
+        const double msx = s[4] * inv_n, msy = s[5] * inv_n;
+        const double j00 = s[6] - s[4] * mdu, j01 = s[7] - s[4] * mdv;  // J = sum S' (grad w - mean)^T
+        const double j10 = s[8] - s[5] * mdu, j11 = s[9] - s[5] * mdv;
+        const double det = j00 * j11 - j01 * j10;
+        if (!(fabs(det) > 0.0)) continue;  // no solution to differentiate: keep the frozen rule
+        const double2 gu = A.gpu[k];
+        // J^T lambda = -gu
+        const double lx = -(j11 * gu.x - j10 * gu.y) / det;
+        const double ly = -(-j01 * gu.x + j00 * gu.y) / det;
+        for (int q = lane; q < n; q += 32) {
+            const int x = px + q % ps, y = py + q / ps;
+            const double gx = sobel_fwd(L.S0, pitch, w, h, x, y, true), gy = sobel_fwd(L.S0, pitch, w, h, x, y, false);
+            const Taps t = taps_at(L.S1, w, h, pitch, x, y, u.x, u.y);
+            const double c = lx * (gx - msx) + ly * (gy - msy);
+            taps_scatter(L.gS1, t, c);
+            fx_add(gS0acc + (long long)y * pitch + x, -c);
+            const double r = (t.val - mw) - (L.S0[(long long)y * pitch + x] - mean0);
+            const double ax = 0.125 * lx * r, ay = 0.125 * ly * r;
+            // Sobel transpose: Ix(x, y) = (1/8) sum kx I0(clamp(x + dx), clamp(y + dy)), likewise Iy
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const double kx = (double)dx * (dy == 0 ? 2.0 : 1.0), ky = (double)dy * (dx == 0 ? 2.0 : 1.0);
+                    const double v = ax * kx + ay * ky;
+                    if (v != 0.0)
+                        fx_add(gS0acc + (long long)clampi(y + dy, 0, h - 1) * pitch + clampi(x + dx, 0, w - 1), v);
+                }
+        }
+        if (lane == 0) A.gpu[k] = make_double2(0.0, 0.0);
+    }
+}
+
 __global__ void __launch_bounds__(256) uinit_bwd_kernel(Dens64 A, int w, int h, unsigned long long* gUc, int wc,
                                                         int hc, double cs)
 {
@@ -1045,6 +1124,16 @@ cudaError_t launch_uinit_bwd(const Dens64& A, int w, int h, unsigned long long* 
                              const LaunchCfg& lc, cudaStream_t s)
 {
     LAUNCH(uinit_bwd_kernel, (long long)A.nx * A.ny, A, w, h, gUc, wc, hc, cs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_search_ift_bwd(const Lvl64& L, const Dens64& A, const float2* frozen, unsigned long long* gS0acc,
+                                  const LaunchCfg& lc, cudaStream_t s)
+{
+    const long long np = (long long)A.nx * A.ny;
+    if (np <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>((np * 32 + 127) / 128, (long long)lc.sm_count * 16);
+    search_ift_bwd_kernel<<<blocks, 128, 0, s>>>(L, A, frozen, gS0acc);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,7 @@ class dis_params(ctypes.Structure):
         ("huber_b", ctypes.c_float),
         ("term_eps", ctypes.c_float),
         ("fb", ctypes.c_int32),
+        ("search_grad", ctypes.c_int32),
     ]
 
 
