@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
         const float* gdu = rs + (long long)src * pl;
         const float* gdv = gdu + pl;
         // U and the increments on R1 (zero outside the image, never used there)
+#pragma unroll 2
         for (int t = threadIdx.x; t < E1; t += kOuterThreads) {
             const int ly = t / S1, lx = t - ly * S1;
             const int x = x1 + lx, y = y1 + ly;
@@ -345,19 +346,27 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
         // its left / right neighbours (the other colour) at the same position minus 1 when lx
         // is even, plus 1 when lx is odd, and its upper / lower ones one half row away.
         float* gsys = J.rs + (long long)rs_sys(C, 0) * pl;
-        for (int t = threadIdx.x; t < E0; t += kOuterThreads) {
+        if constexpr (PHASE == 2) {
+            // the stored systems of the pass's first chunk, with their halo (loads batched)
+#pragma unroll 4
+            for (int t = threadIdx.x; t < E0; t += kOuterThreads) {
+                const int ly = t / S0, lx = t - ly * S0;
+                const int x = x1 + 1 + lx, y = y1 + 1 + ly;
+                if (x < 0 || x >= w || y < 0 || y >= h) continue;
+                const int c0 = ((x + y) & 1) * HE0 + ly * HS0 + (lx >> 1);
+                const long long o = (long long)y * pitch + x;
+                r0[c0] = make_float2(gsys[o], gsys[pl + o]);
+                r0[E0 + c0] = make_float2(gsys[2 * pl + o], gsys[3 * pl + o]);
+                r0[2 * E0 + c0] = make_float2(gsys[4 * pl + o], gsys[5 * pl + o]);
+            }
+        }
+        for (int t = threadIdx.x; PHASE != 2 && t < E0; t += kOuterThreads) {
             const int ly = t / S0, lx = t - ly * S0;
             const int x = x1 + 1 + lx, y = y1 + 1 + ly;
             if (x < 0 || x >= w || y < 0 || y >= h) continue;
             const int c = (x + y) & 1;
             const int c0 = c * HE0 + ly * HS0 + (lx >> 1);
             const long long o = (long long)y * pitch + x;
-            if (PHASE == 2) {
-                r0[c0] = make_float2(gsys[o], gsys[pl + o]);
-                r0[E0 + c0] = make_float2(gsys[2 * pl + o], gsys[3 * pl + o]);
-                r0[2 * E0 + c0] = make_float2(gsys[4 * pl + o], gsys[5 * pl + o]);
-                continue;
-            }
             const int pos = (ly + 1) * HS1 + ((lx + 1) >> 1), oth = (1 - c) * HE1 + pos;
             const int odd = (lx + 1) & 1;
             const float4 me = r1[c * HE1 + pos];
@@ -492,7 +501,7 @@ static cudaError_t launch_outer(const Jobs<LevelJob>& js, long long total_tiles,
     static_assert(KT % KC == 0, "chunks divide the pass");
     for (int ot = 0; ot < a.outer; ++ot) {
         cudaError_t e = cudaSuccess;
-        if (KC == KT) {
+        if constexpr (KC == KT) {
             e = outer_launch<KT, 0>(js, total_tiles, a, src, dst, 0, lc, s);
             std::swap(src, dst);
         } else {
