@@ -20,7 +20,8 @@ def _level_dims(w, h, s):
 
 class DifferentiableDIS:
     """Grayscale DIS with gradients w.r.t. I0, I1 (H, W float32 CUDA, [0, 1]) and the initial
-    flow (level theta_ss resolution, (h_ss, w_ss, 2)).  finest_scale must be 0.
+    flow (level theta_ss resolution, (h_ss, w_ss, 2)).  With finest_scale > 0 the final bilinear
+    up-scaling is part of the map.
 
     The patch searches are replayed from their recorded increments (recorded by the FP32 search
     of each call, or given as `frozen`, dis_levels' total_patches x 2).  search_grad=0 (default)

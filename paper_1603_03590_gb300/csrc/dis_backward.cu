@@ -150,7 +150,7 @@ cudaError_t replay(const Ctx& c, const float* I0, const float* I1, long long pit
         e = dis::launch_f2_to_d2(reinterpret_cast<const float2*>(init), c.D2(L.init64), (long long)L.w[L.ss] * L.h[L.ss],
                                  c.lc, c.s);
     long long off = 0;
-    for (int s = L.ss; s >= 0 && e == cudaSuccess; --s) {
+    for (int s = L.ss; s >= L.sf && e == cudaSuccess; --s) {
         const int w = L.w[s], h = L.h[s];
         const double2* Uc = nullptr;
         int wc = w, hc = h;
@@ -183,6 +183,9 @@ cudaError_t replay(const Ctx& c, const float* I0, const float* I1, long long pit
             e = cudaMemcpyAsync(c.D2(L.U[s]), c.D2(L.Ud[s]), sizeof(double2) * w * h, cudaMemcpyDeviceToDevice, c.s);
         }
     }
+    if (e == cudaSuccess && L.sf > 0)  // final up-scaling to full resolution (Sec. 3.1)
+        e = dis::launch_upsample64(c.D2(L.U[L.sf]), L.w[L.sf], L.h[L.sf], (double)(1 << L.sf), c.D2(L.U[0]), L.w[0],
+                                   L.h[0], c.lc, c.s);
     return e;
 }
 
@@ -195,7 +198,6 @@ dis_status check_common(dis_handle* hd, const float* I0, const float* I1, int W,
     dis_status st = validate_params(p, err);
     if (st != DIS_OK) return set_fail(hd, st, err);
     if (p->channels != 1) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: grayscale (channels = 1) only");
-    if (p->finest_scale != 0) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: finest_scale must be 0");
     if (p->dof != 2) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: dof must be 2 (optical flow)");
     if (p->fb) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: no forward-backward consistency");
     if (p->search_grad && p->norm != 0)
@@ -282,7 +284,10 @@ dis_status dis_backward(dis_handle* hd, const float* I0, const float* I1, int W,
     if (e == cudaSuccess) e = replay(c, I0, I1, pitch, init_flow, frozen);
     if (e == cudaSuccess)
         e = dis::launch_f2_to_d2(reinterpret_cast<const float2*>(grad_flow), c.D2(L.gU[0]), (long long)W * H, lc, s);
-    for (int sl = 0; sl <= L.ss && e == cudaSuccess; ++sl) {
+    if (e == cudaSuccess && L.sf > 0)  // the final up-scaling's transpose into level theta_sf
+        e = dis::launch_upsample_bwd(c.D2(L.gU[0]), W, H, (double)(1 << L.sf), c.U64(L.gUacc[L.sf]), L.w[L.sf],
+                                     L.h[L.sf], lc, s);
+    for (int sl = L.sf; sl <= L.ss && e == cudaSuccess; ++sl) {
         const int w = L.w[sl], h = L.h[sl];
         const long long plane = (long long)L.pitch[sl] * h;
         if (sl > 0) e = dis::launch_fx_to_double(c.U64(L.gUacc[sl]), 2 * w, c.D(L.gU[sl]), 2 * w, 2 * w, h, 1.0, false, lc, s);

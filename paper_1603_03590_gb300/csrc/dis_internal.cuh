@@ -256,6 +256,12 @@ cudaError_t launch_search_ift_bwd(const Lvl64& L, const Dens64& A, const float2*
 cudaError_t launch_pyr_bwd(const double* gc, int wc, int hc, int pc, double* gf, int wf, int hf, int pf,
                            const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_f2_to_d2(const float2* in, double2* out, long long n, const LaunchCfg& lc, cudaStream_t s);
+// FP64 final up-scaling (out = factor * in(x / factor), bilinear, clamped) and its transpose,
+// accumulated into gin (2^-40 fixed point, dense wi*hi*2).
+cudaError_t launch_upsample64(const double2* in, int wi, int hi, double factor, double2* out, int wo, int ho,
+                              const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_upsample_bwd(const double2* gout, int wo, int ho, double factor, unsigned long long* gin, int wi,
+                                int hi, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_d2_to_f2(const double2* in, float2* out, long long n, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_scale_out(const double* in, int ipitch, float* out, int opitch, int w, int h, double scale,
                              const LaunchCfg& lc, cudaStream_t s);

@@ -965,6 +965,36 @@ __global__ void __launch_bounds__(256) start_flow_kernel(Lvl64 L, const double2*
     PIX_END
 }
 
+// Final up-scaling (Sec. 3.1): out(x) = factor * in(x / factor), bilinear with clamping, and its
+// transpose (fixed-point scatter into the coarse field's accumulator).
+__global__ void __launch_bounds__(256) upsample64_kernel(const double2* __restrict__ in, int wi, int hi, double factor,
+                                                         double2* out, int wo, int ho)
+{
+    PIX_LOOP(wo, ho)
+    const FlowTaps t = flow_taps(wi, hi, x / factor, y / factor);
+    const double2 a = in[t.i00], b = in[t.i10], c = in[t.i01], d = in[t.i11];
+    out[g] = make_double2(factor * (t.w00 * a.x + t.w10 * b.x + t.w01 * c.x + t.w11 * d.x),
+                          factor * (t.w00 * a.y + t.w10 * b.y + t.w01 * c.y + t.w11 * d.y));
+    PIX_END
+}
+
+__global__ void __launch_bounds__(256) upsample_bwd_kernel(const double2* __restrict__ gout, int wo, int ho,
+                                                           double factor, unsigned long long* gin, int wi, int hi)
+{
+    PIX_LOOP(wo, ho)
+    const FlowTaps t = flow_taps(wi, hi, x / factor, y / factor);
+    const double2 gk = gout[g];
+    fx_add(gin + 2 * t.i00, factor * t.w00 * gk.x);
+    fx_add(gin + 2 * t.i00 + 1, factor * t.w00 * gk.y);
+    fx_add(gin + 2 * t.i10, factor * t.w10 * gk.x);
+    fx_add(gin + 2 * t.i10 + 1, factor * t.w10 * gk.y);
+    fx_add(gin + 2 * t.i01, factor * t.w01 * gk.x);
+    fx_add(gin + 2 * t.i01 + 1, factor * t.w01 * gk.y);
+    fx_add(gin + 2 * t.i11, factor * t.w11 * gk.x);
+    fx_add(gin + 2 * t.i11 + 1, factor * t.w11 * gk.y);
+    PIX_END
+}
+
 __global__ void __launch_bounds__(256) f2_to_d2_kernel(const float2* __restrict__ in, double2* out, long long n)
 {
     for (long long g = gtid(); g < n; g += gstride()) out[g] = make_double2((double)in[g].x, (double)in[g].y);
@@ -1141,6 +1171,20 @@ cudaError_t launch_pyr_bwd(const double* gc, int wc, int hc, int pc, double* gf,
                            const LaunchCfg& lc, cudaStream_t s)
 {
     LAUNCH(pyr_bwd_kernel, (long long)wf * hf, gc, wc, hc, pc, gf, wf, hf, pf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upsample64(const double2* in, int wi, int hi, double factor, double2* out, int wo, int ho,
+                              const LaunchCfg& lc, cudaStream_t s)
+{
+    LAUNCH(upsample64_kernel, (long long)wo * ho, in, wi, hi, factor, out, wo, ho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upsample_bwd(const double2* gout, int wo, int ho, double factor, unsigned long long* gin, int wi,
+                                int hi, const LaunchCfg& lc, cudaStream_t s)
+{
+    LAUNCH(upsample_bwd_kernel, (long long)wo * ho, gout, wo, ho, factor, gin, wi, hi);
     return cudaGetLastError();
 }
 

@@ -193,3 +193,70 @@ def test_batch_of_eight_pairs(env):
         assert np.isfinite(total)
     finally:
         dd.close()
+
+
+def test_adjoint_with_final_upscaling_matches_fd(env):
+    """theta_sf = 1: the map ends with the bilinear up-scaling of level 1 to full resolution, and
+    the backward starts with its transpose."""
+    torch, dis, ag, dev = env
+    W, H = 256, 128
+    kw = dict(PARAMS, coarsest_scale=3, finest_scale=1)
+    I0, I1, _ = synth.layered_pair(3002, width=W, height=H, max_disp=10.0)
+    dd = ag.DifferentiableDIS(W, H, **kw)
+    try:
+        hs, ws = dd.coarsest_shape(W, H)
+        from scipy import ndimage
+        g = np.random.default_rng(9)
+        init = np.stack([ndimage.gaussian_filter(g.normal(0, 1.0, (hs, ws)), 2.0) for _ in range(2)], -1)
+        init = init.astype(np.float32)
+        a = torch.tensor(I0, device=dev, requires_grad=True)
+        b = torch.tensor(I1, device=dev, requires_grad=True)
+        it = torch.tensor(init, device=dev, requires_grad=True)
+        flow = dd(a, b, it)
+        loss = ag.photometric_loss(a, b, flow)
+        loss.backward()
+        grads = {"I0": a.grad.cpu().numpy().astype(np.float64), "I1": b.grad.cpu().numpy().astype(np.float64),
+                 "init": it.grad.cpu().numpy().astype(np.float64)}
+        n = dis.dis_levels(W, H, dd.params)[2]
+        rec = torch.empty((n, 2), device=dev)
+        tmp = torch.empty((H, W, 2), device=dev)
+        dis.dis_compute_flow_ex(dd.handle, a.detach(), b.detach(), W, H, W, dd.params, it.detach(), None, rec, None,
+                                tmp)
+        torch.cuda.synchronize()
+        dflow = (tmp - flow.detach()).abs()
+        assert float(dflow.mean()) <= 0.01 and float(torch.quantile(dflow.flatten(), 0.999)) <= 0.05
+        rec = rec.cpu().numpy().astype(np.float64)
+    finally:
+        dd.close()
+    rng = np.random.default_rng(77)
+    coords = ([("I0", int(i)) for i in rng.integers(0, I0.size, 50)] +
+              [("I1", int(i)) for i in rng.integers(0, I1.size, 50)] +
+              [("init", int(i)) for i in rng.integers(0, init.size, 20)])
+    steps = (H_STEP, -H_STEP, 0.5 * H_STEP, -0.5 * H_STEP)
+    tasks = [(k, i, st) for k, i in coords for st in steps] + [("I0", 0, 0.0)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1), initializer=_init_worker,
+                  initargs=(I0.astype(np.float64), I1.astype(np.float64), rec, init.astype(np.float64), kw)) as pool:
+        res = pool.map(_fd_task, tasks, chunksize=4)
+    h0 = res[-1][1]
+    flips, unconverged, errs = 0, 0, []
+    for c, (k, i) in enumerate(coords):
+        (lp, hp), (lm, hm), (lp2, hp2), (lm2, hm2) = res[4 * c:4 * c + 4]
+        if hp2 != h0 or hm2 != h0:
+            flips += 1
+            continue
+        fd = (lp - lm) / (2 * H_STEP)
+        fd2 = (lp2 - lm2) / H_STEP
+        an = grads[k].reshape(-1)[i]
+        if abs(fd - fd2) > 0.3 * REL_TOL * max(abs(fd), 1e-12):
+            unconverged += 1
+            continue
+        errs.append((abs(an - fd) / max(abs(fd), 1e-12), k, i, an, fd))
+    errs.sort(reverse=True)
+    print("adjoint with theta_sf = 1 vs FD: %d compared, %d flips, %d unconverged; worst: %s"
+          % (len(errs), flips, unconverged, errs[:5]))
+    assert len(errs) >= 40
+    mags = np.array([abs(e[4]) for e in errs])
+    floor = 1e-3 * np.median(mags)
+    bad = [e for e in errs if abs(e[3] - e[4]) > REL_TOL * max(abs(e[4]), floor)]
+    assert not bad, bad[:10]
