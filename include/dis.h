@@ -363,9 +363,9 @@ dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, flo
  * (record_out); dis_replay_flow evaluates F and dis_backward its gradient.  Both compute in
  * double precision: the refinement's robust weights Psi'(a^2) = 1 / (2 sqrt(a^2 + eps^2))
  * (eps = 0.001) make the gradient depend on flow and residual differences near 1e-6, below the
- * resolution of FP32 flow values.  Grayscale and dof == 2 only (DIS_ERR_NOT_SUPPORTED
- * otherwise); with finest_scale > 0 the final bilinear up-scaling (and its transpose) is part of
- * F.  The search norm does not enter F (it only decides the recorded increments).  frozen: dis_levels' total_patches x 2 floats, coarsest level first; init_flow
+ * resolution of FP32 flow values.  Grayscale only (DIS_ERR_NOT_SUPPORTED otherwise; no
+ * forward-backward consistency); with finest_scale > 0 the final bilinear up-scaling (and its
+ * transpose) is part of F, with dof 1 the stereo refinement.  The search norm does not enter F (it only decides the recorded increments).  frozen: dis_levels' total_patches x 2 floats, coarsest level first; init_flow
  * (nullable): level theta_ss resolution, dense, 2 floats per pixel.  Nothing is allocated: the
  * caller passes a device workspace of dis_backward_workspace_bytes bytes. */
 

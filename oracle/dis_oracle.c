@@ -287,7 +287,8 @@ static void init_at(const double* Uc, int wc, int hc, double cscale, double x, d
  * (the fixed point of the update: du = H'^-1 g) by Newton steps u <- u - J^-1 g with
  * J = dg/du = sum_q S'_q (grad w_q - mean grad w)^T (the bilinear interpolant's derivative,
  * 0 across a clamped coordinate), until a step is below 1e-13 px (at most `polish` steps;
- * whether it got there joins the decision trace); then the reset test.  This is the converged
+ * whether it got there joins the decision trace; a patch that does not get there has no
+ * solution and returns to u_init); then the reset test.  This is the converged
  * search, whose solution depends on the frames and not on where it started; the
  * differentiable form's implicit-function gradient is the derivative of this map. */
 void or_search_level(const double* I0, const double* Ix, const double* Iy, const double* I1, int w, int h,
@@ -380,10 +381,16 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
                         j10 += gy[q] * (T2x[q] - mgx);
                         j11 += gy[q] * (T2y[q] - mgy);
                     }
-                    double dj = j00 * j11 - j01 * j10;
-                    if (!(fabs(dj) > 0.0)) break;
-                    double du = (j11 * g0 - j01 * g1) / dj;
-                    double dv = (j00 * g1 - j10 * g0) / dj;
+                    double du, dv = 0.0;
+                    if (dof == 1) { /* [R20] v stays: the scalar root of g_x in u */
+                        if (!(fabs(j00) > 0.0)) break;
+                        du = g0 / j00;
+                    } else {
+                        double dj = j00 * j11 - j01 * j10;
+                        if (!(fabs(dj) > 0.0)) break;
+                        du = (j11 * g0 - j01 * g1) / dj;
+                        dv = (j00 * g1 - j10 * g0) / dj;
+                    }
                     u -= du;
                     v -= dv;
                     if (du * du + dv * dv <= 1e-26) {
@@ -417,7 +424,17 @@ void or_search_level(const double* I0, const double* Ix, const double* Iy, const
                     v -= dv;
                     if (term_eps > 0.0 && du * du + dv * dv <= term_eps * term_eps) break;
                 }
-                if (polishing) note(converged);
+                if (polishing) {
+                    /* the solution's bilinear cell joins the trace: g is only piecewise smooth in
+                     * u, so a root that crosses a cell boundary under a perturbation is a kink */
+                    note(converged);
+                    note((int64_t)floor(u));
+                    note((int64_t)floor(v));
+                    if (!converged) { /* no root found (Newton cycles or stalls): no solution */
+                        u = ui[0];
+                        v = ui[1];
+                    }
+                }
                 double ex = u - ui[0], ey = v - ui[1];
                 if (sqrt(ex * ex + ey * ey) > (double)ps) {
                     st = OR_PATCH_RESET;

@@ -114,6 +114,7 @@ struct Ctx {
         v.gamma = p.gamma;
         v.alpha = p.alpha;
         v.omega = p.sor_omega;
+        v.dof = p.dof;
         return v;
     }
     dis::Dens64 dens(int s) const
@@ -198,7 +199,6 @@ dis_status check_common(dis_handle* hd, const float* I0, const float* I1, int W,
     dis_status st = validate_params(p, err);
     if (st != DIS_OK) return set_fail(hd, st, err);
     if (p->channels != 1) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: grayscale (channels = 1) only");
-    if (p->dof != 2) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: dof must be 2 (optical flow)");
     if (p->fb) return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "differentiable form: no forward-backward consistency");
     if (p->search_grad && p->norm != 0)
         return set_fail(hd, DIS_ERR_NOT_SUPPORTED, "implicit search gradient: L2 search norm only");
@@ -337,7 +337,7 @@ dis_status dis_backward(dis_handle* hd, const float* I0, const float* I1, int W,
             long long off = 0;  // increments of coarser levels come first
             for (int q = L.ss; q > sl; --q) off += L.np[q];
             e = dis::launch_search_ift_bwd(lv, A, reinterpret_cast<const float2*>(frozen) + off, c.U64(L.gS0acc[sl]),
-                                           lc, s);
+                                           c.p.dof, lc, s);
         }
         if (e == cudaSuccess) {
             if (sl < L.ss)

@@ -210,6 +210,7 @@ struct Lvl64 {
     long long plane;
     int w, h, pitch;
     double delta, gamma, alpha, omega;
+    int dof;  // 1: stereo, the SOR solves the scalar x equation and dv stays 0
 };
 
 struct Dens64 {
@@ -252,7 +253,7 @@ cudaError_t launch_uinit_bwd(const Dens64& A, int w, int h, unsigned long long* 
 // increment (see k_adjoint.cu): scatters into L.gS1 and gS0acc (2^-40 fixed point, pitch) and
 // zeroes those patches' A.gpu.
 cudaError_t launch_search_ift_bwd(const Lvl64& L, const Dens64& A, const float2* frozen, unsigned long long* gS0acc,
-                                  const LaunchCfg& lc, cudaStream_t s);
+                                  int dof, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_pyr_bwd(const double* gc, int wc, int hc, int pc, double* gf, int wf, int hf, int pf,
                            const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_f2_to_d2(const float2* in, double2* out, long long n, const LaunchCfg& lc, cudaStream_t s);

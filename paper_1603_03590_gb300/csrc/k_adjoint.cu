@@ -341,6 +341,10 @@ __global__ void __launch_bounds__(256) ref64_sor_kernel(Lvl64 L, int colour)
             r2 = fma(wq, (Uq.y + dv_p[oq]) - Up.y, r2);
         }
         const double m11 = S[o] + sw, m12 = S[pl + o], m22 = S[2 * pl + o] + sw;
+        if (L.dof == 1) {  // stereo: the scalar x equation, dv stays
+            if (m11 > 0.0) du_p[o] = (1.0 - L.omega) * du_p[o] + L.omega * (r1 / m11);
+            continue;
+        }
         const double det = m11 * m22 - m12 * m12;
         if (det > 0.0) {
             const double d1 = (m22 * r1 - m12 * r2) / det, d2 = (m11 * r2 - m12 * r1) / det;
@@ -460,21 +464,39 @@ __global__ void __launch_bounds__(256) sor_bwd_p_kernel(Lvl64 L, const double* _
             r2 = fma(wq[q], dyq[q], r2);
         }
         const double m11 = S[o] + sw, m12 = S[pl + o], m22 = S[2 * pl + o] + sw;
-        const double det = m11 * m22 - m12 * m12;
-        if (!(det > 0.0)) {
-            T[o] = T[pl + o] = T[2 * pl + o] = 0.0;
-            continue;
+        double d1, d2, gr1, gr2;
+        if (L.dof == 1) {
+            // stereo: du = (1 - omega) du + omega r1 / m11; dv (and its adjoint) pass unchanged
+            if (!(m11 > 0.0)) {
+                T[o] = T[pl + o] = T[2 * pl + o] = 0.0;
+                continue;
+            }
+            d1 = r1 / m11;
+            d2 = 0.0;
+            gr1 = L.omega * gdu[o] / m11;
+            gr2 = 0.0;
+            gdu[o] *= (1.0 - L.omega);
+            gS[o] -= gr1 * d1;
+            gS[3 * pl + o] += gr1;
+        } else {
+            const double det = m11 * m22 - m12 * m12;
+            if (!(det > 0.0)) {
+                T[o] = T[pl + o] = T[2 * pl + o] = 0.0;
+                continue;
+            }
+            d1 = (m22 * r1 - m12 * r2) / det;
+            d2 = (m11 * r2 - m12 * r1) / det;
+            const double gd1 = L.omega * gdu[o], gd2 = L.omega * gdv[o];
+            gr1 = (m22 * gd1 - m12 * gd2) / det;
+            gr2 = (m11 * gd2 - m12 * gd1) / det;
+            gdu[o] *= (1.0 - L.omega);
+            gdv[o] *= (1.0 - L.omega);
+            gS[o] -= gr1 * d1;
+            gS[pl + o] -= gr1 * d2 + gr2 * d1;
+            gS[2 * pl + o] -= gr2 * d2;
+            gS[3 * pl + o] += gr1;
+            gS[4 * pl + o] += gr2;
         }
-        const double d1 = (m22 * r1 - m12 * r2) / det, d2 = (m11 * r2 - m12 * r1) / det;
-        const double gd1 = L.omega * gdu[o], gd2 = L.omega * gdv[o];
-        const double gr1 = (m22 * gd1 - m12 * gd2) / det, gr2 = (m11 * gd2 - m12 * gd1) / det;
-        gdu[o] *= (1.0 - L.omega);
-        gdv[o] *= (1.0 - L.omega);
-        gS[o] -= gr1 * d1;
-        gS[pl + o] -= gr1 * d2 + gr2 * d1;
-        gS[2 * pl + o] -= gr2 * d2;
-        gS[3 * pl + o] += gr1;
-        gS[4 * pl + o] += gr2;
         const double gsw = -(gr1 * d1 + gr2 * d2);
         double gps = 0.0, gux = 0.0, guy = 0.0;
         for (int q = 0; q < 4; ++q) {
@@ -834,10 +856,14 @@ __global__ void __launch_bounds__(128) dens_bwd_patch_kernel(Lvl64 L, Dens64 A)
 //   I0 through T_q:     -lambda . (S'_q - mean S')
 //   I0 through S'_q:     lambda_x r_q, lambda_y r_q       (Sobel transpose), r_q = w~_q - T_q.
 // The solution does not depend on u_init, so the patch's gradient is consumed here (gpu = 0).
+// dof 1 (stereo): g = sum S'_x (w~ - T) in u alone, J = its scalar derivative, lambda_y = 0; v is
+// u_init's, and the solution u depends on it through g (the samples at x + (u, v)), so v's
+// gradient gains lambda_x dg/dv = lambda_x sum S'_x (dw/dv - mean dw/dv) before it goes on to the
+// initial-displacement transpose.
 // A zero frozen increment marks a patch that was reset, flat or never moved: it stays at
 // u_init and keeps its gradient for the initial-displacement transpose.  One warp per patch.
 __global__ void __launch_bounds__(128) search_ift_bwd_kernel(Lvl64 L, Dens64 A, const float2* __restrict__ frozen,
-                                                             unsigned long long* __restrict__ gS0acc)
+                                                             unsigned long long* __restrict__ gS0acc, int dof)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -876,12 +902,20 @@ __global__ void __launch_bounds__(128) search_ift_bwd_kernel(Lvl64 L, Dens64 A, 
         const double msx = s[4] * inv_n, msy = s[5] * inv_n;
         const double j00 = s[6] - s[4] * mdu, j01 = s[7] - s[4] * mdv;  // J = sum S' (grad w - mean)^T
         const double j10 = s[8] - s[5] * mdu, j11 = s[9] - s[5] * mdv;
-        const double det = j00 * j11 - j01 * j10;
-        if (!(fabs(det) > 0.0)) continue;  // no solution to differentiate: keep the frozen rule
         const double2 gu = A.gpu[k];
-        // J^T lambda = -gu
-        const double lx = -(j11 * gu.x - j10 * gu.y) / det;
-        const double ly = -(-j01 * gu.x + j00 * gu.y) / det;
+        double lx, ly;
+        if (dof == 1) {
+            // stereo: g = sum S'_x (w~ - T) = 0 in u alone; v is u_init's and keeps its gradient
+            if (!(fabs(j00) > 0.0)) continue;
+            lx = -gu.x / j00;
+            ly = 0.0;
+        } else {
+            const double det = j00 * j11 - j01 * j10;
+            if (!(fabs(det) > 0.0)) continue;  // no solution to differentiate: keep the frozen rule
+            // J^T lambda = -gu
+            lx = -(j11 * gu.x - j10 * gu.y) / det;
+            ly = -(-j01 * gu.x + j00 * gu.y) / det;
+        }
         for (int q = lane; q < n; q += 32) {
             const int x = px + q % ps, y = py + q / ps;
             const double gx = sobel_fwd(L.S0, pitch, w, h, x, y, true), gy = sobel_fwd(L.S0, pitch, w, h, x, y, false);
@@ -900,7 +934,7 @@ __global__ void __launch_bounds__(128) search_ift_bwd_kernel(Lvl64 L, Dens64 A, 
                         fx_add(gS0acc + (long long)clampi(y + dy, 0, h - 1) * pitch + clampi(x + dx, 0, w - 1), v);
                 }
         }
-        if (lane == 0) A.gpu[k] = make_double2(0.0, 0.0);
+        if (lane == 0) A.gpu[k] = make_double2(0.0, dof == 1 ? fma(lx, j01, gu.y) : 0.0);
     }
 }
 
@@ -1158,12 +1192,12 @@ cudaError_t launch_uinit_bwd(const Dens64& A, int w, int h, unsigned long long* 
 }
 
 cudaError_t launch_search_ift_bwd(const Lvl64& L, const Dens64& A, const float2* frozen, unsigned long long* gS0acc,
-                                  const LaunchCfg& lc, cudaStream_t s)
+                                  int dof, const LaunchCfg& lc, cudaStream_t s)
 {
     const long long np = (long long)A.nx * A.ny;
     if (np <= 0) return cudaSuccess;
     const int blocks = (int)std::min<long long>((np * 32 + 127) / 128, (long long)lc.sm_count * 16);
-    search_ift_bwd_kernel<<<blocks, 128, 0, s>>>(L, A, frozen, gS0acc);
+    search_ift_bwd_kernel<<<blocks, 128, 0, s>>>(L, A, frozen, gS0acc, dof);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,10 @@ def _init_worker(I0, I1, rec, init, kw):
     _W.update(I0=I0, I1=I1, rec=rec, init=init, q=oracle.params(polish=POLISH, **kw))
 
 
+def _init_worker_kw(I0, I1, rec, init, kw):
+    _W.update(I0=I0, I1=I1, rec=rec, init=init, q=oracle.params(**kw))
+
+
 def _fd_task(task):
     kind, idx, step = task
     I0, I1, init = _W["I0"].copy(), _W["I1"].copy(), _W["init"].copy()
@@ -132,6 +136,81 @@ def test_implicit_search_gradient_matches_fp64_finite_differences(env):
           "within h/2, %d whose FD has not converged at that step; worst: %s"
           % (H_STEP, len(errs), flips, unconverged, errs[:5]))
     assert len(errs) >= 60
+    mags = np.array([abs(e[4]) for e in errs])
+    floor = 1e-3 * np.median(mags)
+    bad = [e for e in errs if abs(e[3] - e[4]) > REL_TOL * max(abs(e[4]), floor)]
+    assert not bad, bad[:10]
+
+
+@pytest.mark.parametrize("search_grad", [0, 1])
+def test_stereo_gradient_matches_fp64_finite_differences(env, search_grad):
+    """The differentiable form in the stereo mode (one degree of freedom: the scalar SOR update in
+    the replay and its adjoint), with the search frozen or differentiated implicitly (the scalar
+    stationarity condition in u)."""
+    torch, dis, ag, dev = env
+    W, H = 192, 128
+    kw = dict(PARAMS, dof=1)
+    I0, I1, _ = synth.layered_pair(3101, width=W, height=H, n_ellipses=6, max_disp=6.0, horizontal=True)
+    dd = ag.DifferentiableDIS(W, H, search_grad=search_grad, **kw)
+    try:
+        hs, ws = dd.coarsest_shape(W, H)
+        from scipy import ndimage
+        g = np.random.default_rng(10)
+        init = np.stack([ndimage.gaussian_filter(g.normal(0, 0.5, (hs, ws)), 2.0), np.zeros((hs, ws))], -1)
+        init = init.astype(np.float32)
+        a = torch.tensor(I0, device=dev, requires_grad=True)
+        b = torch.tensor(I1, device=dev, requires_grad=True)
+        it = torch.tensor(init, device=dev, requires_grad=True)
+        n = dis.dis_levels(W, H, dd.params)[2]
+        rec0 = torch.empty((n, 2), device=dev)
+        tmp = torch.empty((H, W, 2), device=dev)
+        dis.dis_compute_flow_ex(dd.handle, a.detach(), b.detach(), W, H, W, dd.params, it.detach(), None, rec0, None,
+                                tmp)
+        torch.cuda.synchronize()
+        rec = rec0.cpu().numpy().astype(np.float64)
+        if search_grad:
+            q = oracle.params(polish=POLISH, **kw)
+            _, rec = oracle.dis_flow(I0.astype(np.float64), I1.astype(np.float64), q,
+                                     init_flow=init.astype(np.float64), frozen=rec, record=True)
+        rec = rec.astype(np.float32)
+        assert (rec[:, 1] == 0.0).all()
+        flow = dd(a, b, it, frozen=torch.from_numpy(rec).to(dev))
+        loss = ag.photometric_loss(a, b, flow)
+        loss.backward()
+        grads = {"I0": a.grad.cpu().numpy().astype(np.float64), "I1": b.grad.cpu().numpy().astype(np.float64),
+                 "init": it.grad.cpu().numpy().astype(np.float64)}
+    finally:
+        dd.close()
+    rng = np.random.default_rng(4400 + search_grad)
+    coords = ([("I0", int(i)) for i in rng.integers(0, I0.size, 50)] +
+              [("I1", int(i)) for i in rng.integers(0, I1.size, 50)] +
+              [("init", int(i)) for i in rng.integers(0, init.size, 20)])
+    steps = (H_STEP, -H_STEP, 0.5 * H_STEP, -0.5 * H_STEP)
+    tasks = [(k, i, st) for k, i in coords for st in steps] + [("I0", 0, 0.0)]
+    ctx = mp.get_context("spawn")
+    kw_fd = dict(kw, polish=POLISH if search_grad else 0)
+    with ctx.Pool(min(16, os.cpu_count() or 1), initializer=_init_worker_kw,
+                  initargs=(I0.astype(np.float64), I1.astype(np.float64), rec.astype(np.float64),
+                            init.astype(np.float64), kw_fd)) as pool:
+        res = pool.map(_fd_task, tasks, chunksize=4)
+    h0 = res[-1][1]
+    flips, unconverged, errs = 0, 0, []
+    for c, (k, i) in enumerate(coords):
+        (lp, hp), (lm, hm), (lp2, hp2), (lm2, hm2) = res[4 * c:4 * c + 4]
+        if hp2 != h0 or hm2 != h0:
+            flips += 1
+            continue
+        fd = (lp - lm) / (2 * H_STEP)
+        fd2 = (lp2 - lm2) / H_STEP
+        an = grads[k].reshape(-1)[i]
+        if abs(fd - fd2) > 0.3 * REL_TOL * max(abs(fd), 1e-12):
+            unconverged += 1
+            continue
+        errs.append((abs(an - fd) / max(abs(fd), 1e-12), k, i, an, fd))
+    errs.sort(reverse=True)
+    print("stereo gradient (search_grad %d) vs FD: %d compared, %d flips, %d unconverged; worst: %s"
+          % (search_grad, len(errs), flips, unconverged, errs[:4]))
+    assert len(errs) >= 40
     mags = np.array([abs(e[4]) for e in errs])
     floor = 1e-3 * np.median(mags)
     bad = [e for e in errs if abs(e[3] - e[4]) > REL_TOL * max(abs(e[4]), floor)]

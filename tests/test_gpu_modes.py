@@ -206,27 +206,29 @@ def test_e2e_stereo(env, preset):
                       oracle_e2e(I0, I1, oracle_params(p)), gt)
 
 
-def test_differentiable_form_refuses_stereo(env):
+def test_differentiable_form_replays_stereo(env):
+    """The differentiable form takes the stereo mode: its FP64 replay of the recorded increments
+    reproduces the FP32 stereo flow to the end-to-end bar and keeps v at 0."""
     torch, dis, dev = env
-    p = dis.dis_default_params("stereo_dense")  # grayscale, finest scale 0: only dof is refused
+    p = dis.dis_default_params("stereo_dense")
     I0, I1, _ = synth.workload_pair("stereo320x240", 0)
     n = dis.dis_levels(320, 240, p)[2]
     ws_bytes = dis.dis_backward_workspace_bytes(320, 240, p)
-    assert ws_bytes > 0
     h = dis.dis_create(320, 240, 1, 1)
     try:
         a, b = to_dev(torch, I0, dev), to_dev(torch, I1, dev)
         ws = torch.zeros(ws_bytes // 4 + 1, device=dev)
-        fz = torch.zeros((n, 2), device=dev)
+        rec = torch.zeros((n, 2), device=dev)
+        f32 = torch.zeros((240, 320, 2), device=dev)
+        dis.dis_compute_flow_ex(h, a, b, 320, 240, 320, p, None, None, rec, None, f32)
         flow = torch.zeros((240, 320, 2), device=dev)
-        with pytest.raises(dis.DisError) as ei:
-            dis.dis_replay_flow(h, a, b, 320, 240, 320, p, None, fz, flow, ws, ws.numel() * 4)
-        assert ei.value.status == dis.DIS_ERR_NOT_SUPPORTED
-        p.dof = 2  # the same call as optical flow runs
-        dis.dis_replay_flow(h, a, b, 320, 240, 320, p, None, fz, flow, ws, ws.numel() * 4)
+        dis.dis_replay_flow(h, a, b, 320, 240, 320, p, None, rec, flow, ws, ws.numel() * 4)
         torch.cuda.synchronize()
     finally:
         dis.dis_destroy(h)
+    d = (flow - f32).abs()
+    assert float(d.mean()) <= 0.01 and float(torch.quantile(d.flatten(), 0.999)) <= 0.05
+    assert float(flow[..., 1].abs().max()) == 0.0
 
 
 @pytest.mark.parametrize("norm,hb", [("l1", 5.0), ("huber", 5.0), ("huber", 20.0)])

@@ -841,6 +841,12 @@ def test_polished_search_finds_the_exact_translation_of_a_bilinear_scene():
     u, _, st = oracle.search_level(I0, gx, gy, I1, ps, st_, 0, frozen=frozen, polish=50)
     inner = [_patch_index(w, ps, st_, px, py) for px in (8, 16, 24, 32) for py in (8, 16, 24, 32)]
     assert np.abs(u.reshape(-1, 2)[inner] - t).max() < 1e-12
+    # one degree of freedom: the scalar root in u with v held; a horizontal translation of the
+    # same scene is found exactly and v keeps its start
+    I1h = _bilinear_scene(h, w, c, (t[0], 0.0))[1]
+    fz1 = np.stack([t[0] + g.uniform(-0.3, 0.3, n), np.zeros(n)], -1)
+    u1, _, _ = oracle.search_level(I0, gx, gy, I1h, ps, st_, 0, frozen=fz1, polish=50, dof=1)
+    assert np.abs(u1.reshape(-1, 2)[inner, 0] - t[0]).max() < 1e-12 and (u1[..., 1] == 0.0).all()
     # a zero increment stands for a patch that did not move: it stays at u_init
     z = frozen.copy()
     z[inner[0]] = 0.0
