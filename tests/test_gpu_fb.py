@@ -225,3 +225,38 @@ def test_fb_refusals(env):
             dis.dis_compute_flow(h, a, b, W, H, W, p, flow)
     finally:
         dis.dis_destroy(h)
+
+
+def test_e2e_fb_combined_with_stereo_huber_and_early_termination(env):
+    """The extensions together: forward-backward consistency on a rectified pair with the stereo
+    preset, the Huber search norm and early termination (the flow's v stays 0 both ways)."""
+    torch, dis, dev = env
+    I0, I1, gt = synth.workload_pair("stereo320x240", 2)
+    p = dis.dis_default_params("stereo_dense", norm="huber", term_eps=0.01)
+    p.fb = 1
+    H, W = I0.shape
+    a, b = to_dev(torch, I0, dev), to_dev(torch, I1, dev)
+    f = torch.full((H, W, 2), float("nan"), device=dev)
+    fb_ = torch.full((H, W, 2), float("nan"), device=dev)
+    h = dis.dis_create(W, H, 2, 1)
+    try:
+        dis.dis_compute_flow_fb(h, a, b, W, H, W, p, f, fb_)
+        torch.cuda.synchronize()
+    finally:
+        dis.dis_destroy(h)
+    got_f, got_b = host(f), host(fb_)
+    assert (got_f[..., 1] == 0.0).all() and (got_b[..., 1] == 0.0).all()
+    q = oracle_params(p)
+    q.fb = 1
+
+    def ref_spread(A, B):
+        ref, spread = oracle_e2e(A, B, q)
+        eps = q.term_eps
+        for fct in (1.0 - 2e-3, 1.0 + 2e-3):  # the termination threshold's decisions too
+            q.term_eps = eps * fct
+            spread = np.maximum(spread, np.abs(oracle.dis_flow(A, B, q) - ref).max(-1))
+        q.term_eps = eps
+        return ref, spread
+
+    check_e2e("stereo320x240 fb+huber+term forward", got_f, ref_spread(I0, I1), gt, max_unstable=0.05)
+    check_e2e("stereo320x240 fb+huber+term backward", got_b, ref_spread(I1, I0), max_unstable=0.05)
