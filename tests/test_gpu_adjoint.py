@@ -189,7 +189,7 @@ def test_batch_of_eight_pairs(env):
             loss.backward()
             assert torch.isfinite(a.grad).all() and torch.isfinite(b.grad).all()
             assert float(a.grad.abs().sum()) > 0 and float(b.grad.abs().sum()) > 0
-            total += float(loss)
+            total += float(loss.detach())
         assert np.isfinite(total)
     finally:
         dd.close()
