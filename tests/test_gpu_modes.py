@@ -256,3 +256,40 @@ def test_e2e_stereo_robust_dense(env):
     got, _ = run_gpu(torch, dis, dev, I0, I1, p)
     assert (got[..., 1] == 0.0).all()
     check_e2e("stereo-rgb320x240-dense-huber", got, oracle_e2e(I0, I1, oracle_params(p)), gt)
+
+
+@pytest.mark.parametrize("W,H,kw", [
+    (12, 12, dict(patch_size=12, coarsest_scale=0, dof=1)),
+    (13, 9, dict(patch_size=8, stride_override=3, norm="l1")),
+    (37, 29, dict(patch_size=5, overlap=0.6, grad_iters=0, norm="huber", huber_b=2.0, dof=1)),
+    (67, 45, dict(patch_size=16, overlap=0.5, finest_scale=1, fb=1)),
+    (100, 64, dict(patch_size=7, overlap=0.9, grad_iters=24, refine=0, fb=1, dof=1, term_eps=0.02)),
+])
+def test_e2e_edge_sizes_of_the_extensions(env, W, H, kw):
+    """The extensions on degenerate and ragged sizes: a frame of one patch, a 13x9 frame, no
+    iterations, a 16x16 patch with the final up-scaling and consistency, stride 1 without
+    refinement with every extension at once."""
+    torch, dis, dev = env
+    I0, I1, gt = synth.layered_pair(18, width=W, height=H, n_ellipses=2, max_disp=2.0,
+                                    horizontal=kw.get("dof", 2) == 1)
+    p = dis.dis_default_params(**kw)
+    a, b = to_dev(torch, I0, dev, W + 1), to_dev(torch, I1, dev, W + 1)
+    f = torch.full((H, W, 2), float("nan"), device=dev)
+    h = dis.dis_create(W, H, 2, 1)
+    try:
+        dis.dis_compute_flow(h, a, b, W, H, W + 1, p, f)
+        torch.cuda.synchronize()
+    finally:
+        dis.dis_destroy(h)
+    got = host(f)
+    if p.dof == 1:
+        assert (got[..., 1] == 0.0).all()
+    q = oracle_params(p)
+    ref, spread = oracle_e2e(I0, I1, q)
+    if q.term_eps > 0:
+        eps = q.term_eps
+        for fct in (1.0 - 2e-3, 1.0 + 2e-3):
+            q.term_eps = eps * fct
+            spread = np.maximum(spread, np.abs(oracle.dis_flow(I0, I1, q) - ref).max(-1))
+        q.term_eps = eps
+    check_e2e("extensions edge %dx%d %s" % (W, H, kw), got, (ref, spread), max_unstable=0.05)
