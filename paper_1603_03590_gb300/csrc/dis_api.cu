@@ -715,7 +715,7 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
     off = align_up(off + sizeof(float) * h->rs_floats, kAlign);
     h->slot_bytes = off;
     h->jobs_bytes = align_up((size_t)max_batch * (4 + 2 * L) * 256 + 4096, kAlign);
-    h->arena_bytes = h->slot_bytes * max_batch + h->jobs_bytes;
+    h->arena_bytes = h->slot_bytes * max_batch + h->jobs_bytes + kAlign;  // + the search work queue
     cudaError_t e = cudaMalloc(&h->arena, h->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -723,6 +723,12 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
         return fail(nullptr, DIS_ERR_OUT_OF_MEMORY, std::string("arena allocation failed: ") + cudaGetErrorString(e));
     }
     h->jobs_dev = h->arena + h->slot_bytes * max_batch;
+    unsigned int* wq = (unsigned int*)(h->jobs_dev + h->jobs_bytes);
+    if ((e = cudaMemset(wq, 0, 2 * sizeof(unsigned int))) != cudaSuccess) {
+        cudaGetLastError();
+        dis_destroy(h);
+        return fail(nullptr, DIS_ERR_CUDA, std::string("handle setup failed: ") + cudaGetErrorString(e));
+    }
     if ((e = cudaMallocHost(&h->jobs_pinned, h->jobs_bytes)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->jobs_ev, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -731,6 +737,7 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
     }
     cudaEventRecord(h->jobs_ev, h->cap_stream);
     h->lc = dis::query_launch_cfg();
+    h->lc.wq = wq;
     const char* ng = std::getenv("DIS_NO_GRAPH");
     h->use_graphs = !(ng && ng[0] == '1');
     *out = h;

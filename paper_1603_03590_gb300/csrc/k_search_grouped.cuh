@@ -104,7 +104,7 @@ __device__ __forceinline__ void group_sum12(float (&Q)[12], unsigned gmask, int 
 template <int LPP, int PPL, int PSC, int MINB, bool GSM, int DOF = 2, bool ROBUST = false, bool TERM = false>
 __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
                                                      int ps_rt, int stride, int iters, int norm, float huber_b,
-                                                     float term2)
+                                                     float term2, unsigned int* __restrict__ wq)
 {
     static_assert(DOF == 1 || DOF == 2, "one or two degrees of freedom");
     extern __shared__ float smem[];
@@ -118,8 +118,17 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
     float* gxs = win + ws * ws;                                             // then (GSM) the template
     float* gys = gxs + n;                                                   // gradients
     const float inv_n = 1.0f / (float)n;
-    const long long step = (long long)gridDim.x * wpb * GPW;
-    for (long long g = ((long long)blockIdx.x * wpb + wib) * GPW + grp; g < total; g += step) {
+    // Patch assignment.  Every group starts on patch (its index in the grid); with a work queue
+    // it then takes the next unclaimed patch (patch costs vary several-fold with the texture and
+    // the iterations to convergence, so a fixed stride leaves SMs idle at the end of the launch),
+    // else it strides by the number of groups.  A patch's result does not depend on the group
+    // that computes it.
+    const long long ngroups = (long long)gridDim.x * wpb * GPW;
+    long long g = ((long long)blockIdx.x * wpb + wib) * GPW + grp;
+    while (g < total) {
+        // claimed now, read after this patch: the atomic's latency hides behind the patch
+        unsigned int qn = 0;
+        if (wq && gl == 0) qn = atomicAdd(wq, 1u);
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::patch_base));
         const long long pk = g - J.patch_base;
         const int w = J.w, h = J.h, pitch = J.pitch;
@@ -422,6 +431,17 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
             if (J.pst) J.pst[pk] = st;
             if (J.record) J.record[pk] = make_float2(u - ui.x, v - ui.y);
         }
+        g = wq ? ngroups + (long long)__shfl_sync(gmask, qn, grp * LPP) : g + ngroups;
+    }
+    if (wq && gl == 0) {
+        // this group claims nothing more; the last group to get here zeroes the queue for the
+        // next launch (every other group's last claim is ordered before its count by the fence)
+        __threadfence();
+        if (atomicAdd(wq + 1, 1u) == (unsigned int)ngroups - 1u) {
+            __threadfence();
+            atomicExch(wq, 0u);
+            atomicExch(wq + 1, 0u);
+        }
     }
 }
 
@@ -444,8 +464,10 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
     long long blocks = (total + per_block - 1) / per_block;
     const long long cap = (long long)lc.sm_count * occ;
     if (blocks > cap) blocks = cap;
+    // the queue's 32-bit counters hold the patch count plus one claim per group
+    unsigned int* wq = total + blocks * per_block < (1LL << 31) ? lc.wq : nullptr;
     search_kernel<LPP, PPL, PSC, MINB, GSM, DOF, ROBUST, TERM>
-        <<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters, norm, huber_b, term2);
+        <<<(int)blocks, threads, smem, s>>>(js, total, ps, stride, iters, norm, huber_b, term2, wq);
     return cudaGetLastError();
 }
 
