@@ -237,6 +237,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     plan.key.push_back(hd->search_lanes[p.patch_size]);
     plan.key.push_back(hd->refine_fused);
     plan.key.push_back(hd->probe_kind);
+    plan.key.push_back(hd->lc.wq != nullptr);
     plan.key.push_back(hd->probe_level);
 
     auto slot = [&](int i) { return hd->arena + (size_t)i * hd->slot_bytes; };
@@ -737,7 +738,7 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
     }
     cudaEventRecord(h->jobs_ev, h->cap_stream);
     h->lc = dis::query_launch_cfg();
-    h->lc.wq = wq;
+    h->lc.wq = h->wq = wq;
     const char* ng = std::getenv("DIS_NO_GRAPH");
     h->use_graphs = !(ng && ng[0] == '1');
     *out = h;
@@ -971,6 +972,14 @@ dis_status dis_set_refine_fusion(dis_handle* hd, int fused)
     if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
     if (fused < 0 || fused > 3) return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_refine_fusion: mode must be 0 to 3");
     hd->refine_fused = fused;
+    return DIS_OK;
+}
+
+dis_status dis_set_work_queue(dis_handle* hd, int on)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    if (on != 0 && on != 1) return fail(hd, DIS_ERR_INVALID_ARG, "dis_set_work_queue: on must be 0 or 1");
+    hd->lc.wq = on ? hd->wq : nullptr;
     return DIS_OK;
 }
 

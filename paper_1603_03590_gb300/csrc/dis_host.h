@@ -12,7 +12,7 @@
 #include "dis_internal.cuh"
 
 // The handle: one device arena (max_batch slots of per-level planes, a refinement scratch,
-// a job-table region), the job upload state and the CUDA-graph cache.
+// a job-table region, the search work queue), the job upload state and the CUDA-graph cache.
 struct dis_handle {
     int max_w = 0, max_h = 0, max_batch = 0, C = 1, levels = 0, device = 0;
     char* arena = nullptr;
@@ -36,6 +36,7 @@ struct dis_handle {
     bool use_graphs = true;
     int search_lanes[17] = {};  // autotuned lanes per patch by patch size (0 = default)
     int refine_fused = 1;       // refinement launch form (dis_set_refine_fusion)
+    unsigned int* wq = nullptr;  // the search work queue in the arena (lc.wq while enabled)
     // probe: events recorded around one launch group in every call (also inside graphs)
     int probe_kind = -1, probe_level = 0;
     cudaEvent_t probe_a = nullptr, probe_b = nullptr;

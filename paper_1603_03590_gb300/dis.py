@@ -87,6 +87,7 @@ _SIGS = {
     "dis_get_tuning": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "dis_set_probe": (_i, [_vp, _i, _i]),
     "dis_set_refine_fusion": (_i, [_vp, _i]),
+    "dis_set_work_queue": (_i, [_vp, _i]),
     "dis_probe_ms": (_i, [_vp, ctypes.POINTER(_f)]),
     "dis_trace_batched": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, _vp, _i, ctypes.POINTER(_i)]),
     "dis_set_search_variant": (_i, [_vp, _i, _i]),
@@ -242,6 +243,12 @@ def dis_set_refine_fusion(handle, mode):
     """Refinement launch form: 0 per-half-sweep launches, 1 fused as measured fastest (default),
     2 one fused launch per pass, 3 two per pass (True / False map to 1 / 0)."""
     _check(_lib.dis_set_refine_fusion(handle, int(mode)), handle)
+
+
+def dis_set_work_queue(handle, on):
+    """Inverse-search patch scheduling: True hands patches out from the handle's work queue
+    (default), False uses a fixed grid stride; both give the same flow bit for bit."""
+    _check(_lib.dis_set_work_queue(handle, int(bool(on))), handle)
 
 
 def dis_set_probe(handle, kind, level=0):

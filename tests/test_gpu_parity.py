@@ -415,6 +415,47 @@ def test_e2e_fused_refinement_equals_per_sweep_bit_exact(env, preset, C):
         assert all(np.array_equal(out[0][k], o[k]) for o in out[1:]), (preset, sizes[k])
 
 
+def test_search_work_queue_equals_grid_stride_bit_exact(env):
+    """Patch scheduling: the work queue (default) and the fixed grid stride give the same flows
+    bit for bit, over a batch of uneven sizes, in repeated calls (graph replays) and after calls
+    with a different number of patches (another grid size): the queue starts every launch from
+    zero."""
+    torch, dis, dev = env
+    sizes = [(173, 91), (320, 240), (64, 48)]
+    pairs = [synth.layered_pair(90 + k, width=w, height=h, n_ellipses=4, max_disp=0.04 * w) for k, (w, h) in enumerate(sizes)]
+    p = dis.dis_default_params("dense", grad_iters=32)
+    h = dis.dis_create(320, 240, len(pairs), 1)
+    try:
+        dev_pairs = [(to_dev(torch, a, dev), to_dev(torch, b, dev)) for a, b, _ in pairs]
+
+        def run(subset):
+            flows = [torch.full((pairs[k][0].shape[-2], pairs[k][0].shape[-1], 2), float("nan"), device=dev) for k in subset]
+            items = [(dev_pairs[k][0], dev_pairs[k][1], pairs[k][0].shape[-1], pairs[k][0].shape[-2],
+                      pairs[k][0].shape[-1], f) for k, f in zip(subset, flows)]
+            dis.dis_compute_flow_batched(h, dis.make_pairs(items), len(items), p)
+            torch.cuda.synchronize()
+            return [host(f) for f in flows]
+
+        every = list(range(len(pairs)))
+        ref = run(every)                     # queue, first call (graph captured)
+        again = run(every)                   # queue, graph replay
+        small = run([2])                     # another grid in between
+        after = run(every)
+        dis.dis_set_work_queue(h, False)
+        stride = run(every)                  # fixed grid stride
+        small_stride = run([2])
+        dis.dis_set_work_queue(h, True)
+        back = run(every)
+        assert dis._lib.dis_set_work_queue(h, 2) == dis.DIS_ERR_INVALID_ARG
+    finally:
+        dis.dis_destroy(h)
+    for k in range(len(pairs)):
+        assert np.isfinite(ref[k]).all()
+        for o in (again, after, stride, back):
+            assert np.array_equal(ref[k], o[k]), sizes[k]
+    assert np.array_equal(small[0], ref[2]) and np.array_equal(small_stride[0], ref[2])
+
+
 def test_e2e_rgb(env):
     torch, dis, dev = env
     I0, I1, gt = synth.layered_pair(4000, width=256, height=144, max_disp=10.0, channels=3, rotation_deg=2.0)
