@@ -513,7 +513,7 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                     e = traced(DIS_LAUNCH_DENSIFY, ph.s, [&] {
                         if (p.fb)
                             return dis::launch_densify_fb(js, ph.total, ph.total4, ph.n, ps, stride, hd->lc, s);
-                        return dis::launch_densify(js, ph.total2, ps, stride, hd->lc, s);
+                        return dis::launch_densify(js, ph.total2, ph.total4, ps, stride, hd->lc, s);
                     });
                 for (const auto& c : plan.copies)
                     if (e == cudaSuccess && c.s == ph.s) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s);
@@ -1195,7 +1195,10 @@ dis_status dis_densify_level(const float* I0, const float* I1, int w, int h, int
     J.nx = grid_n(w, ps, stride);
     J.ny = grid_n(h, ps, stride);
     J.C = 1;
-    cudaError_t e = dis::launch_densify(dis::single_job(J), (long long)w * h, ps, stride, stage_lc(), (cudaStream_t)stream);
+    long long tiles = 0;
+    dis::set_refine_tiles(J, tiles);
+    cudaError_t e = dis::launch_densify(dis::single_job(J), (long long)w * h, tiles, ps, stride, stage_lc(),
+                                        (cudaStream_t)stream);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_densify_level");
 }
 

@@ -166,8 +166,10 @@ cudaError_t launch_densify_fb(const Jobs<LevelJob>& js, long long total_patches,
                               int ps, int stride, const LaunchCfg& lc, cudaStream_t s);
 // Ints of refinement scratch the lists of one job take (at most), for a w x h level.
 long long fb_scratch_ints(int w, int h, int ps, int stride);
-cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, int stride, const LaunchCfg& lc,
-                           cudaStream_t s);
+// Plain densification of `total` pixels; `tiles` > 0: the jobs carry their refinement tiles
+// (tile_base, tiles_x), `tiles` in all, and the tiled form runs where the stride allows it.
+cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, long long tiles, int ps, int stride,
+                           const LaunchCfg& lc, cudaStream_t s);
 struct RefineArgs {
     int outer, inner;
     float delta, gamma, alpha, omega;

@@ -82,6 +82,99 @@ __global__ void __launch_bounds__(256) densify_kernel(const __grid_constant__ Jo
     }
 }
 
+// Tiled form for the strides of the presets: a block per 32 x 32 tile (the refinement tiles of
+// the job).  Every pixel of a patch samples I1 with the patch's displacement, so the parts of
+// the bilinear sample that depend on the patch alone (the clamped displacement's floor and
+// fraction) and the patch flow are staged once per tile for all patches that cover it, instead
+// of once per (pixel, patch).  Each pixel then runs the loop of own_sums over the staged patches
+// in the same row-major order with the same operations: the result equals densify_kernel's bit
+// for bit.  Covering patches per tile and axis: at most (30 + ps) / stride + 1 regular ones and
+// the last one, so at most 17 for ps <= 16 and stride >= 3.
+constexpr int kDensTile = kRefineTile;
+constexpr int kDensAxis = 18;
+constexpr int kDensThreads = 256;
+
+struct DensPatch {
+    float ax, ay, u, v;  // fraction of the clamped displacement, patch flow
+};
+
+template <int SC>
+__global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid_constant__ Jobs<LevelJob> js,
+                                                                    long long tiles, int ps)
+{
+    constexpr int stride = SC;
+    static_assert(SC >= 3, "the staged table holds kDensAxis patches per axis");
+    __shared__ DensPatch tab[kDensAxis * kDensAxis];
+    __shared__ int2 cell[kDensAxis * kDensAxis];  // integer part of the clamped displacement
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const LevelJob& J = job_ref(js, find_job(js, t, &LevelJob::tile_base));
+        const int tk = (int)(t - J.tile_base);
+        const int w = J.w, h = J.h, pitch = J.pitch, nx = J.nx, ny = J.ny;
+        const int tx0 = (tk % J.tiles_x) * kDensTile, ty0 = (tk / J.tiles_x) * kDensTile;
+        const int tx1 = min(tx0 + kDensTile, w) - 1, ty1 = min(ty0 + kDensTile, h) - 1;
+        // regular patches covering the tile's columns / rows, then the last one
+        int ib, ie, jb, je, d0, d1;
+        bool lx, ly, l0;
+        cover_range<SC>(tx0, w, ps, stride, nx, ib, d0, l0);
+        cover_range<SC>(tx1, w, ps, stride, nx, d1, ie, lx);
+        cover_range<SC>(ty0, h, ps, stride, ny, jb, d0, l0);
+        cover_range<SC>(ty1, h, ps, stride, ny, d1, je, ly);
+        const int nreg_x = max(0, ie - ib + 1), nreg_y = max(0, je - jb + 1);
+        const int tw = nreg_x + (lx ? 1 : 0), th = nreg_y + (ly ? 1 : 0);
+        for (int q = threadIdx.x; q < tw * th; q += kDensThreads) {
+            const int a = q % tw, b = q / tw;
+            const int i = a < nreg_x ? ib + a : nx - 1, j = b < nreg_y ? jb + b : ny - 1;
+            const float2 up = J.pu[(long long)j * nx + i];
+            // the patch-only part of sample_shift
+            const float uc = fminf(fmaxf(up.x, -1.0e7f), 1.0e7f);
+            const float vc = fminf(fmaxf(up.y, -1.0e7f), 1.0e7f);
+            const float fu = floorf(uc), fv = floorf(vc);
+            tab[q] = DensPatch{uc - fu, vc - fv, up.x, up.y};
+            cell[q] = make_int2((int)fu, (int)fv);
+        }
+        __syncthreads();
+        const int x = tx0 + (int)(threadIdx.x % kDensTile);
+        for (int y = ty0 + (int)(threadIdx.x / kDensTile); y <= ty1; y += kDensThreads / kDensTile) {
+            if (x > tx1) break;
+            int ilo, ihi, jlo, jhi;
+            bool ilast, jlast;
+            cover_range<SC>(x, w, ps, stride, nx, ilo, ihi, ilast);
+            cover_range<SC>(y, h, ps, stride, ny, jlo, jhi, jlast);
+            const float i0 = __ldg(J.S0 + (long long)y * pitch + x);
+            float nu = 0.0f, nv = 0.0f, Z = 0.0f;
+            const int jend = jhi + (jlast ? 1 : 0), iend = ihi + (ilast ? 1 : 0);
+            for (int jj = jlo; jj <= jend; ++jj) {
+                const int row = (jj > jhi ? nreg_y : jj - jb) * tw;
+                for (int ii = ilo; ii <= iend; ++ii) {
+                    const int q = row + (ii > ihi ? nreg_x : ii - ib);
+                    const DensPatch P = tab[q];
+                    const int2 c = cell[q];
+                    const int xi = x + c.x, yi = y + c.y;
+                    const int x0 = clampi(xi, 0, w - 1), x1 = clampi(xi + 1, 0, w - 1);
+                    const int y0 = clampi(yi, 0, h - 1), y1 = clampi(yi + 1, 0, h - 1);
+                    const float* r0 = J.S1 + (long long)y0 * pitch;
+                    const float* r1 = J.S1 + (long long)y1 * pitch;
+                    const float pa = __ldg(r0 + x0), pb = __ldg(r0 + x1), pc = __ldg(r1 + x0), pd = __ldg(r1 + x1);
+                    const float top = fmaf(P.ax, pb - pa, pa), bot = fmaf(P.ax, pd - pc, pc);
+                    const float d = fmaf(P.ay, bot - top, top) - i0;
+                    const float wt = __frcp_rn(fmaxf(1.0f, fabsf(d)));  // as in own_sums
+                    nu = fmaf(wt, P.u, nu);
+                    nv = fmaf(wt, P.v, nv);
+                    Z += wt;
+                }
+            }
+            float2 r;
+            if (Z > 0.0f) {
+                r = make_float2(nu / Z, nv / Z);
+            } else {
+                r = init_flow_at(J.Uc, J.wc, J.hc, J.cscale, (float)x, (float)y);
+            }
+            J.U[(long long)y * w + x] = r;
+        }
+        __syncthreads();  // the table is rewritten for the next tile
+    }
+}
+
 // ---- forward-backward consistency ------------------------------------------------------
 
 constexpr int kFbTile = kRefineTile;  // the lists use the refinement tiles of each job
@@ -360,10 +453,22 @@ cudaError_t launch_densify_fb(const Jobs<LevelJob>& js, long long total_patches,
     return cudaGetLastError();
 }
 
-cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, int ps, int stride, const LaunchCfg& lc,
-                           cudaStream_t s)
+cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, long long tiles, int ps, int stride,
+                           const LaunchCfg& lc, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
+    if (tiles > 0 && stride >= 3 && stride <= 6 && (30 + ps) / stride + 2 <= kDensAxis) {
+        long long b = tiles;
+        const long long cap = (long long)lc.sm_count * 4;
+        if (b > cap) b = cap;
+        switch (stride) {
+            case 3: densify_tile_kernel<3><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
+            case 4: densify_tile_kernel<4><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
+            case 5: densify_tile_kernel<5><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
+            default: densify_tile_kernel<6><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
+        }
+        return cudaGetLastError();
+    }
     long long b = (total + 255) / 256;
     const long long cap = (long long)lc.sm_count * lc.max_blocks_256;
     if (b > cap) b = cap;
