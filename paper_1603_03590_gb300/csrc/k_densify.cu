@@ -82,17 +82,20 @@ __global__ void __launch_bounds__(256) densify_kernel(const __grid_constant__ Jo
     }
 }
 
-// Tiled form for the strides of the presets: a block per 32 x 32 tile (the refinement tiles of
-// the job).  Every pixel of a patch samples I1 with the patch's displacement, so the parts of
-// the bilinear sample that depend on the patch alone (the clamped displacement's floor and
-// fraction) and the patch flow are staged once per tile for all patches that cover it, instead
-// of once per (pixel, patch).  Each pixel then runs the loop of own_sums over the staged patches
-// in the same row-major order with the same operations: the result equals densify_kernel's bit
-// for bit.  Covering patches per tile and axis: at most (30 + ps) / stride + 1 regular ones and
-// the last one, so at most 17 for ps <= 16 and stride >= 3.
+// Tiled form for the strides of the presets: a block per band of 32 x 8 pixels (a quarter of one
+// of the job's 32 x 32 refinement tiles), a thread per pixel.  Every pixel of a patch samples I1
+// with the patch's displacement, so the parts of the bilinear sample that depend on the patch
+// alone (the clamped displacement's floor and fraction) and the patch flow are staged once per
+// band for all patches that cover it, instead of once per (pixel, patch).  Each pixel then runs
+// the loop of own_sums over the staged patches in the same row-major order with the same
+// operations: the result equals densify_kernel's bit for bit.  Covering patches per band and
+// axis: at most (30 + ps) / stride + 1 regular ones and the last one, so at most 17 for
+// ps <= 16 and stride >= 3.
 constexpr int kDensTile = kRefineTile;
+constexpr int kDensRows = 8;  // rows of a band
+constexpr int kDensBands = kDensTile / kDensRows;
 constexpr int kDensAxis = 18;
-constexpr int kDensThreads = 256;
+constexpr int kDensThreads = kDensTile * kDensRows;
 
 struct DensPatch {
     float ax, ay, u, v;  // fraction of the clamped displacement, patch flow
@@ -100,18 +103,21 @@ struct DensPatch {
 
 template <int SC>
 __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid_constant__ Jobs<LevelJob> js,
-                                                                    long long tiles, int ps)
+                                                                    long long bands, int ps)
 {
     constexpr int stride = SC;
     static_assert(SC >= 3, "the staged table holds kDensAxis patches per axis");
     __shared__ DensPatch tab[kDensAxis * kDensAxis];
     __shared__ int2 cell[kDensAxis * kDensAxis];  // integer part of the clamped displacement
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (long long g = blockIdx.x; g < bands; g += gridDim.x) {
+        const long long t = g / kDensBands;
         const LevelJob& J = job_ref(js, find_job(js, t, &LevelJob::tile_base));
         const int tk = (int)(t - J.tile_base);
         const int w = J.w, h = J.h, pitch = J.pitch, nx = J.nx, ny = J.ny;
-        const int tx0 = (tk % J.tiles_x) * kDensTile, ty0 = (tk / J.tiles_x) * kDensTile;
-        const int tx1 = min(tx0 + kDensTile, w) - 1, ty1 = min(ty0 + kDensTile, h) - 1;
+        const int tx0 = (tk % J.tiles_x) * kDensTile;
+        const int ty0 = (tk / J.tiles_x) * kDensTile + (int)(g % kDensBands) * kDensRows;
+        if (ty0 >= h) continue;  // a band below the frame in the last row of tiles (uniform)
+        const int tx1 = min(tx0 + kDensTile, w) - 1, ty1 = min(ty0 + kDensRows, h) - 1;
         // regular patches covering the tile's columns / rows, then the last one
         int ib, ie, jb, je, d0, d1;
         bool lx, ly, l0;
@@ -133,9 +139,8 @@ __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid
             cell[q] = make_int2((int)fu, (int)fv);
         }
         __syncthreads();
-        const int x = tx0 + (int)(threadIdx.x % kDensTile);
-        for (int y = ty0 + (int)(threadIdx.x / kDensTile); y <= ty1; y += kDensThreads / kDensTile) {
-            if (x > tx1) break;
+        const int x = tx0 + (int)(threadIdx.x % kDensTile), y = ty0 + (int)(threadIdx.x / kDensTile);
+        if (x <= tx1 && y <= ty1) {
             int ilo, ihi, jlo, jhi;
             bool ilast, jlast;
             cover_range<SC>(x, w, ps, stride, nx, ilo, ihi, ilast);
@@ -458,14 +463,15 @@ cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, long long 
 {
     if (total <= 0) return cudaSuccess;
     if (tiles > 0 && stride >= 3 && stride <= 6 && (30 + ps) / stride + 2 <= kDensAxis) {
-        long long b = tiles;
+        const long long bands = tiles * kDensBands;
+        long long b = bands;
         const long long cap = (long long)lc.sm_count * 4;
         if (b > cap) b = cap;
         switch (stride) {
-            case 3: densify_tile_kernel<3><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
-            case 4: densify_tile_kernel<4><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
-            case 5: densify_tile_kernel<5><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
-            default: densify_tile_kernel<6><<<(int)b, kDensThreads, 0, s>>>(js, tiles, ps); break;
+            case 3: densify_tile_kernel<3><<<(int)b, kDensThreads, 0, s>>>(js, bands, ps); break;
+            case 4: densify_tile_kernel<4><<<(int)b, kDensThreads, 0, s>>>(js, bands, ps); break;
+            case 5: densify_tile_kernel<5><<<(int)b, kDensThreads, 0, s>>>(js, bands, ps); break;
+            default: densify_tile_kernel<6><<<(int)b, kDensThreads, 0, s>>>(js, bands, ps); break;
         }
         return cudaGetLastError();
     }
