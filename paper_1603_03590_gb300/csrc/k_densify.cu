@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid
         const int ty0 = (tk / J.tiles_x) * kDensTile + (int)(g % kDensBands) * kDensRows;
         if (ty0 >= h) continue;  // a band below the frame in the last row of tiles (uniform)
         const int tx1 = min(tx0 + kDensTile, w) - 1, ty1 = min(ty0 + kDensRows, h) - 1;
-        // regular patches covering the tile's columns / rows, then the last one
+        // regular patches covering the band's columns / rows, then the last one
         int ib, ie, jb, je, d0, d1;
         bool lx, ly, l0;
         cover_range<SC>(tx0, w, ps, stride, nx, ib, d0, l0);
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid
             }
             J.U[(long long)y * w + x] = r;
         }
-        __syncthreads();  // the table is rewritten for the next tile
+        __syncthreads();  // the table is rewritten for the next band
     }
 }
 
