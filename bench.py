@@ -227,7 +227,8 @@ def workload_config(args, batch, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    # 60 steps of 32 pairs take about 0.9 s: long enough for several clock samples at 200 ms
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="flow", choices=sorted(WORKLOADS))
