@@ -317,6 +317,39 @@ def test_densify_two_patch_hand_example():
     assert U[0, 2, 0] == 1.0 and U[0, 10, 0] == 0.0
 
 
+@pytest.mark.parametrize("W,H,ps,st_", [(29, 23, 8, 3), (37, 26, 12, 3), (31, 19, 8, 5), (20, 13, 12, 6)])
+def test_densify_ragged_grid_by_brute_force(W, H, ps, st_):
+    """Eq. 3 evaluated from its definition: every patch at its corner (min(i*stride, W - ps),
+    min(j*stride, H - ps)), i = 0 .. ceil((W - ps) / stride), contributes to the pixels it
+    contains with weight 1 / max(1, |I1(x + u_i) - I0(x)|), I1 sampled bilinearly at coordinates
+    clamped to the frame (scipy's order-1 interpolation with edge extension).  The ragged sizes
+    put the last patch of each row and column off the regular stride, and a few large patch
+    flows reach past the frame."""
+    g = np.random.default_rng(W * 100 + ps)
+    I0, I1 = g.uniform(0, 255, (H, W)), g.uniform(0, 255, (H, W))
+    xs = [min(i * st_, W - ps) for i in range(-(-(W - ps) // st_) + 1)]
+    ys = [min(j * st_, H - ps) for j in range(-(-(H - ps) // st_) + 1)]
+    u = g.normal(0.0, 1.5, (len(ys), len(xs), 2))
+    u[::3, ::2] *= 8.0
+    U = oracle.densify_level(I0, I1, u, ps, st_)
+    assert U.shape == (H, W, 2)
+    num = np.zeros((H, W, 2))
+    den = np.zeros((H, W))
+    yy, xx = np.mgrid[0:H, 0:W].astype(float)
+    for j, py in enumerate(ys):
+        for i, px in enumerate(xs):
+            cx = np.clip(xx + u[j, i, 0], 0, W - 1)
+            cy = np.clip(yy + u[j, i, 1], 0, H - 1)
+            w1 = ndimage.map_coordinates(I1, [cy, cx], order=1, mode="nearest")
+            wt = 1.0 / np.maximum(1.0, np.abs(w1 - I0))
+            inside = (xx >= px) & (xx < px + ps) & (yy >= py) & (yy < py + ps)
+            num += np.where(inside, wt, 0.0)[..., None] * u[j, i]
+            den += np.where(inside, wt, 0.0)
+    assert den.min() > 0  # the grid covers every pixel
+    ref = num / den[..., None]
+    assert np.abs(U - ref).max() < 1e-10
+
+
 # ---------------------------------------------------------------- refinement (Sec. 2.3)
 def test_refine_two_pixel_hand_sweep():
     # delta = gamma = 0: pure smoothing.  2x1 image, U = [(1,0), (0,0)], both pixels have
