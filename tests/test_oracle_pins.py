@@ -81,6 +81,25 @@ def test_sobel_exact_on_bilinear_function():
     assert np.abs(gy[1:-1, 1:-1] - (-0.7 + 0.05 * x[1:-1, 1:-1])).max() < 1e-12
 
 
+@pytest.mark.parametrize("h,w", [(17, 23), (8, 5), (1, 6)])
+def test_pyramid_and_sobel_equal_library_filters_on_noise(h, w):
+    """On white noise (no symmetry to hide a transposed or misplaced tap) the pyramid step is
+    scipy's separable [1 4 6 4 1]/16 correlation with edge replication sampled at even (x, y),
+    and the gradients are scipy's Sobel (difference along the axis, [1 2 1] across it, edge
+    replication) divided by 8.  A ramp or a bilinear function cannot tell the Sobel smoothing
+    axis apart; noise can."""
+    g = np.random.default_rng(h * 31 + w)
+    img = g.uniform(0, 255, (h, w))
+    k = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0
+    ref = ndimage.correlate1d(ndimage.correlate1d(img, k, axis=0, mode="nearest"), k, axis=1, mode="nearest")
+    out = oracle.pyr_down(img)
+    assert out.shape == ((h + 1) // 2, (w + 1) // 2)
+    assert np.abs(out - ref[::2, ::2]).max() < 1e-11
+    gx, gy = oracle.sobel(img)
+    assert np.abs(gx - ndimage.sobel(img, axis=1, mode="nearest") / 8.0).max() < 1e-11
+    assert np.abs(gy - ndimage.sobel(img, axis=0, mode="nearest") / 8.0).max() < 1e-11
+
+
 # ---------------------------------------------------------------- bilinear sampling
 def test_bilinear_exact_and_clamped():
     h, w = 9, 13
