@@ -520,6 +520,23 @@ def test_upsample_linear_field():
     assert np.array_equal(oracle.upsample_flow(U, 1.0, (hi, wi)), U)
 
 
+@pytest.mark.parametrize("factor,src,dst", [(2.0, (7, 9), (13, 18)), (4.0, (5, 6), (20, 23)), (8.0, (3, 4), (17, 29))])
+def test_upsample_random_field_equals_library_interpolation(factor, src, dst):
+    """U_out(x) = factor * U(x / factor), bilinear at coordinates clamped to the coarse field:
+    on a random field, against scipy's order-1 interpolation with edge extension (which equals
+    clamping the coordinate), per component; the output sizes leave the last coarse sample
+    behind the clamp."""
+    g = np.random.default_rng(int(factor) * 7 + src[0])
+    U = g.normal(0.0, 3.0, src + (2,))
+    out = oracle.upsample_flow(U, factor, dst)
+    yo, xo = np.mgrid[0:dst[0], 0:dst[1]].astype(float)
+    cy = np.clip(yo / factor, 0, src[0] - 1)
+    cx = np.clip(xo / factor, 0, src[1] - 1)
+    for c in range(2):
+        ref = factor * ndimage.map_coordinates(U[..., c], [cy, cx], order=1, mode="nearest")
+        assert np.abs(out[..., c] - ref).max() < 1e-11
+
+
 def test_pipeline_recovers_translation_of_saddle_image():
     # bilinear (saddle) scene: every pyramid level stays bilinear in its interior, interior
     # patches contract exactly onto t / 2^s, so interior pixels of the final flow equal t.
