@@ -40,7 +40,7 @@ typedef enum dis_status {
     DIS_ERR_CUDA = 3,          /* a CUDA call or kernel launch failed */
     DIS_ERR_TOO_SMALL = 4,     /* the image is smaller than one patch at the coarsest level */
     DIS_ERR_TIMEOUT = 5,       /* reserved: a bounded device-side wait gave up */
-    DIS_ERR_NOT_SUPPORTED = 6  /* valid request outside what this build implements */
+    DIS_ERR_NOT_SUPPORTED = 6  /* valid request outside what the library implements */
 } dis_status;
 
 /* Parameters of the method (Table 1, Sec. 3.1).  dis_default_params fills the paper's
