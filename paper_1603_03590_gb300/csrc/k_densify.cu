@@ -303,7 +303,8 @@ constexpr int kFbChunk = kFbThreads;  // listed patches staged in shared memory 
 // enter a bin (atomic) does not change them.
 template <int SC>
 __global__ void __launch_bounds__(kFbThreads, 6) densify_fb_kernel(const __grid_constant__ Jobs<LevelJob> js,
-                                                                   long long total, int ps, int stride)
+                                                                   long long total, int ps, int stride,
+                                                                   unsigned int* __restrict__ wq)
 {
     constexpr int NB = (kFbTile / kFbBin) * (kFbTile / kFbBin);
     constexpr int NP = kFbTile * kFbTile;
@@ -316,9 +317,16 @@ __global__ void __launch_bounds__(kFbThreads, 6) densify_fb_kernel(const __grid_
     __shared__ long long acc[3][NP];  // fixed-point sums per tile pixel: -w u'_x, -w u'_y, w
     __shared__ float s0[NP];          // the tile of I0
     __shared__ float red[kFbThreads / 32];
+    __shared__ long long next_tile;
     const int bin = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx0 = (bin % (kFbTile / kFbBin)) * kFbBin, by0 = (bin / (kFbTile / kFbBin)) * kFbBin;
-    for (long long g = blockIdx.x; g < total; g += gridDim.x) {
+    // Tiles differ in how many partner footprints their lists hold, so with a work queue (the
+    // search's counters, free while this kernel runs) each block claims its next tile when it
+    // starts the current one; else the grid stride.  A tile's result does not depend on the block.
+    long long g = blockIdx.x;
+    while (g < total) {
+        unsigned int qn = 0;
+        if (wq && threadIdx.x == 0) qn = atomicAdd(wq, 1u);
         const LevelJob& J = job_ref(js, find_job(js, g, &LevelJob::tile_base));
         const LevelJob& P = job_ref(js, J.partner);
         const long long t = g - J.tile_base;
@@ -422,7 +430,18 @@ __global__ void __launch_bounds__(kFbThreads, 6) densify_fb_kernel(const __grid_
             }
             J.U[(long long)y * J.w + x] = r;
         }
-        __syncthreads();  // the accumulators, red and bcnt are rewritten for the next tile
+        if (threadIdx.x == 0) next_tile = wq ? (long long)gridDim.x + qn : g + gridDim.x;
+        __syncthreads();  // the accumulators, red, bcnt and next_tile are rewritten for the next tile
+        g = next_tile;
+    }
+    if (wq && threadIdx.x == 0) {
+        // the last block to finish zeroes the queue for the next launch
+        __threadfence();
+        if (atomicAdd(wq + 1, 1u) == gridDim.x - 1u) {
+            __threadfence();
+            atomicExch(wq, 0u);
+            atomicExch(wq + 1, 0u);
+        }
     }
 }
 
@@ -447,13 +466,15 @@ cudaError_t launch_densify_fb(const Jobs<LevelJob>& js, long long total_patches,
     if (total_patches > 0) fb_list_kernel<false><<<grid(total_patches, lc.max_blocks_256), 256, 0, s>>>(js, total_patches, ps, stride);
     fb_scan_kernel<<<std::min(njobs, lc.sm_count * 2), 1024, 0, s>>>(js, njobs);
     if (total_patches > 0) fb_list_kernel<true><<<grid(total_patches, lc.max_blocks_256), 256, 0, s>>>(js, total_patches, ps, stride);
-    const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * 12);
+    // with the queue one block per resident slot (6 per SM), else two waves of them
+    unsigned int* wq = total_tiles + (long long)lc.sm_count * 12 < (1LL << 31) ? lc.wq : nullptr;
+    const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * (wq ? 6 : 12));
     switch (stride) {
-        case 3: densify_fb_kernel<3><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride); break;
-        case 4: densify_fb_kernel<4><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride); break;
-        case 5: densify_fb_kernel<5><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride); break;
-        case 6: densify_fb_kernel<6><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride); break;
-        default: densify_fb_kernel<0><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride); break;
+        case 3: densify_fb_kernel<3><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride, wq); break;
+        case 4: densify_fb_kernel<4><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride, wq); break;
+        case 5: densify_fb_kernel<5><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride, wq); break;
+        case 6: densify_fb_kernel<6><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride, wq); break;
+        default: densify_fb_kernel<0><<<gt, kFbThreads, 0, s>>>(js, total_tiles, ps, stride, wq); break;
     }
     return cudaGetLastError();
 }
