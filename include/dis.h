@@ -225,12 +225,13 @@ dis_status dis_trace_batched(dis_handle* h, const dis_pair* pairs, int n, const 
  * values: DIS_ERR_INVALID_ARG. */
 dis_status dis_set_refine_fusion(dis_handle* h, int fused);
 
-/* Patch scheduling of the inverse search (not in the paper) for handle h.  on = 1 (the default):
- * the grouped search kernels hand out patches from a work queue in the handle's arena (two
- * counters; each group of lanes claims its next patch with one atomic, so groups that drew
- * cheap patches take more of them); on = 0: a fixed grid stride.  Both give the same result bit
- * for bit; the queue keeps every SM busy to the end of the launch.  Calls with and without the
- * queue use different cached graphs.  Other values: DIS_ERR_INVALID_ARG. */
+/* Work scheduling (not in the paper) for handle h.  on = 1 (the default): the grouped search
+ * kernels hand out patches, and the forward-backward densification its tiles, from a work queue
+ * in the handle's arena (two counters; each group of lanes or block claims its next item with
+ * one atomic, so those that drew cheap items take more of them); on = 0: a fixed grid stride.
+ * Both give the same result bit for bit; the queue keeps every SM busy to the end of the launch.
+ * Calls with and without the queue use different cached graphs.  Other values:
+ * DIS_ERR_INVALID_ARG. */
 dis_status dis_set_work_queue(dis_handle* h, int on);
 
 /* Probe (not in the paper): from now on every call of handle h records two events of its own

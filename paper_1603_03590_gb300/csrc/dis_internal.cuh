@@ -124,10 +124,11 @@ __host__ __device__ inline int rs_planes(int C) { return 15 * C + 8; }
 struct LaunchCfg {
     int sm_count;
     int max_blocks_256;  // resident 256-thread blocks per SM for the elementwise kernels
-    // Work queue of the grouped patch search (two zeroed counters in device memory owned by a
-    // handle: the next patch to hand out, the groups that found none left; the last group to
-    // finish zeroes both again, so consecutive launches on the handle's stream and graph
-    // replays each start from zero).  Null: the static grid-stride assignment.
+    // Work queue of the grouped patch search and the forward-backward densification (two zeroed
+    // counters in device memory owned by a handle: the next item to hand out, the groups or
+    // blocks that found none left; the last to finish zeroes both again, so consecutive launches
+    // on the handle's stream and graph replays each start from zero).  Null: the static
+    // grid-stride assignment.
     unsigned int* wq = nullptr;
 };
 

@@ -246,8 +246,9 @@ def dis_set_refine_fusion(handle, mode):
 
 
 def dis_set_work_queue(handle, on):
-    """Inverse-search patch scheduling: True hands patches out from the handle's work queue
-    (default), False uses a fixed grid stride; both give the same flow bit for bit."""
+    """Work scheduling: True hands search patches and forward-backward densification tiles out
+    from the handle's work queue (default), False uses a fixed grid stride; both give the same
+    flow bit for bit."""
     _check(_lib.dis_set_work_queue(handle, int(bool(on))), handle)
 
 
