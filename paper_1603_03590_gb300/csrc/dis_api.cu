@@ -725,7 +725,10 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
     }
     h->jobs_dev = h->arena + h->slot_bytes * max_batch;
     unsigned int* wq = (unsigned int*)(h->jobs_dev + h->jobs_bytes);
-    if ((e = cudaMemset(wq, 0, 2 * sizeof(unsigned int))) != cudaSuccess) {
+    // zeroed before dis_create returns: the caller's stream may be one that does not wait for
+    // the legacy default stream, on which cudaMemset runs
+    if ((e = cudaMemset(wq, 0, 2 * sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) {
         cudaGetLastError();
         dis_destroy(h);
         return fail(nullptr, DIS_ERR_CUDA, std::string("handle setup failed: ") + cudaGetErrorString(e));
