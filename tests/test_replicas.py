@@ -78,3 +78,47 @@ def test_reference_arm_is_silent_on_other_ranks(capsys):
     args = argparse.Namespace(steps=1, warmup=3, preset="dense", gpus=2)
     assert bench.run_reference(args, 1, 2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_0(capsys, monkeypatch):
+    """The reference arm's JSON line: the same metric, unit and config as the GPU arm, the rate of
+    the timed steps only (warm-up steps discarded), no host-device copies, and the oracle sample
+    described.  The oracle itself is replaced by a stand-in that reports a given rate per call."""
+    import json
+    import bench
+    rates = iter([9.0, 9.0, 9.0, 0.5, 0.25])  # three warm-up calls, then two timed steps
+
+    def fake_cpu_baseline(preset, workload="flow", norm="l2", fb=False, term_eps=0.0):
+        return {"value": next(rates), "unit": bench.UNIT, "cores": 1, "kind": "oracle", "sample": "stand-in"}
+
+    monkeypatch.setattr(bench, "cpu_baseline", fake_cpu_baseline)
+    args = argparse.Namespace(steps=2, warmup=3, preset="dense", gpus=1, workload="flow", norm="l2", fb=False,
+                              term_eps=0.0, batch=32)
+    bench.run_reference(args, 0, 1)
+    line = json.loads(capsys.readouterr().out.strip())
+    metric, W, H = bench.WORKLOADS["flow"][:3]
+    assert line["impl"] == "reference" and line["metric"] == metric and line["unit"] == bench.UNIT
+    # each step is 1/4 of a pair's area at the sampled rate: 0.5 and 0.25 pairs/s take 0.5 s and 1 s
+    assert abs(line["value"] - 2 * 0.25 / 1.5) < 1e-12
+    assert line["steps"] == 2 and line["warmup"] == 3 and line["higher_is_better"] is True
+    assert line["dtype"] == "f64" and line["vs_baseline"] is None
+    assert line["config"] == bench.workload_config(args, 32, 1)
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert "%dx%d" % (W // 2, H // 2) in cb["sample"]
+
+
+def test_bench_defaults_keep_the_timing_rules(monkeypatch):
+    """No flags: one GPU, at least three warm-up steps, and a warm-up below three is raised to three."""
+    import bench
+    seen = {}
+    monkeypatch.setattr(bench, "run_reference", lambda args, rank, world: seen.update(vars(args)))
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference"])
+    bench.main()
+    assert seen["gpus"] == 1 and seen["warmup"] >= 3 and seen["steps"] >= 1 and seen["batch"] == 32
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--warmup", "1"])
+    bench.main()
+    assert seen["warmup"] == 3
+
