@@ -21,7 +21,9 @@
  *    immediately and leave every output untouched; device-side failures surface as
  *    DIS_ERR_CUDA on a later call.
  *  - Handles are not thread-safe: use one handle per host thread / stream.
- *  - No entry point throws; no entry point allocates device memory except dis_create.
+ *  - No entry point throws.  Device memory is allocated by dis_create (the arena) and by
+ *    dis_compute_flow_batched_host, which grows the handle's own host-copy staging on first
+ *    use or when a larger batch arrives; every other entry point allocates nothing.
  */
 #ifndef DIS_H
 #define DIS_H
@@ -418,6 +420,10 @@ dis_status dis_backward(dis_handle* h, const float* I0, const float* I1, int w, 
  *    rejected with DIS_ERR_INVALID_ARG before any work is enqueued.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *    with that device current) and caches it; make that first call before any stream capture.
+ *    cudaDeviceReset on a device releases the array with its context, which leaves the cached
+ *    address stale: do not call this entry point on a device after resetting it.
+ *  - It always uses refinement launch form 1 (dis_set_refine_fusion mode 1: one fused launch per
+ *    outer pass, two above 128 Ki pixels); all launch forms give the same flow bit for bit.
  *  - All calls share the one array, which keeps the last call's contents (the call itself
  *    zeroes what must start at zero).  Calls whose GPU work overlaps - on different streams
  *    or host threads - race on it: serialise them (e.g. one stream).

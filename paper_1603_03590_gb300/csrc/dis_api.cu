@@ -1214,7 +1214,10 @@ dis_status dis_refine_level_ex(dis_handle* hd, const float* I0, const float* I1,
         !finite(delta) || !finite(gamma) || !finite(alpha) || !(omega > 0.0f && omega < 2.0f) ||
         (dof != 1 && dof != 2))
         return fail(hd, DIS_ERR_INVALID_ARG, "dis_refine_level: bad pointer, size, pitch or parameter");
-    if ((size_t)dis::rs_planes(channels) * (size_t)pitch * (size_t)h > hd->rs_floats)
+    // each factor is bounded before the product, so that it cannot wrap
+    if (pitch > (int64_t)hd->rs_floats || h > (int64_t)hd->rs_floats ||
+        (unsigned long long)pitch * (unsigned long long)h > (unsigned long long)hd->rs_floats ||
+        (size_t)dis::rs_planes(channels) * (size_t)pitch * (size_t)h > hd->rs_floats)
         return fail(hd, DIS_ERR_INVALID_ARG, "dis_refine_level: level larger than the handle's scratch");
     LevelJob J;
     std::memset(&J, 0, sizeof(J));

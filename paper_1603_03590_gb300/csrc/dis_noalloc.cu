@@ -12,7 +12,8 @@
 // Host code cannot hand `g_refine_scratch` to a kernel: in host code that name denotes a
 // host-side stand-in, not device memory.  The device address is looked up once per device
 // with cudaGetSymbolAddress (with that device current) on the first call made on it, cached,
-// and passed to the kernels.
+// and passed to the kernels.  cudaDeviceReset destroys the array with the context, so the
+// cached address of a device is not valid after a reset of that device.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -43,6 +44,13 @@ extern "C" dis_status dis_refine_level_noalloc(const float* I0, const float* I1,
     if (!I0 || !I1 || !U || w < 1 || h < 1 || pitch < w || channels < 1 || channels > 3 || outer < 0 || inner < 0 ||
         !std::isfinite(delta) || !std::isfinite(gamma) || !std::isfinite(alpha) || !(omega > 0.0f && omega < 2.0f))
         return noalloc_fail(DIS_ERR_INVALID_ARG, "dis_refine_level_noalloc: bad pointer, size, pitch or parameter");
+    // bound each factor before the product, so that it cannot wrap: any level that fits the
+    // array has pitch * h below 2^22
+    if (pitch > (int64_t)DIS_NOALLOC_SCRATCH_FLOATS || h > (int)DIS_NOALLOC_SCRATCH_FLOATS ||
+        (unsigned long long)pitch * (unsigned long long)h > (unsigned long long)DIS_NOALLOC_SCRATCH_FLOATS)
+        return noalloc_fail(DIS_ERR_INVALID_ARG,
+                            "dis_refine_level_noalloc: pitch * height above the fixed scratch of " +
+                                std::to_string((unsigned long long)DIS_NOALLOC_SCRATCH_FLOATS) + " floats");
     const unsigned long long need =
         (unsigned long long)dis::rs_planes(channels) * (unsigned long long)pitch * (unsigned long long)h;
     if (need > (unsigned long long)DIS_NOALLOC_SCRATCH_FLOATS)
@@ -78,7 +86,9 @@ extern "C" dis_status dis_refine_level_noalloc(const float* I0, const float* I1,
     J.rs = scratch;  // every plane is written before it is read; the increments are zeroed first
     long long tiles = 0;
     dis::set_refine_tiles(J, tiles);
-    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega, true, channels};
+    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega};
+    a.fused = 1;  // launch form 1: one fused launch per outer pass, two above kRefineFusedMaxPixels
+    a.C = channels;
     e = dis::launch_refine(dis::single_job(J), (long long)w * h, (long long)h * ((w + 1) / 2), tiles, a,
                            dis::stage_launch_cfg(), (cudaStream_t)stream);
     if (e != cudaSuccess) return noalloc_fail(DIS_ERR_CUDA, std::string("dis_refine_level_noalloc: ") + cudaGetErrorString(e));

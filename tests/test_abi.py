@@ -146,3 +146,15 @@ def test_frames_beyond_32_bit_pixel_indexing_are_refused(dis):
     assert lib.dis_create(ctypes.byref(h), 65536, 32768, 1, 1) == dis.DIS_ERR_INVALID_ARG and not h.value
     assert lib.dis_pyr_down(ctypes.c_void_p(16), 65536, 32768, ctypes.c_int64(65536), ctypes.c_void_p(16),
                             ctypes.c_int64(32768), None) == dis.DIS_ERR_INVALID_ARG
+
+
+def test_refinement_size_checks_cannot_wrap(dis):
+    """A pitch so large that (15 C + 8) * pitch * h wraps 64 bits must still be refused before
+    any work is enqueued (the pointers are never dereferenced)."""
+    lib = ctypes.CDLL(dis.LIB_PATH)
+    fake = ctypes.c_void_p(256)
+    for pitch, h in [(1 << 62, 4), (1 << 40, 1 << 24), ((1 << 31) + 5, 2), ((1 << 22) + 1, 1)]:
+        st = lib.dis_refine_level_noalloc(fake, fake, 8, h, ctypes.c_int64(pitch), 1, fake, 1, 1, ctypes.c_float(5.0),
+                                          ctypes.c_float(10.0), ctypes.c_float(10.0), ctypes.c_float(1.6), None)
+        assert st == dis.DIS_ERR_INVALID_ARG, (pitch, h)
+        assert "scratch" in dis.dis_last_error_string(None)
