@@ -266,6 +266,11 @@ dis_status dis_autotune(dis_handle* h, const dis_pair* pairs, int n, const dis_p
  * (dis_set_refine_fusion) handle h uses for patch size ps; either pointer may be NULL. */
 dis_status dis_get_tuning(const dis_handle* h, int patch_size, int* search_variant, int* refine_fusion);
 
+/* Kernels launched by the most recent call on h (not in the paper): the kernel nodes of the CUDA
+ * graph that call replayed, counted when the graph was captured.  *count is -1 when that call
+ * ran without a graph (checkpoints, or graphs disabled) or no call has run yet. */
+dis_status dis_last_call_kernels(const dis_handle* h, int* count);
+
 /* Search variants offered for patch size ps (codes as for dis_autotune, the default first):
  * writes up to `cap` of them to out (nullable when cap is 0) and returns their count, or 0 for
  * a patch size outside [2, 16]. */

@@ -569,12 +569,17 @@ dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaS
     dis_status ust = upload_jobs(hd, plan, s);
     if (ust != DIS_OK) return ust;
     if (!hd->use_graphs || !plan.graphable) {
+        hd->last_kernels = -1;
         if ((e = record_plan(hd, plan, p, s)) != cudaSuccess) return cuda_fail(hd, e, "kernel launch");
         return DIS_OK;
     }
     cudaGraphExec_t exec = nullptr;
+    int kernels = -1;
     for (auto& g : hd->graphs)
-        if (g.key == plan.key) exec = g.exec;
+        if (g.key == plan.key) {
+            exec = g.exec;
+            kernels = g.kernels;
+        }
     if (!exec) {
         cudaGraph_t graph = nullptr;
         if ((e = cudaStreamBeginCapture(hd->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
@@ -586,6 +591,17 @@ dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaS
             return cuda_fail(hd, le, "kernel launch (capture)");
         }
         if (e != cudaSuccess) return cuda_fail(hd, e, "graph capture end");
+        // count the kernel nodes: the kernels every replay of this graph launches
+        size_t nn = 0;
+        kernels = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+                for (size_t k = 0; k < nn; ++k) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nodes[k], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+                }
+        }
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(hd, e, "graph instantiate");
@@ -593,9 +609,10 @@ dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaS
             cudaGraphExecDestroy(hd->graphs.front().exec);
             hd->graphs.erase(hd->graphs.begin());
         }
-        hd->graphs.push_back({plan.key, exec});
+        hd->graphs.push_back({plan.key, exec, kernels});
     }
     if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(hd, e, "graph launch");
+    hd->last_kernels = kernels;
     return DIS_OK;
 }
 
@@ -1356,6 +1373,13 @@ extern "C" dis_status dis_get_tuning(const dis_handle* hd, int patch_size, int* 
         *search_variant = hd->search_lanes[patch_size] ? hd->search_lanes[patch_size] : opts[0];
     }
     if (refine_fusion) *refine_fusion = hd->refine_fused;
+    return DIS_OK;
+}
+
+extern "C" dis_status dis_last_call_kernels(const dis_handle* hd, int* count)
+{
+    if (!hd || !count) return fail(const_cast<dis_handle*>(hd), DIS_ERR_INVALID_ARG, "dis_last_call_kernels: NULL argument");
+    *count = hd->last_kernels;
     return DIS_OK;
 }
 

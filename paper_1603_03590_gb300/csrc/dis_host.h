@@ -30,12 +30,14 @@ struct dis_handle {
     struct Graph {
         std::vector<int64_t> key;
         cudaGraphExec_t exec;
+        int kernels;  // kernel nodes of the captured graph
     };
     std::vector<Graph> graphs;
     dis::LaunchCfg lc{};
     bool use_graphs = true;
     int search_lanes[17] = {};  // autotuned lanes per patch by patch size (0 = default)
     int refine_fused = 1;       // refinement launch form (dis_set_refine_fusion)
+    int last_kernels = -1;      // kernels of the graph the most recent call replayed (-1: none)
     unsigned int* wq = nullptr;  // the search work queue in the arena (lc.wq while enabled)
     // probe: events recorded around one launch group in every call (also inside graphs)
     int probe_kind = -1, probe_level = 0;

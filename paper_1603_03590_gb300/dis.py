@@ -85,6 +85,7 @@ _SIGS = {
     "dis_autotune": (_i, [_vp, ctypes.POINTER(dis_pair), _i, _P, _vp, ctypes.POINTER(_i)]),
     "dis_search_variants": (_i, [_i, ctypes.POINTER(_i), _i]),
     "dis_get_tuning": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "dis_last_call_kernels": (_i, [_vp, ctypes.POINTER(_i)]),
     "dis_set_probe": (_i, [_vp, _i, _i]),
     "dis_set_refine_fusion": (_i, [_vp, _i]),
     "dis_set_work_queue": (_i, [_vp, _i]),
@@ -270,6 +271,14 @@ def dis_get_tuning(handle, patch_size):
     v, r = _i(), _i()
     _check(_lib.dis_get_tuning(handle, patch_size, ctypes.byref(v), ctypes.byref(r)), handle)
     return v.value, r.value
+
+
+def dis_last_call_kernels(handle):
+    """Kernels the most recent call on the handle launched (its graph's kernel nodes; -1 when it
+    ran without a graph)."""
+    c = _i()
+    _check(_lib.dis_last_call_kernels(handle, ctypes.byref(c)), handle)
+    return c.value
 
 
 def dis_search_variants(patch_size):

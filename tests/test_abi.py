@@ -158,3 +158,17 @@ def test_refinement_size_checks_cannot_wrap(dis):
                                           ctypes.c_float(10.0), ctypes.c_float(10.0), ctypes.c_float(1.6), None)
         assert st == dis.DIS_ERR_INVALID_ARG, (pitch, h)
         assert "scratch" in dis.dis_last_error_string(None)
+
+
+def test_bench_preset_table_matches_the_library(dis):
+    """bench.py builds the oracle's parameters of its CPU legs from a plain table (so that those
+    legs load no product code); the table must hold the library's preset values."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    for name, vals in bench.PRESETS.items():
+        p = dis.dis_default_params(name)
+        for k, v in vals.items():
+            assert abs(getattr(p, k) - v) < 1e-6, (name, k, getattr(p, k), v)
+    p = dis.dis_default_params("default", **bench.DIFF_PARAMS)
+    assert (p.patch_size, p.var_outer, p.var_inner, p.coarsest_scale) == (8, 1, 10, 3)

@@ -5,6 +5,7 @@ import multiprocessing as mp
 import os
 import socket
 
+import numpy as np
 import pytest
 
 from paper_1603_03590_gb300 import replicas
@@ -80,34 +81,73 @@ def test_reference_arm_is_silent_on_other_ranks(capsys):
     assert capsys.readouterr().out == ""
 
 
+class _FakePool:
+    """Stand-in for bench.OraclePool: records the specs it is given and reports 0.5 s of oracle
+    time per unit, one pair each, without running the oracle."""
+    seen = []
+
+    def __init__(self, procs):
+        self.procs = procs
+
+    def map(self, specs):
+        _FakePool.seen.append(list(specs))
+        return [(0.5, 1.0, None) for _ in specs]
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
 def test_reference_arm_line_on_rank_0(capsys, monkeypatch):
-    """The reference arm's JSON line: the same metric, unit and config as the GPU arm, the rate of
-    the timed steps only (warm-up steps discarded), no host-device copies, and the oracle sample
-    described.  The oracle itself is replaced by a stand-in that reports a given rate per call."""
+    """The reference arm's JSON line: the same metric, unit and workload config as the GPU arm,
+    one full-size pair per step, warm-up steps run first on other pairs, the rate of the timed
+    steps over their wall time (ms_per_step x steps is that wall time), no host-device copies,
+    and the oracle run described.  The pool of oracle processes is replaced by a stand-in."""
     import json
     import bench
-    rates = iter([9.0, 9.0, 9.0, 0.5, 0.25])  # three warm-up calls, then two timed steps
-
-    def fake_cpu_baseline(preset, workload="flow", norm="l2", fb=False, term_eps=0.0):
-        return {"value": next(rates), "unit": bench.UNIT, "cores": 1, "kind": "oracle", "sample": "stand-in"}
-
-    monkeypatch.setattr(bench, "cpu_baseline", fake_cpu_baseline)
+    _FakePool.seen = []
+    monkeypatch.setattr(bench, "OraclePool", _FakePool)
     args = argparse.Namespace(steps=2, warmup=3, preset="dense", gpus=1, workload="flow", norm="l2", fb=False,
                               term_eps=0.0, batch=32)
     bench.run_reference(args, 0, 1)
     line = json.loads(capsys.readouterr().out.strip())
-    metric, W, H = bench.WORKLOADS["flow"][:3]
-    assert line["impl"] == "reference" and line["metric"] == metric and line["unit"] == bench.UNIT
-    # each step is 1/4 of a pair's area at the sampled rate: 0.5 and 0.25 pairs/s take 0.5 s and 1 s
-    assert abs(line["value"] - 2 * 0.25 / 1.5) < 1e-12
-    assert line["steps"] == 2 and line["warmup"] == 3 and line["higher_is_better"] is True
+    assert line["impl"] == "reference" and line["metric"] == bench.WORKLOADS["flow"]["metric"]
+    assert line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["steps"] == 2 and line["warmup"] == 3
     assert line["dtype"] == "f64" and line["vs_baseline"] is None
     assert line["config"] == bench.workload_config(args, 32, 1)
+    # warm-up units first (pairs 2, 3, 4), then the timed ones (pairs 0, 1), one pair per step
+    assert [sp[2] for sp in _FakePool.seen[0]] == [[2], [3], [4]]
+    assert [sp[2] for sp in _FakePool.seen[1]] == [[0], [1]]
+    assert all(sp[0] == "flow" and sp[1] == "dense" and sp[3] is None for sp in _FakePool.seen[1])
+    wall = line["ms_per_step"] * line["steps"] / 1000.0
+    assert abs(line["value"] - 2 / wall) <= 1e-9 * line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
-    assert "%dx%d" % (W // 2, H // 2) in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == line["value"]
+    assert "1024x436" in cb["sample"] and "0.50 s median" in cb["sample"]
+
+
+def test_cpu_units_match_the_workloads():
+    """The CPU legs' units: full pairs of the workload's generator (the GPU arm's pair k), or a
+    stated sample at 1/16 (RGB 4K) and 1/4 (stereo) of the area."""
+    import bench
+    from paper_1603_03590_gb300 import synth
+    I0, I1, gt, q, per, _ = bench.cpu_unit("flow", "dense", 1)
+    r0, r1, _ = synth.workload_pair("layered1024x436", 1)
+    assert np.array_equal(I0, r0) and np.array_equal(I1, r1) and per == 1.0
+    assert q["patch_size"] == 12 and q["grad_iters"] == 128 and q["coarsest_scale"] == 4 and q["refine"] == 1
+    q = bench.cpu_unit("flow", "fast", 0)[3]
+    assert (q["patch_size"], q["grad_iters"], q["finest_scale"], q["refine"]) == (8, 16, 2, 0)
+    I0, _, _, q, per, _ = bench.cpu_unit("rgb4k", "dense", 0)
+    assert I0.shape == (3, 540, 960) and per == 1.0 / 16 and q["channels"] == 3 and q["coarsest_scale"] == 4
+    I0, _, _, q, per, _ = bench.cpu_unit("stereo", "stereo_dense", 0)
+    assert I0.shape == (480, 720) and per == 0.25 and q["dof"] == 1
+    I0, _, _, q, per, _ = bench.cpu_unit("translate128x96", "cfg0", 0)
+    assert I0.shape == (96, 128) and q["stride_override"] == 4
 
 
 def test_bench_defaults_keep_the_timing_rules(monkeypatch):
@@ -118,6 +158,7 @@ def test_bench_defaults_keep_the_timing_rules(monkeypatch):
     monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference"])
     bench.main()
     assert seen["gpus"] == 1 and seen["warmup"] >= 3 and seen["steps"] >= 1 and seen["batch"] == 32
+    assert seen["unique"] == 32  # 32 distinct scenes per batch
     monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--warmup", "1"])
     bench.main()
     assert seen["warmup"] == 3
