@@ -4,33 +4,48 @@
 // eps = 0.001, with the normalised intensity term E_I = beta0 (I_x du + I_y dv + I_z)^2, the
 // gradient term E_G = betax (I_xx du + I_xy dv + I_xz)^2 + betay (I_xy du + I_yy dv + I_yz)^2
 // (beta = (|grad_2 .|^2 + 0.01)^-1), summed over channels inside each Psi, and the smoothness
-// term E_S = |grad(u + du)|^2 + |grad(v + dv)|^2.  Discretisation: I1 warped once by U;
-// first derivatives are Sobel/8 of (I0 + I1w)/2, second derivatives Sobel/8 of those,
-// I_z = I1w - I0, I_xz / I_yz the Sobel/8 differences of I1w and I0; smoothness by central
-// differences (replicated border) and 4-neighbour edge weights (psiS_p + psiS_q)/2.
-// theta_vo lagged-nonlinearity passes each freeze psi = weight * Psi'(.) and run theta_vi
-// red-black SOR sweeps (red = (x + y) even first) on the per-pixel 2x2 systems.
+// term E_S = |grad(u + du)|^2 + |grad(v + dv)|^2.  Discretisation: I1 warped once by U; with the
+// mean image Ibar = (I0 + I1w)/2 and the temporal difference I_z = I1w - I0, first derivatives
+// are Sobel/8 of Ibar, second derivatives Sobel/8 of those, I_xz / I_yz Sobel/8 of I_z (the
+// difference of the two frames' Sobel derivatives); smoothness by central differences
+// (replicated border) and 4-neighbour edge weights (psiS_p + psiS_q)/2.  theta_vo
+// lagged-nonlinearity passes each freeze psi = weight * Psi'(.) and run theta_vi red-black SOR
+// sweeps (red = (x + y) even first) on the per-pixel 2x2 systems.
 //
-// Kernels (thread per pixel, flattened over all jobs of a phase):
-//   warp     I1w = I1(x + U), dU = 0                                  (once per level)
-//   deriv1   I_x, I_y, I_z, I_xz, I_yz                                 (once per level)
-//   deriv2   I_xx, I_xy, I_yy, betas -> 9 data values per channel      (once per level)
-//   weights  A (3), b (2), psiS from the data values and U + dU        (per outer pass)
-//   sor      one colour of one sweep                                   (2 per sweep)
-//   apply    U += dU                                                   (once per level)
-// or, fused (the default), weights and all half-sweeps of one outer pass in one launch: each
-// block loads a 32x32 tile with a halo as wide as the half-sweeps (K <= 10) into shared
-// memory, computes the lagged weights there, runs the K red-black half-sweeps with a block
-// barrier between them (the halo absorbs the values that go stale at the tile's edge: after
-// half-sweep j only pixels within K - j of the tile are still exact) and writes the tile's
-// increments to the other of two increment buffers.  The arithmetic is shared with the
-// per-sweep kernels, so both forms give the same result bit for bit.
+// Every form starts with refine_prep (thread per pixel): I1w = I1(x + U) and the two planes per
+// channel every later step derives its data from, Ibar and I_z.
+//
+// Fused form (the default): one launch per outer pass (or two, each with half of its
+// half-sweeps and half the halo).  A block takes a 32x32 tile and, in shared memory,
+//   - loads Ibar and I_z of the tile with a halo of K + 2 (K = the launch's half-sweeps),
+//   - forms I_x, I_y on a halo of K + 1 and from them, per pixel of a halo of K, the nine data
+//     values of each channel and the lagged 2x2 system (the increment at the pass start comes
+//     from global memory),
+//   - loads U and that increment on a halo of K + 1 and forms the smoothness weights,
+//   - runs the K red-black half-sweeps with a block barrier between them (after half-sweep j
+//     only pixels within K - 1 - j of the tile still need to be exact, so each sweeps a smaller
+//     square), and writes the tile's increment.
+// Nothing but Ibar, I_z, U and the increments crosses DRAM.
+// Per-sweep form (dis_set_refine_fusion 0, or more than 5 sweeps per pass): thread-per-pixel
+// kernels write I_x, I_y, then the data values, then per pass the systems and one launch per
+// half-sweep.  Both forms share every arithmetic step (refine_dvals, refine_energy_acc,
+// refine_psi, refine_system_acc, refine_smooth_weight, refine_sor_update), so they agree bit
+// for bit.
 #include <algorithm>
+#include <stdint.h>
 #include <type_traits>
 
 #include "dis_device.cuh"
 
 namespace dis {
+
+// Planes of the refinement scratch (rs_mid slots of channel c): the mean image and I_z (every
+// form), I_x and I_y (per-sweep form).  The fused form keeps its increments in rs_du, in the
+// fifth and sixth intermediate planes of channel 0 and in the first two system planes.
+__host__ __device__ inline int rp_bar(int C, int c) { return rs_mid(C, c, 0); }
+__host__ __device__ inline int rp_iz(int C, int c) { return rs_mid(C, c, 1); }
+__host__ __device__ inline int rp_ix(int C, int c) { return rs_mid(C, c, 2); }
+__host__ __device__ inline int rp_iy(int C, int c) { return rs_mid(C, c, 3); }
 
 #define DIS_PIX_LOOP(BASE)                                                               \
     for (long long g = gtid(); g < total; g += gstride()) {                              \
@@ -43,112 +58,71 @@ namespace dis {
 
 #define DIS_PIX_END }
 
-__global__ void __launch_bounds__(256) refine_warp_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total)
+// ---------------------------------------------------------------- shared arithmetic
+// Sobel/8 of a 3x3 neighbourhood v (row-major, centre v[4]).  (2 (f - d) is exact, so whether
+// the compiler fuses it into the following add does not change the result.)
+__device__ __forceinline__ float sobel_x9(const float (&v)[9])
 {
-    DIS_PIX_LOOP(pix_base)
-    const float2 U = J.U[k];
-    for (int c = 0; c < J.C; ++c)
-        J.rs[rs_mid(J.C, c, 0) * J.plane + o] = sample_shift(J.P1 + c * J.plane, w, h, pitch, x, y, U.x, U.y);
-    J.rs[rs_du(J.C, 0) * J.plane + o] = 0.0f;
-    J.rs[rs_du(J.C, 1) * J.plane + o] = 0.0f;
-    DIS_PIX_END
+    return 0.125f * (((v[2] - v[0]) + 2.0f * (v[5] - v[3])) + (v[8] - v[6]));
+}
+__device__ __forceinline__ float sobel_y9(const float (&v)[9])
+{
+    return 0.125f * (((v[6] - v[0]) + 2.0f * (v[7] - v[1])) + (v[8] - v[2]));
 }
 
-// Sobel/8 of plane P at (x, y) with replicated border.
-__device__ __forceinline__ void sobel_at(const float* __restrict__ P, int pitch, int xl, int x, int xr,
-                                         long long ru, long long rc, long long rd, float& gx, float& gy)
+// The nine data values of one channel at a pixel, from the 3x3 neighbourhoods of I_x, I_y and
+// I_z around it: sqrt(beta0) (I_x, I_y, I_z), sqrt(betax) (I_xx, I_xy, I_xz), sqrt(betay)
+// (I_xy, I_yy, I_yz), with I_xx = Sobel_x(I_x), I_xy = Sobel_y(I_x), I_yy = Sobel_y(I_y).
+__device__ __forceinline__ void refine_dvals(const float (&ix)[9], const float (&iy)[9], const float (&iz)[9],
+                                             float (&d)[9])
 {
-    const float a = P[ru + xl], b = P[ru + x], c = P[ru + xr];
-    const float d = P[rc + xl], f = P[rc + xr];
-    const float p = P[rd + xl], q = P[rd + x], s = P[rd + xr];
-    gx = 0.125f * ((c - a) + 2.0f * (f - d) + (s - p));
-    gy = 0.125f * ((p - a) + 2.0f * (q - b) + (s - c));
+    const float Ixx = sobel_x9(ix), Ixy = sobel_y9(ix), Iyy = sobel_y9(iy);
+    const float Ixz = sobel_x9(iz), Iyz = sobel_y9(iz);
+    const float Ix = ix[4], Iy = iy[4], Iz = iz[4];
+    const float s0 = 1.0f / sqrtf(fmaf(Ix, Ix, fmaf(Iy, Iy, 0.01f)));
+    const float sx = 1.0f / sqrtf(fmaf(Ixx, Ixx, fmaf(Ixy, Ixy, 0.01f)));
+    const float sy = 1.0f / sqrtf(fmaf(Ixy, Ixy, fmaf(Iyy, Iyy, 0.01f)));
+    d[0] = s0 * Ix;
+    d[1] = s0 * Iy;
+    d[2] = s0 * Iz;
+    d[3] = sx * Ixx;
+    d[4] = sx * Ixy;
+    d[5] = sx * Ixz;
+    d[6] = sy * Ixy;
+    d[7] = sy * Iyy;
+    d[8] = sy * Iyz;
 }
 
-__global__ void __launch_bounds__(256) refine_deriv1_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total)
+// One channel's share of the data energies at increment (du, dv).
+__device__ __forceinline__ void refine_energy_acc(const float (&d)[9], float du, float dv, float& EI, float& EG)
 {
-    DIS_PIX_LOOP(pix_base)
-    const int xl = max(x - 1, 0), xr = min(x + 1, w - 1);
-    const long long ru = (long long)max(y - 1, 0) * pitch, rc = (long long)y * pitch,
-                    rd = (long long)min(y + 1, h - 1) * pitch;
-    for (int c = 0; c < J.C; ++c) {
-        const float* P0 = J.P0 + c * J.plane;
-        const float* W1 = J.rs + rs_mid(J.C, c, 0) * J.plane;
-        float sx0, sy0, sx1, sy1;
-        sobel_at(P0, pitch, xl, x, xr, ru, rc, rd, sx0, sy0);
-        sobel_at(W1, pitch, xl, x, xr, ru, rc, rd, sx1, sy1);
-        J.rs[rs_mid(J.C, c, 1) * J.plane + o] = 0.5f * (sx0 + sx1);
-        J.rs[rs_mid(J.C, c, 2) * J.plane + o] = 0.5f * (sy0 + sy1);
-        J.rs[rs_mid(J.C, c, 3) * J.plane + o] = W1[o] - P0[o];
-        J.rs[rs_mid(J.C, c, 4) * J.plane + o] = sx1 - sx0;
-        J.rs[rs_mid(J.C, c, 5) * J.plane + o] = sy1 - sy0;
-    }
-    DIS_PIX_END
+    const float eI = fmaf(d[0], du, fmaf(d[1], dv, d[2]));
+    const float eX = fmaf(d[3], du, fmaf(d[4], dv, d[5]));
+    const float eY = fmaf(d[6], du, fmaf(d[7], dv, d[8]));
+    EI = fmaf(eI, eI, EI);
+    EG = fmaf(eX, eX, fmaf(eY, eY, EG));
 }
 
-__global__ void __launch_bounds__(256) refine_deriv2_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total)
-{
-    DIS_PIX_LOOP(pix_base)
-    const int xl = max(x - 1, 0), xr = min(x + 1, w - 1);
-    const long long ru = (long long)max(y - 1, 0) * pitch, rc = (long long)y * pitch,
-                    rd = (long long)min(y + 1, h - 1) * pitch;
-    for (int c = 0; c < J.C; ++c) {
-        const float* Ixp = J.rs + rs_mid(J.C, c, 1) * J.plane;
-        const float* Iyp = J.rs + rs_mid(J.C, c, 2) * J.plane;
-        float Ixx, Ixy, Iyx, Iyy;
-        sobel_at(Ixp, pitch, xl, x, xr, ru, rc, rd, Ixx, Ixy);
-        sobel_at(Iyp, pitch, xl, x, xr, ru, rc, rd, Iyx, Iyy);
-        (void)Iyx;
-        const float Ix = Ixp[o], Iy = Iyp[o];
-        const float Iz = J.rs[rs_mid(J.C, c, 3) * J.plane + o];
-        const float Ixz = J.rs[rs_mid(J.C, c, 4) * J.plane + o];
-        const float Iyz = J.rs[rs_mid(J.C, c, 5) * J.plane + o];
-        const float s0 = 1.0f / sqrtf(Ix * Ix + Iy * Iy + 0.01f);
-        const float sx = 1.0f / sqrtf(Ixx * Ixx + Ixy * Ixy + 0.01f);
-        const float sy = 1.0f / sqrtf(Ixy * Ixy + Iyy * Iyy + 0.01f);
-        float* D = J.rs + rs_dat(J.C, c, 0) * J.plane + o;
-        D[0 * J.plane] = s0 * Ix;
-        D[1 * J.plane] = s0 * Iy;
-        D[2 * J.plane] = s0 * Iz;
-        D[3 * J.plane] = sx * Ixx;
-        D[4 * J.plane] = sx * Ixy;
-        D[5 * J.plane] = sx * Ixz;
-        D[6 * J.plane] = sy * Ixy;
-        D[7 * J.plane] = sy * Iyy;
-        D[8 * J.plane] = sy * Iyz;
-    }
-    DIS_PIX_END
-}
-
-// Lagged data terms of pixel o at increment (du, dv): the 2x2 system A dU = b of the data
-// energy with psi = weight * Psi'(.) frozen (summed over channels inside each Psi).
-__device__ __forceinline__ void refine_data_system(const float* __restrict__ rs, int C, long long pl, long long o,
-                                                   float du, float dv, float delta, float gamma, float& a11,
-                                                   float& a12, float& a22, float& b1, float& b2)
+// Lagged weights psi = weight * Psi'(E) of the two data terms.
+__device__ __forceinline__ void refine_psi(float EI, float EG, float delta, float gamma, float& psiI, float& psiG)
 {
     const float eps2 = 1.0e-6f;
-    float EI = 0.0f, EG = 0.0f;
-    for (int c = 0; c < C; ++c) {
-        const float* D = rs + rs_dat(C, c, 0) * pl + o;
-        const float eI = fmaf(D[0], du, fmaf(D[pl], dv, D[2 * pl]));
-        const float eX = fmaf(D[3 * pl], du, fmaf(D[4 * pl], dv, D[5 * pl]));
-        const float eY = fmaf(D[6 * pl], du, fmaf(D[7 * pl], dv, D[8 * pl]));
-        EI = fmaf(eI, eI, EI);
-        EG = fmaf(eX, eX, fmaf(eY, eY, EG));
-    }
-    const float psiI = delta / (2.0f * sqrtf(EI + eps2));
-    const float psiG = gamma / (2.0f * sqrtf(EG + eps2));
-    a11 = a12 = a22 = b1 = b2 = 0.0f;
-    for (int c = 0; c < C; ++c) {
-        const float* D = rs + rs_dat(C, c, 0) * pl + o;
-        const float d0 = D[0], d1 = D[pl], d2 = D[2 * pl], d3 = D[3 * pl], d4 = D[4 * pl], d5 = D[5 * pl];
-        const float d6 = D[6 * pl], d7 = D[7 * pl], d8 = D[8 * pl];
-        a11 += psiI * d0 * d0 + psiG * (d3 * d3 + d6 * d6);
-        a12 += psiI * d0 * d1 + psiG * (d3 * d4 + d6 * d7);
-        a22 += psiI * d1 * d1 + psiG * (d4 * d4 + d7 * d7);
-        b1 -= psiI * d2 * d0 + psiG * (d5 * d3 + d8 * d6);
-        b2 -= psiI * d2 * d1 + psiG * (d5 * d4 + d8 * d7);
-    }
+    psiI = delta / (2.0f * sqrtf(EI + eps2));
+    psiG = gamma / (2.0f * sqrtf(EG + eps2));
+}
+
+// One channel's share of the 2x2 data system A dU = b with the weights psi frozen.
+__device__ __forceinline__ void refine_system_acc(const float (&d)[9], float psiI, float psiG, float& a11, float& a12,
+                                                  float& a22, float& b1, float& b2)
+{
+    const float p0 = __fmul_rn(psiI, d[0]), p1 = __fmul_rn(psiI, d[1]), p2 = __fmul_rn(psiI, d[2]);
+    const float q3 = __fmul_rn(psiG, d[3]), q4 = __fmul_rn(psiG, d[4]), q5 = __fmul_rn(psiG, d[5]);
+    const float q6 = __fmul_rn(psiG, d[6]), q7 = __fmul_rn(psiG, d[7]), q8 = __fmul_rn(psiG, d[8]);
+    a11 = __fadd_rn(a11, fmaf(p0, d[0], fmaf(q3, d[3], __fmul_rn(q6, d[6]))));
+    a12 = __fadd_rn(a12, fmaf(p0, d[1], fmaf(q3, d[4], __fmul_rn(q6, d[7]))));
+    a22 = __fadd_rn(a22, fmaf(p1, d[1], fmaf(q4, d[4], __fmul_rn(q7, d[7]))));
+    b1 = __fsub_rn(b1, fmaf(p2, d[0], fmaf(q5, d[3], __fmul_rn(q8, d[6]))));
+    b2 = __fsub_rn(b2, fmaf(p2, d[1], fmaf(q5, d[4], __fmul_rn(q8, d[7]))));
 }
 
 // Smoothness weight alpha * Psi'(|grad(u + du)|^2) from the four central differences.
@@ -162,36 +136,6 @@ __device__ __forceinline__ float refine_smooth_weight(float ux, float uy, float 
 __device__ __forceinline__ float refine_cdiff(float Ur, float dur, float Ul, float dul)
 {
     return 0.5f * ((Ur + dur) - (Ul + dul));
-}
-
-__global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_constant__ Jobs<LevelJob> js,
-                                                             long long total, float delta, float gamma, float alpha)
-{
-    DIS_PIX_LOOP(pix_base)
-    const long long pl = J.plane;
-    const float* du_p = J.rs + rs_du(J.C, 0) * pl;
-    const float* dv_p = J.rs + rs_du(J.C, 1) * pl;
-    float a11, a12, a22, b1, b2;
-    refine_data_system(J.rs, J.C, pl, o, du_p[o], dv_p[o], delta, gamma, a11, a12, a22, b1, b2);
-    // smoothness: central differences of u + du, replicated border
-    const int xl = max(x - 1, 0), xr = min(x + 1, w - 1), yu = max(y - 1, 0), yd = min(y + 1, h - 1);
-    const long long fl = (long long)y * w + xl, fr = (long long)y * w + xr;
-    const long long fu = (long long)yu * w + x, fd = (long long)yd * w + x;
-    const long long ol = (long long)y * pitch + xl, orr = (long long)y * pitch + xr;
-    const long long ou = (long long)yu * pitch + x, od = (long long)yd * pitch + x;
-    const float2 Ul = J.U[fl], Ur = J.U[fr], Uu = J.U[fu], Ud = J.U[fd];
-    const float ux = refine_cdiff(Ur.x, du_p[orr], Ul.x, du_p[ol]);
-    const float vx = refine_cdiff(Ur.y, dv_p[orr], Ul.y, dv_p[ol]);
-    const float uy = refine_cdiff(Ud.x, du_p[od], Uu.x, du_p[ou]);
-    const float vy = refine_cdiff(Ud.y, dv_p[od], Uu.y, dv_p[ou]);
-    float* S = J.rs + rs_sys(J.C, 0) * pl + o;
-    S[0] = a11;
-    S[pl] = a12;
-    S[2 * pl] = a22;
-    S[3 * pl] = b1;
-    S[4 * pl] = b2;
-    S[5 * pl] = refine_smooth_weight(ux, uy, vx, vy, alpha);
-    DIS_PIX_END
 }
 
 // One SOR update of pixel p: neighbours q (left, right, up, down; `in[q]` false outside the
@@ -236,6 +180,126 @@ __device__ __forceinline__ void refine_sor_update(float a11, float a12, float a2
     }
 }
 
+// ---------------------------------------------------------------- thread-per-pixel kernels
+// I1w = I1(x + U) per channel, then Ibar = (I0 + I1w)/2 and I_z = I1w - I0; zero_du: also
+// zero the increment planes (the per-sweep form starts from them).
+__global__ void __launch_bounds__(256) refine_prep_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
+                                                          int zero_du)
+{
+    DIS_PIX_LOOP(pix_base)
+    const float2 U = J.U[k];
+    for (int c = 0; c < J.C; ++c) {
+        const float w1 = sample_shift(J.P1 + c * J.plane, w, h, pitch, x, y, U.x, U.y);
+        const float p0 = J.P0[c * J.plane + o];
+        J.rs[rp_bar(J.C, c) * J.plane + o] = 0.5f * (p0 + w1);
+        J.rs[rp_iz(J.C, c) * J.plane + o] = w1 - p0;
+    }
+    if (zero_du) {
+        J.rs[rs_du(J.C, 0) * J.plane + o] = 0.0f;
+        J.rs[rs_du(J.C, 1) * J.plane + o] = 0.0f;
+    }
+    DIS_PIX_END
+}
+
+// 3x3 neighbourhood of plane P around (x, y), replicated border (xl, xr, row offsets clamped).
+__device__ __forceinline__ void gather3x3(const float* __restrict__ P, int xl, int x, int xr, long long ru,
+                                          long long rc, long long rd, float (&v)[9])
+{
+    v[0] = P[ru + xl], v[1] = P[ru + x], v[2] = P[ru + xr];
+    v[3] = P[rc + xl], v[4] = P[rc + x], v[5] = P[rc + xr];
+    v[6] = P[rd + xl], v[7] = P[rd + x], v[8] = P[rd + xr];
+}
+
+// Per-sweep form: I_x, I_y = Sobel/8 of the mean image.
+__global__ void __launch_bounds__(256) refine_grad_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total)
+{
+    DIS_PIX_LOOP(pix_base)
+    const int xl = max(x - 1, 0), xr = min(x + 1, w - 1);
+    const long long ru = (long long)max(y - 1, 0) * pitch, rc = (long long)y * pitch,
+                    rd = (long long)min(y + 1, h - 1) * pitch;
+    for (int c = 0; c < J.C; ++c) {
+        float v[9];
+        gather3x3(J.rs + rp_bar(J.C, c) * J.plane, xl, x, xr, ru, rc, rd, v);
+        J.rs[rp_ix(J.C, c) * J.plane + o] = sobel_x9(v);
+        J.rs[rp_iy(J.C, c) * J.plane + o] = sobel_y9(v);
+    }
+    DIS_PIX_END
+}
+
+// Per-sweep form: the nine data values per channel.
+__global__ void __launch_bounds__(256) refine_data_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total)
+{
+    DIS_PIX_LOOP(pix_base)
+    const int xl = max(x - 1, 0), xr = min(x + 1, w - 1);
+    const long long ru = (long long)max(y - 1, 0) * pitch, rc = (long long)y * pitch,
+                    rd = (long long)min(y + 1, h - 1) * pitch;
+    for (int c = 0; c < J.C; ++c) {
+        float ix[9], iy[9], iz[9], d[9];
+        gather3x3(J.rs + rp_ix(J.C, c) * J.plane, xl, x, xr, ru, rc, rd, ix);
+        gather3x3(J.rs + rp_iy(J.C, c) * J.plane, xl, x, xr, ru, rc, rd, iy);
+        gather3x3(J.rs + rp_iz(J.C, c) * J.plane, xl, x, xr, ru, rc, rd, iz);
+        refine_dvals(ix, iy, iz, d);
+        float* D = J.rs + rs_dat(J.C, c, 0) * J.plane + o;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) D[q * J.plane] = d[q];
+    }
+    DIS_PIX_END
+}
+
+// Lagged data system of pixel o from the data planes (per-sweep form), channel order as in the
+// fused form.
+__device__ __forceinline__ void refine_data_system(const float* __restrict__ rs, int C, long long pl, long long o,
+                                                   float du, float dv, float delta, float gamma, float& a11,
+                                                   float& a12, float& a22, float& b1, float& b2)
+{
+    float EI = 0.0f, EG = 0.0f;
+    for (int c = 0; c < C; ++c) {
+        float d[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] = rs[(rs_dat(C, c, 0) + q) * pl + o];
+        refine_energy_acc(d, du, dv, EI, EG);
+    }
+    float psiI, psiG;
+    refine_psi(EI, EG, delta, gamma, psiI, psiG);
+    a11 = a12 = a22 = b1 = b2 = 0.0f;
+    for (int c = 0; c < C; ++c) {
+        float d[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] = rs[(rs_dat(C, c, 0) + q) * pl + o];
+        refine_system_acc(d, psiI, psiG, a11, a12, a22, b1, b2);
+    }
+}
+
+__global__ void __launch_bounds__(256) refine_weights_kernel(const __grid_constant__ Jobs<LevelJob> js,
+                                                             long long total, float delta, float gamma, float alpha)
+{
+    DIS_PIX_LOOP(pix_base)
+    const long long pl = J.plane;
+    const float* du_p = J.rs + rs_du(J.C, 0) * pl;
+    const float* dv_p = J.rs + rs_du(J.C, 1) * pl;
+    float a11, a12, a22, b1, b2;
+    refine_data_system(J.rs, J.C, pl, o, du_p[o], dv_p[o], delta, gamma, a11, a12, a22, b1, b2);
+    // smoothness: central differences of u + du, replicated border
+    const int xl = max(x - 1, 0), xr = min(x + 1, w - 1), yu = max(y - 1, 0), yd = min(y + 1, h - 1);
+    const long long fl = (long long)y * w + xl, fr = (long long)y * w + xr;
+    const long long fu = (long long)yu * w + x, fd = (long long)yd * w + x;
+    const long long ol = (long long)y * pitch + xl, orr = (long long)y * pitch + xr;
+    const long long ou = (long long)yu * pitch + x, od = (long long)yd * pitch + x;
+    const float2 Ul = J.U[fl], Ur = J.U[fr], Uu = J.U[fu], Ud = J.U[fd];
+    const float ux = refine_cdiff(Ur.x, du_p[orr], Ul.x, du_p[ol]);
+    const float vx = refine_cdiff(Ur.y, dv_p[orr], Ul.y, dv_p[ol]);
+    const float uy = refine_cdiff(Ud.x, du_p[od], Uu.x, du_p[ou]);
+    const float vy = refine_cdiff(Ud.y, dv_p[od], Uu.y, dv_p[ou]);
+    float* S = J.rs + rs_sys(J.C, 0) * pl + o;
+    S[0] = a11;
+    S[pl] = a12;
+    S[2 * pl] = a22;
+    S[3 * pl] = b1;
+    S[4 * pl] = b2;
+    S[5 * pl] = refine_smooth_weight(ux, uy, vx, vy, alpha);
+    DIS_PIX_END
+}
+
 // One colour of one red-black sweep: the pixels with (x + y) % 2 == colour.
 __global__ void __launch_bounds__(256) refine_sor_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
                                                          int colour, float omega, int dof)
@@ -276,15 +340,46 @@ __global__ void __launch_bounds__(256) refine_sor_kernel(const __grid_constant__
     }
 }
 
-// Weights and K half-sweeps of one outer pass on 32x32 tiles (see the header).  The increment
-// is read from planes `src` (rs_du or rs_mid(C, 0, .)) and written to planes `dst`.
-// Shared memory holds two square regions around the tile, each stored colour by colour (all
-// red pixels row by row, then all black ones) so that a half-sweep reads and writes
-// consecutive words: R1, halo K + 1, with U and the increment (du, dv) per pixel, and R0,
-// halo K, with the systems (a11, a12), (a22, b1), (b2, psiS).  The half-sweeps cover the tile
-// with a halo of K - 1 (the pixels whose neighbours all carry weights) as horizontal pixel
-// pairs, one pixel of each colour, with a fixed pair-to-thread assignment.
-constexpr int kOuterThreads = 448;  // 1250 swept pairs at K = 10: 3 per thread (2.8 on average)
+__global__ void __launch_bounds__(256) refine_apply_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
+                                                           int src)
+{
+    DIS_PIX_LOOP(pix_base)
+    float2 U = J.U[k];
+    U.x += J.rs[(long long)src * J.plane + o];
+    U.y += J.rs[(long long)(src + 1) * J.plane + o];
+    J.U[k] = U;
+    DIS_PIX_END
+}
+
+// ---------------------------------------------------------------- fused pass kernel
+constexpr int kTile = kRefineTile;
+
+// Shared-memory geometry of a launch of K half-sweeps with C channels.  Regions are squares
+// around the 32x32 tile with a margin: R0 (the systems, margin K), R1 (U and the increment,
+// margin K + 1), B (I_x, I_y, margin K + 1) and A (Ibar, I_z, margin K + 2, rows padded so that
+// each starts on a 16-byte boundary of the image row: OX columns before the region, WA floats per
+// row).  R0 and R1 are stored colour by colour (all red pixels row by row, then all black ones),
+// so that a half-sweep touches consecutive words; R1 reuses the space of A and B once the
+// systems exist.  With three channels R0 has a fourth plane for the energies and the weights
+// between the two passes over the channels.
+template <int K, int C>
+struct PassGeom {
+    static constexpr int S0 = kTile + 2 * K;
+    static constexpr int S1 = kTile + 2 * (K + 1);
+    static constexpr int SB = S1;
+    static constexpr int SA = kTile + 2 * (K + 2);
+    static constexpr int OX = ((K + 2 + 3) / 4) * 4 - (K + 2);
+    static constexpr int WA = ((OX + SA + 3) / 4) * 4;
+    static constexpr int R0P = C == 1 ? 3 : 4;
+    static constexpr size_t bytes_r0 = sizeof(float2) * R0P * S0 * S0;
+    static constexpr size_t bytes_ab = sizeof(float) * 2 * ((size_t)WA * SA + (size_t)SB * SB);
+    static constexpr size_t bytes_r1 = sizeof(float4) * S1 * S1;
+    static constexpr size_t bytes = bytes_r0 + (bytes_ab > bytes_r1 ? bytes_ab : bytes_r1);
+    // threads per block and resident blocks per SM: three blocks of 256 threads in 74 KB at
+    // K <= 5 (gray), two of 448 threads in 113 KB at K = 10
+    static constexpr int threads = K <= 5 ? 256 : 448;
+    static constexpr int min_blocks = (K <= 5 && C == 1) ? 3 : 2;
+};
 
 // Index of local pixel (lx, ly) in a colour-split square region of even side S whose origin
 // has colour parity p.
@@ -293,80 +388,164 @@ __device__ __forceinline__ int csplit(int lx, int ly, int S, int p)
     return ((lx + ly + p) & 1) * (S * S / 2) + ly * (S / 2) + (lx >> 1);
 }
 
-// PHASE 0: the whole pass (weights, K half-sweeps).  PHASE 1 / 2: the first / a later chunk of
-// a pass split into launches of K half-sweeps each, which narrows the halo to K: the first
-// computes the weights and also stores the tile's systems (rs_sys planes) for the later ones,
-// which load them with their halo instead of recomputing them from an increment they no longer
-// have.  j0: index of the chunk's first half-sweep in the pass (its colour parity).
-template <int K, int PHASE>
-__global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __grid_constant__ Jobs<LevelJob> js,
-                                                                        long long total_tiles, int src, int dst,
-                                                                        int j0, float delta, float gamma,
-                                                                        float alpha, float omega, int dof)
+// PHASE 0: the whole pass (systems, K = 2 theta_vi half-sweeps).  PHASE 1 / 2: the first / second
+// half of a pass split into two launches of K = theta_vi half-sweeps (half the halo).  Planes:
+// `start` holds the increment at the pass start (-1: zero, the first pass), which fixes the
+// lagged weights; PHASE 2 continues the sweeps from the first half's increment in `cur`; the
+// tile's increment goes to `dst`.  j0: index of the launch's first half-sweep within the pass
+// (its colour parity).
+template <int K, int PHASE, int C>
+__global__ void __launch_bounds__(PassGeom<K, C>::threads, PassGeom<K, C>::min_blocks)
+    refine_pass_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total_tiles, int start, int cur, int dst,
+                       int j0, float delta, float gamma, float alpha, float omega, int dof)
 {
+    using G = PassGeom<K, C>;
+    constexpr int NT = G::threads;
+    constexpr int S0 = G::S0, S1 = G::S1, SB = G::SB, SA = G::SA, WA = G::WA;
+    constexpr int HS0 = S0 / 2, HE0 = S0 * S0 / 2, HS1 = S1 / 2, HE1 = S1 * S1 / 2;
+    constexpr int E0 = S0 * S0;
     extern __shared__ float4 sm4[];
-    constexpr int T = kRefineTile;
-    constexpr int H = K;                 // halo of the systems
-    constexpr int S1 = T + 2 * (H + 1);  // side of R1
-    constexpr int S0 = T + 2 * H;        // side of R0
-    constexpr int S2 = T + 2 * (H - 1);  // side of the swept region (even)
-    constexpr int E1 = S1 * S1, E0 = S0 * S0;
-    constexpr int npairs = S2 * S2 / 2, pairs_row = S2 / 2;
-    constexpr int HS1 = S1 / 2, HE1 = E1 / 2, HS0 = S0 / 2, HE0 = E0 / 2;  // half rows / halves
-    float4* r1 = sm4;                                       // (U.x, U.y, du, dv)
-    float2* r0 = reinterpret_cast<float2*>(sm4 + E1);       // 3 planes of E0 float2
+    float2* r0 = reinterpret_cast<float2*>(sm4);  // planes: (a11, a12) (a22, b1) (b2, psiS) [(EI, EG) or psi]
+    float* Ab = reinterpret_cast<float*>(reinterpret_cast<char*>(sm4) + G::bytes_r0);
+    float* Az = Ab + WA * SA;
+    float* Bx = Az + WA * SA;
+    float* By = Bx + SB * SB;
+    float4* r1 = reinterpret_cast<float4*>(Ab);  // (U.x, U.y, du, dv), after the systems
     for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const LevelJob& J = job_ref(js, find_job(js, tile, &LevelJob::tile_base));
         const long long tk = tile - J.tile_base;
         const int ty = (int)(tk / J.tiles_x), tx = (int)(tk - (long long)ty * J.tiles_x);
-        const int w = J.w, h = J.h, pitch = J.pitch, C = J.C;
+        const int w = J.w, h = J.h, pitch = J.pitch;
         const long long pl = J.plane;
         const float* rs = J.rs;
-        const float2* Ug = J.U;
-        const int x1 = tx * T - (H + 1), y1 = ty * T - (H + 1);  // origin of R1
-        const int p1 = (x1 + y1) & 1;                            // colour parity of R1's origin (= R0's)
-        const float* gdu = rs + (long long)src * pl;
-        const float* gdv = gdu + pl;
-        // U and the increments on R1 (zero outside the image, never used there)
-#pragma unroll 2
-        for (int t = threadIdx.x; t < E1; t += kOuterThreads) {
+        const int bx0 = tx * kTile, by0 = ty * kTile;               // tile origin
+        const int xa = bx0 - (K + 2) - G::OX, ya = by0 - (K + 2);  // region A (xa: multiple of 4)
+        const int x1 = bx0 - (K + 1), y1 = by0 - (K + 1);          // regions B and R1
+        const int x0 = bx0 - K, y0 = by0 - K;                      // region R0
+        const int p1 = (x1 + y1) & 1;                              // colour parity of R1's and R0's origins
+        const float* gds = start >= 0 ? rs + (long long)start * pl : nullptr;
+        // A loads as float4 rows when it lies inside the image and the planes are 16-byte aligned
+        const bool vec = xa >= 0 && ya >= 0 && xa + WA <= w && ya + SA <= h && (pitch & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(rs) | (uintptr_t)(pl * 4)) & 15) == 0;
+        // ---- lagged systems on R0, channel by channel (three channels: energies first, then
+        // the systems, as in refine_data_system)
+        for (int sweep_c = 0; sweep_c < (C == 1 ? 1 : 2); ++sweep_c) {
+            for (int c = 0; c < C; ++c) {
+                const float* Pb = rs + (long long)rp_bar(C, c) * pl;
+                const float* Pz = rs + (long long)rp_iz(C, c) * pl;
+                if (vec) {
+                    constexpr int Q4 = WA / 4;
+                    for (int t = threadIdx.x; t < 2 * SA * Q4; t += NT) {
+                        const int z = t >= SA * Q4;
+                        const int tt = t - z * SA * Q4;
+                        const int ly = tt / Q4, q = tt - ly * Q4;
+                        const float4 v =
+                            __ldg(reinterpret_cast<const float4*>((z ? Pz : Pb) + (long long)(ya + ly) * pitch + xa) + q);
+                        reinterpret_cast<float4*>(z ? Az : Ab)[ly * Q4 + q] = v;
+                    }
+                } else {
+                    for (int t = threadIdx.x; t < 2 * SA * WA; t += NT) {
+                        const int z = t >= SA * WA;
+                        const int tt = t - z * SA * WA;
+                        const int ly = tt / WA, lx = tt - ly * WA;
+                        const long long o =
+                            (long long)clampi(ya + ly, 0, h - 1) * pitch + clampi(xa + lx, 0, w - 1);
+                        (z ? Az : Ab)[tt] = __ldg((z ? Pz : Pb) + o);
+                    }
+                }
+                __syncthreads();
+                // I_x, I_y on B, each at the clamped position (so that B holds the replicated
+                // border of the first derivatives)
+                for (int t = threadIdx.x; t < SB * SB; t += NT) {
+                    const int ly = t / SB, lx = t - ly * SB;
+                    const int ax = clampi(x1 + lx, 0, w - 1) - xa, ay = clampi(y1 + ly, 0, h - 1) - ya;
+                    const float* p = Ab + (ay - 1) * WA + ax - 1;
+                    const float v[9] = {p[0], p[1], p[2], p[WA], p[WA + 1], p[WA + 2], p[2 * WA], p[2 * WA + 1],
+                                        p[2 * WA + 2]};
+                    Bx[t] = sobel_x9(v);
+                    By[t] = sobel_y9(v);
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < E0; t += NT) {
+                    const int ly = t / S0, lx = t - ly * S0;
+                    const int x = x0 + lx, y = y0 + ly;
+                    if (x < 0 || x >= w || y < 0 || y >= h) continue;
+                    const float* bx = Bx + ly * SB + lx;  // (x - 1, y - 1) in B
+                    const float* by = By + ly * SB + lx;
+                    const float* az = Az + (ly + 1) * WA + lx + 1 + G::OX;
+                    const float ix[9] = {bx[0], bx[1], bx[2], bx[SB], bx[SB + 1], bx[SB + 2], bx[2 * SB],
+                                         bx[2 * SB + 1], bx[2 * SB + 2]};
+                    const float iy[9] = {by[0], by[1], by[2], by[SB], by[SB + 1], by[SB + 2], by[2 * SB],
+                                         by[2 * SB + 1], by[2 * SB + 2]};
+                    const float iz[9] = {az[0], az[1], az[2], az[WA], az[WA + 1], az[WA + 2], az[2 * WA],
+                                         az[2 * WA + 1], az[2 * WA + 2]};
+                    float d[9];
+                    refine_dvals(ix, iy, iz, d);
+                    float du = 0.0f, dv = 0.0f;
+                    if (gds) {
+                        const long long o = (long long)y * pitch + x;
+                        du = gds[o];
+                        dv = gds[pl + o];
+                    }
+                    const int ci = csplit(lx, ly, S0, p1);
+                    if constexpr (C == 1) {
+                        float EI = 0.0f, EG = 0.0f, psiI, psiG;
+                        refine_energy_acc(d, du, dv, EI, EG);
+                        refine_psi(EI, EG, delta, gamma, psiI, psiG);
+                        float a11 = 0.0f, a12 = 0.0f, a22 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+                        refine_system_acc(d, psiI, psiG, a11, a12, a22, b1, b2);
+                        r0[ci] = make_float2(a11, a12);
+                        r0[E0 + ci] = make_float2(a22, b1);
+                        r0[2 * E0 + ci].x = b2;
+                    } else if (sweep_c == 0) {
+                        float2 e = c == 0 ? make_float2(0.0f, 0.0f) : r0[3 * E0 + ci];
+                        refine_energy_acc(d, du, dv, e.x, e.y);
+                        r0[3 * E0 + ci] = e;
+                    } else {
+                        const float2 e = r0[3 * E0 + ci];
+                        float psiI, psiG;
+                        refine_psi(e.x, e.y, delta, gamma, psiI, psiG);
+                        float2 s01 = make_float2(0.0f, 0.0f), s23 = s01;
+                        float s4 = 0.0f;
+                        if (c > 0) {
+                            s01 = r0[ci];
+                            s23 = r0[E0 + ci];
+                            s4 = r0[2 * E0 + ci].x;
+                        }
+                        refine_system_acc(d, psiI, psiG, s01.x, s01.y, s23.x, s23.y, s4);
+                        r0[ci] = s01;
+                        r0[E0 + ci] = s23;
+                        r0[2 * E0 + ci].x = s4;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // ---- U and the increment at the pass start on R1 (zero outside the image, never used
+        // there), then the smoothness weights on R0
+        const float* gcur = PHASE == 2 ? rs + (long long)cur * pl : gds;
+        for (int t = threadIdx.x; t < S1 * S1; t += NT) {
             const int ly = t / S1, lx = t - ly * S1;
             const int x = x1 + lx, y = y1 + ly;
             float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (x >= 0 && x < w && y >= 0 && y < h) {
-                const float2 U = Ug[(long long)y * w + x];
-                const long long o = (long long)y * pitch + x;
-                v = make_float4(U.x, U.y, gdu[o], gdv[o]);
+                const float2 U = J.U[(long long)y * w + x];
+                v.x = U.x;
+                v.y = U.y;
+                if (gds) {
+                    const long long o = (long long)y * pitch + x;
+                    v.z = gds[o];
+                    v.w = gds[pl + o];
+                }
             }
             r1[csplit(lx, ly, S1, p1)] = v;
         }
         __syncthreads();
-        // lagged weights on R0 (origin x1 + 1, y1 + 1: the same colour parity as R1).  In a
-        // colour-split region a pixel (lx, ly) of colour c sits at c * half + ly * S/2 + lx/2;
-        // its left / right neighbours (the other colour) at the same position minus 1 when lx
-        // is even, plus 1 when lx is odd, and its upper / lower ones one half row away.
-        float* gsys = J.rs + (long long)rs_sys(C, 0) * pl;
-        if constexpr (PHASE == 2) {
-            // the stored systems of the pass's first chunk, with their halo (loads batched)
-#pragma unroll 4
-            for (int t = threadIdx.x; t < E0; t += kOuterThreads) {
-                const int ly = t / S0, lx = t - ly * S0;
-                const int x = x1 + 1 + lx, y = y1 + 1 + ly;
-                if (x < 0 || x >= w || y < 0 || y >= h) continue;
-                const int c0 = ((x + y) & 1) * HE0 + ly * HS0 + (lx >> 1);
-                const long long o = (long long)y * pitch + x;
-                r0[c0] = make_float2(gsys[o], gsys[pl + o]);
-                r0[E0 + c0] = make_float2(gsys[2 * pl + o], gsys[3 * pl + o]);
-                r0[2 * E0 + c0] = make_float2(gsys[4 * pl + o], gsys[5 * pl + o]);
-            }
-        }
-        for (int t = threadIdx.x; PHASE != 2 && t < E0; t += kOuterThreads) {
+        for (int t = threadIdx.x; t < E0; t += NT) {
             const int ly = t / S0, lx = t - ly * S0;
-            const int x = x1 + 1 + lx, y = y1 + 1 + ly;
+            const int x = x0 + lx, y = y0 + ly;
             if (x < 0 || x >= w || y < 0 || y >= h) continue;
             const int c = (x + y) & 1;
-            const int c0 = c * HE0 + ly * HS0 + (lx >> 1);
-            const long long o = (long long)y * pitch + x;
             const int pos = (ly + 1) * HS1 + ((lx + 1) >> 1), oth = (1 - c) * HE1 + pos;
             const int odd = (lx + 1) & 1;
             const float4 me = r1[c * HE1 + pos];
@@ -375,47 +554,51 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
             const float4 R = x < w - 1 ? r1[oth + odd] : me;
             const float4 Up = y > 0 ? r1[oth - HS1] : me;
             const float4 Dn = y < h - 1 ? r1[oth + HS1] : me;
-            float a11, a12, a22, b1, b2;
-            refine_data_system(rs, C, pl, o, me.z, me.w, delta, gamma, a11, a12, a22, b1, b2);
             const float ux = refine_cdiff(R.x, R.z, L.x, L.z);
             const float vx = refine_cdiff(R.y, R.w, L.y, L.w);
             const float uy = refine_cdiff(Dn.x, Dn.z, Up.x, Up.z);
             const float vy = refine_cdiff(Dn.y, Dn.w, Up.y, Up.w);
-            const float psS = refine_smooth_weight(ux, uy, vx, vy, alpha);
-            r0[c0] = make_float2(a11, a12);
-            r0[E0 + c0] = make_float2(a22, b1);
-            r0[2 * E0 + c0] = make_float2(b2, psS);
-            if (PHASE == 1 && lx >= H && lx < H + T && ly >= H && ly < H + T) {
-                // the tile's own systems, for the second half of the pass
-                gsys[o] = a11;
-                gsys[pl + o] = a12;
-                gsys[2 * pl + o] = a22;
-                gsys[3 * pl + o] = b1;
-                gsys[4 * pl + o] = b2;
-                gsys[5 * pl + o] = psS;
+            r0[2 * E0 + c * HE0 + ly * HS0 + (lx >> 1)].y = refine_smooth_weight(ux, uy, vx, vy, alpha);
+        }
+        if constexpr (PHASE == 2) {
+            // the sweeps continue from the first half's increment
+            __syncthreads();
+            for (int t = threadIdx.x; t < S1 * S1; t += NT) {
+                const int ly = t / S1, lx = t - ly * S1;
+                const int x = x1 + lx, y = y1 + ly;
+                if (x < 0 || x >= w || y < 0 || y >= h) continue;
+                const long long o = (long long)y * pitch + x;
+                float4& v = r1[csplit(lx, ly, S1, p1)];
+                v.z = gcur[o];
+                v.w = gcur[pl + o];
             }
         }
         __syncthreads();
-        // K half-sweeps, red ((x + y) even) first.  Pair pr = (ly, k) covers swept pixels
-        // (2k, ly) and (2k + 1, ly); the one of the current colour is lx = 2k + first.
-        const int x2 = x1 + 2, y2 = y1 + 2;  // origin of the swept region
+        // ---- K half-sweeps, red ((x + y) even) first.  Half-sweep j covers the square of margin
+        // m = K - 1 - j around the tile; pair pr = (ly, k) of that square covers pixels (2k, ly)
+        // and (2k + 1, ly), of which the one of the current colour is updated.
         const bool interior = x1 >= 0 && y1 >= 0 && x1 + S1 <= w && y1 + S1 <= h;
         auto sweep = [&](auto inner_tag) {
             constexpr bool INNER = decltype(inner_tag)::value;  // no image border in R1
+#pragma unroll 1
             for (int j = 0; j < K; ++j) {
-                const int colour = (j + j0) & 1;  // later chunks continue the pass's alternation
-                for (int pr = threadIdx.x; pr < npairs; pr += kOuterThreads) {
-                    const int ly = pr / pairs_row, k = pr - ly * pairs_row;
-                    const int y = y2 + ly;
-                    const int first = ((x2 + y) & 1) == colour ? 0 : 1;
-                    const int x = x2 + 2 * k + first;
+                const int colour = (j + j0) & 1;  // the second half of a pass continues the alternation
+                const int m = K - 1 - j, side = kTile + 2 * m, prow = side / 2;
+                const int xo = bx0 - m, yo = by0 - m;
+                const int off = K + 1 - m;  // R1 position of the square's origin
+                for (int pr = threadIdx.x; pr < side * prow; pr += NT) {
+                    const int ly = pr / prow, k = pr - ly * prow;
+                    const int y = yo + ly;
+                    const int first = ((xo + y) & 1) ^ colour;
+                    const int x = xo + 2 * k + first;
                     if (!INNER && (x < 0 || x >= w || y < 0 || y >= h)) continue;
-                    // R1 position (2k + first + 2, ly + 2), R0 position (2k + first + 1, ly + 1)
-                    const int pos1 = (ly + 2) * HS1 + k + 1, pos0 = (ly + 1) * HS0 + k + first;
+                    const int lx1 = off + 2 * k + first, ly1 = off + ly;
+                    const int pos1 = ly1 * HS1 + (lx1 >> 1), pos0 = (ly1 - 1) * HS0 + ((lx1 - 1) >> 1);
+                    const int odd1 = lx1 & 1, odd0 = 1 - odd1;
                     const int i1 = colour * HE1 + pos1, o1 = (1 - colour) * HE1 + pos1;
                     const int i0 = colour * HE0 + pos0, o0 = (1 - colour) * HE0 + pos0;
-                    const int n1[4] = {o1 - 1 + first, o1 + first, o1 - HS1, o1 + HS1};
-                    const int n0[4] = {o0 - first, o0 + 1 - first, o0 - HS0, o0 + HS0};
+                    const int n1[4] = {o1 - 1 + odd1, o1 + odd1, o1 - HS1, o1 + HS1};
+                    const int n0[4] = {o0 - 1 + odd0, o0 + odd0, o0 - HS0, o0 + HS0};
                     const bool in[4] = {INNER || x > 0, INNER || x < w - 1, INNER || y > 0, INNER || y < h - 1};
                     float psq[4], duq[4], dvq[4];
                     float2 Uq[4];
@@ -443,14 +626,14 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
             sweep(std::true_type{});
         else
             sweep(std::false_type{});
-        // the tile's increments to the other buffer
+        // the tile's increments to `dst`
         float* odu = J.rs + (long long)dst * pl;
         float* odv = odu + pl;
-        for (int t = threadIdx.x; t < T * T; t += kOuterThreads) {
-            const int ly = t / T, lx = t - ly * T;
-            const int x = tx * T + lx, y = ty * T + ly;
+        for (int t = threadIdx.x; t < kTile * kTile; t += NT) {
+            const int ly = t / kTile, lx = t - ly * kTile;
+            const int x = bx0 + lx, y = by0 + ly;
             if (x >= w || y >= h) continue;
-            const float4 v = r1[csplit(lx + H + 1, ly + H + 1, S1, p1)];
+            const float4 v = r1[csplit(lx + K + 1, ly + K + 1, S1, p1)];
             const long long o = (long long)y * pitch + x;
             odu[o] = v.z;
             odv[o] = v.w;
@@ -459,61 +642,75 @@ __global__ void __launch_bounds__(kOuterThreads, 2) refine_outer_kernel(const __
     }
 }
 
-__global__ void __launch_bounds__(256) refine_apply_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
-                                                           int src)
+template <int K, int PHASE, int C>
+static cudaError_t pass_launch(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int start,
+                               int cur, int dst, int j0, const LaunchCfg& lc, cudaStream_t s)
 {
-    DIS_PIX_LOOP(pix_base)
-    float2 U = J.U[k];
-    U.x += J.rs[(long long)src * J.plane + o];
-    U.y += J.rs[(long long)(src + 1) * J.plane + o];
-    J.U[k] = U;
-    DIS_PIX_END
-}
-
-template <int K, int PHASE>
-static cudaError_t outer_launch(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int src, int dst,
-                                int j0, const LaunchCfg& lc, cudaStream_t s)
-{
-    constexpr int S1 = kRefineTile + 2 * (K + 1), S0 = kRefineTile + 2 * K;
-    constexpr size_t smem = sizeof(float4) * (size_t)S1 * S1 + sizeof(float2) * 3 * (size_t)S0 * S0;
+    using G = PassGeom<K, C>;
+    constexpr size_t smem = G::bytes;
     static int occ = 0;
     if (occ == 0) {
         cudaError_t e =
-            cudaFuncSetAttribute(refine_outer_kernel<K, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(refine_pass_kernel<K, PHASE, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, refine_outer_kernel<K, PHASE>, kOuterThreads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, refine_pass_kernel<K, PHASE, C>, G::threads, smem) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
     }
     const int gt = (int)std::min<long long>(total_tiles, (long long)lc.sm_count * occ);
-    refine_outer_kernel<K, PHASE><<<gt, kOuterThreads, smem, s>>>(js, total_tiles, src, dst, j0, a.delta, a.gamma,
-                                                                   a.alpha, a.omega, a.dof);
+    refine_pass_kernel<K, PHASE, C><<<gt, G::threads, smem, s>>>(js, total_tiles, start, cur, dst, j0, a.delta,
+                                                                 a.gamma, a.alpha, a.omega, a.dof);
     return cudaGetLastError();
 }
 
-// a.outer fused passes of KT half-sweeps, each in one launch (KC == KT) or in KT / KC launches
-// of KC; on return `src` names the planes holding the final increment.
-template <int KT, int KC>
-static cudaError_t launch_outer(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int& src,
-                                int& dst, const LaunchCfg& lc, cudaStream_t s)
+// a.outer fused passes of KT half-sweeps, each in one launch (KC == KT) or in two launches of
+// KC = KT / 2.  Increment planes: X = rs_du, Y = the fifth and sixth intermediate planes of
+// channel 0, Z = the first two system planes (all free in this form).  One launch per pass
+// alternates between X and Y; a split pass writes its first half to X and its result to the one
+// of Y, Z that does not hold its start.  Returns the plane of the final increment (-1: none,
+// a.outer == 0).
+template <int KT, int KC, int C>
+static cudaError_t launch_passes(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int& fin,
+                                 const LaunchCfg& lc, cudaStream_t s)
 {
-    static_assert(KT % KC == 0, "chunks divide the pass");
+    static_assert(KT == KC || KT == 2 * KC, "a pass runs in one or two launches");
+    const int X = rs_du(C, 0), Y = rs_mid(C, 0, 4), Z = rs_sys(C, 0);
+    int start = -1;
     for (int ot = 0; ot < a.outer; ++ot) {
-        cudaError_t e = cudaSuccess;
+        cudaError_t e;
+        int dst;
         if constexpr (KC == KT) {
-            e = outer_launch<KT, 0>(js, total_tiles, a, src, dst, 0, lc, s);
-            std::swap(src, dst);
+            dst = start == X ? Y : X;
+            e = pass_launch<KC, 0, C>(js, total_tiles, a, start, -1, dst, 0, lc, s);
         } else {
-            for (int j0 = 0; j0 < KT && e == cudaSuccess; j0 += KC) {
-                e = j0 == 0 ? outer_launch<KC, 1>(js, total_tiles, a, src, dst, j0, lc, s)
-                            : outer_launch<KC, 2>(js, total_tiles, a, src, dst, j0, lc, s);
-                std::swap(src, dst);
-            }
+            dst = start == Y ? Z : Y;
+            e = pass_launch<KC, 1, C>(js, total_tiles, a, start, -1, X, 0, lc, s);
+            if (e == cudaSuccess) e = pass_launch<KC, 2, C>(js, total_tiles, a, start, X, dst, KC, lc, s);
         }
         if (e != cudaSuccess) return e;
+        start = dst;
     }
+    fin = start;
     return cudaSuccess;
+}
+
+template <int C>
+static cudaError_t launch_fused(const Jobs<LevelJob>& js, long long total_tiles, const RefineArgs& a, int chunks,
+                                int& fin, const LaunchCfg& lc, cudaStream_t s)
+{
+    switch (a.inner * 10 + chunks) {
+        case 11: return launch_passes<2, 2, C>(js, total_tiles, a, fin, lc, s);
+        case 12: return launch_passes<2, 1, C>(js, total_tiles, a, fin, lc, s);
+        case 21: return launch_passes<4, 4, C>(js, total_tiles, a, fin, lc, s);
+        case 22: return launch_passes<4, 2, C>(js, total_tiles, a, fin, lc, s);
+        case 31: return launch_passes<6, 6, C>(js, total_tiles, a, fin, lc, s);
+        case 32: return launch_passes<6, 3, C>(js, total_tiles, a, fin, lc, s);
+        case 41: return launch_passes<8, 8, C>(js, total_tiles, a, fin, lc, s);
+        case 42: return launch_passes<8, 4, C>(js, total_tiles, a, fin, lc, s);
+        case 51: return launch_passes<10, 10, C>(js, total_tiles, a, fin, lc, s);
+        default: return launch_passes<10, 5, C>(js, total_tiles, a, fin, lc, s);
+    }
 }
 
 cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, long long total_tiles,
@@ -523,18 +720,16 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
     const long long cap = (long long)lc.sm_count * lc.max_blocks_256;
     const int gp = (int)std::min<long long>((total_pix + 255) / 256, cap);
     const int gh = (int)std::min<long long>((total_half + 255) / 256, cap);
-    refine_warp_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    refine_deriv1_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    refine_deriv2_kernel<<<gp, 256, 0, s>>>(js, total_pix);
-    // the increment starts in rs_du (zeroed by the warp kernel); the fused passes alternate it
-    // with the first two intermediate planes, which are free once deriv2 has run
-    const int du_plane = rs_du(a.C, 0), mid_plane = rs_mid(a.C, 0, 0);
-    // The fused form recomputes the halo: about 2.4x the swept pixels at 10 half-sweeps in one
-    // launch, 1.6x when the pass is split in two launches of 5 (which also stores and reloads
-    // the systems).  Measured on GB300 the single launch wins up to about 128 K pixels per
-    // launch, the split pass above (and both beat the per-sweep kernels); mode 2 / 3 force one.
+    // The fused form recomputes the halo: at 10 half-sweeps in one launch a block forms the
+    // systems of 2.6x the tile's pixels and sweeps 1.5x on average; a pass split into two
+    // launches of 5 forms them twice on 1.7x and sweeps 1.2x, at three blocks per SM instead of
+    // two.  mode 1 takes one launch up to kRefineFusedMaxPixels per launch, two above; mode 2 / 3
+    // force one; mode 0 (and passes of more than five sweeps) run the per-sweep kernels.
     const bool fused = a.fused != 0 && a.inner > 0 && a.inner <= kRefineMaxFusedInner && total_tiles > 0;
+    refine_prep_kernel<<<gp, 256, 0, s>>>(js, total_pix, fused ? 0 : 1);
     if (!fused) {
+        refine_grad_kernel<<<gp, 256, 0, s>>>(js, total_pix);
+        refine_data_kernel<<<gp, 256, 0, s>>>(js, total_pix);
         for (int ot = 0; ot < a.outer; ++ot) {
             refine_weights_kernel<<<gp, 256, 0, s>>>(js, total_pix, a.delta, a.gamma, a.alpha);
             for (int it = 0; it < a.inner; ++it) {
@@ -542,29 +737,15 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
                 refine_sor_kernel<<<gh, 256, 0, s>>>(js, total_half, 1, a.omega, a.dof);
             }
         }
-        refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, du_plane);
+        refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, rs_du(a.C, 0));
         return cudaGetLastError();
     }
-    // chunks per pass: 1 (mode 2, or small launches in mode 1) or 2 (mode 3, or large launches in
-    // mode 1).  (Chunks of one full sweep, halo 2, measured slower than both: each reloads the
-    // systems.)
     const int chunks = (a.fused == 3 || (a.fused == 1 && total_pix > kRefineFusedMaxPixels)) ? 2 : 1;
-    int src = du_plane, dst = mid_plane;
-    cudaError_t e = cudaSuccess;
-    switch (a.inner * 10 + chunks) {
-        case 11: e = launch_outer<2, 2>(js, total_tiles, a, src, dst, lc, s); break;
-        case 12: e = launch_outer<2, 1>(js, total_tiles, a, src, dst, lc, s); break;
-        case 21: e = launch_outer<4, 4>(js, total_tiles, a, src, dst, lc, s); break;
-        case 22: e = launch_outer<4, 2>(js, total_tiles, a, src, dst, lc, s); break;
-        case 31: e = launch_outer<6, 6>(js, total_tiles, a, src, dst, lc, s); break;
-        case 32: e = launch_outer<6, 3>(js, total_tiles, a, src, dst, lc, s); break;
-        case 41: e = launch_outer<8, 8>(js, total_tiles, a, src, dst, lc, s); break;
-        case 42: e = launch_outer<8, 4>(js, total_tiles, a, src, dst, lc, s); break;
-        case 51: e = launch_outer<10, 10>(js, total_tiles, a, src, dst, lc, s); break;
-        default: e = launch_outer<10, 5>(js, total_tiles, a, src, dst, lc, s); break;
-    }
+    int fin = -1;
+    cudaError_t e = a.C == 1 ? launch_fused<1>(js, total_tiles, a, chunks, fin, lc, s)
+                             : launch_fused<3>(js, total_tiles, a, chunks, fin, lc, s);
     if (e != cudaSuccess) return e;
-    refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, src);
+    if (fin >= 0) refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, fin);
     return cudaGetLastError();
 }
 
