@@ -220,12 +220,20 @@ dis_status dis_trace_batched(dis_handle* h, const dis_pair* pairs, int n, const 
 /* Refinement launch form (not in the paper) for handle h.  A fused launch runs lagged-weight
  * passes with their SOR sweeps on shared-memory tiles whose halo is as wide as the half-sweeps
  * it runs (up to 5 sweeps per pass; more always use per-sweep launches).  fused = 1 (the
- * default) runs each pass in one fused launch up to 128 Ki pixels per launch (all pairs of a
- * level together) and in two fused launches of half the sweeps (half the halo) above, which
- * measures fastest on GB300; 2 always uses one launch per pass, 3 always two, 0 one launch per
- * half-sweep (no halo, no shared memory).  All forms give the same result bit for bit.  Other
- * values: DIS_ERR_INVALID_ARG. */
+ * default) runs each pass in one fused launch, except that launches of more pixels than the
+ * handle's split threshold (dis_set_refine_split; default: none, which measures fastest on
+ * GB300 for the dense 1024x436 workload) run each pass as two fused launches of half the sweeps
+ * (half the halo); 2 always uses one launch per pass, 3 always two, 0 one launch per
+ * half-sweep plus thread-per-pixel derivative kernels (no halo, no shared memory).  All forms
+ * give the same result bit for bit.  Other values: DIS_ERR_INVALID_ARG. */
 dis_status dis_set_refine_fusion(dis_handle* h, int fused);
+
+/* Split threshold of refinement form 1 (not in the paper): a level whose pixels over all pairs
+ * of the call exceed `pixels` runs each pass in two fused launches; pixels < 0: never split (the
+ * default).  dis_autotune sets it.  dis_get_refine_split reports it (-1: never).  Calls with
+ * different thresholds use different cached graphs. */
+dis_status dis_set_refine_split(dis_handle* h, int64_t pixels);
+dis_status dis_get_refine_split(const dis_handle* h, int64_t* pixels);
 
 /* Work scheduling (not in the paper) for handle h.  on = 1 (the default): the grouped search
  * kernels hand out patches, and the forward-backward densification its tiles, from a work queue
@@ -249,8 +257,9 @@ dis_status dis_probe_ms(dis_handle* h, float* ms);
 /* Autotuner (not in the paper): time the inverse-search variants the library offers for this
  * workload on the caller's pairs (the batched call, 4 runs per variant, synchronising
  * `stream`) and keep the fastest in the handle for later calls with the same patch size; then,
- * when p->refine is set, time the refinement launch forms of dis_set_refine_fusion (1, 0, 2, 3)
- * with that search and keep the fastest.  The runs write the pairs' flow_out.  *chosen_lanes
+ * when p->refine is set, time the refinement launch forms of dis_set_refine_fusion (0, 2, 3, and
+ * 1 with a split threshold between every two level sizes of the call) with that search and keep
+ * the fastest form and threshold.  The runs write the pairs' flow_out.  *chosen_lanes
  * (nullable) receives the chosen search variant code (dis_get_tuning reports both choices):
  *   4, 8, 16, 32   grouped: that many lanes share one patch (every group runs its own updates
  *                  and rebuilds its cell sums alone);

@@ -236,6 +236,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
     for (size_t i = 0; i < sizeof(dis_params) / 4; ++i) plan.key.push_back(pw[i]);
     plan.key.push_back(hd->search_lanes[p.patch_size]);
     plan.key.push_back(hd->refine_fused);
+    plan.key.push_back(hd->refine_split_px);
     plan.key.push_back(hd->probe_kind);
     plan.key.push_back(hd->lc.wq != nullptr);
     plan.key.push_back(hd->probe_level);
@@ -526,6 +527,7 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
                     a.alpha = p.alpha;
                     a.omega = p.sor_omega;
                     a.fused = hd->refine_fused;
+                    a.split_px = hd->refine_split_px;
                     a.C = p.channels;
                     a.dof = p.dof;
                     e = traced(DIS_LAUNCH_REFINE, ph.s,
@@ -995,6 +997,20 @@ dis_status dis_set_refine_fusion(dis_handle* hd, int fused)
     return DIS_OK;
 }
 
+dis_status dis_set_refine_split(dis_handle* hd, int64_t pixels)
+{
+    if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
+    hd->refine_split_px = pixels < 0 ? dis::kRefineSplitNever : std::min<long long>(pixels, dis::kRefineSplitNever);
+    return DIS_OK;
+}
+
+dis_status dis_get_refine_split(const dis_handle* hd, int64_t* pixels)
+{
+    if (!hd || !pixels) return fail(const_cast<dis_handle*>(hd), DIS_ERR_INVALID_ARG, "dis_get_refine_split: NULL argument");
+    *pixels = hd->refine_split_px >= dis::kRefineSplitNever ? -1 : hd->refine_split_px;
+    return DIS_OK;
+}
+
 dis_status dis_set_work_queue(dis_handle* hd, int on)
 {
     if (!hd) return fail(nullptr, DIS_ERR_INVALID_ARG, "handle is NULL");
@@ -1249,7 +1265,7 @@ dis_status dis_refine_level_ex(dis_handle* hd, const float* I0, const float* I1,
     J.rs = reinterpret_cast<float*>(hd->arena + hd->off_rs);
     long long tiles = 0;
     dis::set_refine_tiles(J, tiles);
-    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega, hd->refine_fused, channels, dof};
+    dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega, hd->refine_fused, hd->refine_split_px, channels, dof};
     const long long tp = (long long)w * h, th = (long long)h * ((w + 1) / 2);
     cudaError_t e = dis::launch_refine(dis::single_job(J), tp, th, tiles, a, hd->lc, (cudaStream_t)stream);
     return e == cudaSuccess ? DIS_OK : cuda_fail(hd, e, "dis_refine_level");
@@ -1340,23 +1356,51 @@ extern "C" dis_status dis_autotune(dis_handle* hd, const dis_pair* pairs, int n,
             best = opts[k];
         }
     }
-    // then the refinement launch form (per-sweep, fused where faster, fused everywhere)
+    // then the refinement launch form: per-sweep launches, or fused passes split into two
+    // launches above a threshold, tried at every gap between the pixel counts of the levels
+    // (all pairs of a level together) and at "never" / "always" (forms 2 and 3)
+    const long long keep_split = hd->refine_split_px;
+    long long best_split = keep_split;
     if (st == DIS_OK && p->refine) {
         hd->search_lanes[ps] = best;
         best_ms = 1e30f;
-        const int modes[4] = {1, 0, 2, 3};
-        for (int k = 0; k < 4 && st == DIS_OK; ++k) {
-            hd->refine_fused = modes[k];
+        std::vector<long long> level_px;
+        {
+            std::vector<PairIn> v;
+            int ss_max = 0;
+            for (int i = 0; i < n; ++i) {
+                int ss = 0, sf = 0;
+                std::string e;
+                if (resolve_levels(pairs[i].width, pairs[i].height, *p, ss, sf, e) == DIS_OK) ss_max = std::max(ss_max, ss);
+            }
+            for (int s = 0; s <= ss_max; ++s) {
+                long long px = 0;
+                for (int i = 0; i < n; ++i) px += (long long)level_dim(pairs[i].width, s) * level_dim(pairs[i].height, s);
+                level_px.push_back(px * (p->fb ? 2 : 1));
+            }
+        }
+        std::vector<std::pair<int, long long>> cand = {{0, keep_split}, {2, keep_split}, {3, keep_split}};
+        for (long long px : level_px) cand.push_back({1, px});  // split the levels larger than this one
+        for (size_t k = 0; k < cand.size() && st == DIS_OK; ++k) {
+            hd->refine_fused = cand[k].first;
+            hd->refine_split_px = cand[k].second;
             float tot = 0.0f;
             st = time_calls(tot);
             if (st == DIS_OK && tot < best_ms) {
                 best_ms = tot;
-                best_refine = modes[k];
+                best_refine = cand[k].first;
+                best_split = cand[k].second;
             }
+        }
+        // form 1 with a threshold at the largest level is form 2: report it as form 1
+        if (best_refine == 2) {
+            best_refine = 1;
+            best_split = dis::kRefineSplitNever;
         }
     }
     hd->search_lanes[ps] = (st == DIS_OK) ? best : keep;
     hd->refine_fused = (st == DIS_OK) ? best_refine : keep_refine;
+    hd->refine_split_px = (st == DIS_OK) ? best_split : keep_split;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (chosen_lanes) *chosen_lanes = hd->search_lanes[ps];

@@ -37,6 +37,7 @@ struct dis_handle {
     bool use_graphs = true;
     int search_lanes[17] = {};  // autotuned lanes per patch by patch size (0 = default)
     int refine_fused = 1;       // refinement launch form (dis_set_refine_fusion)
+    long long refine_split_px = dis::kRefineSplitNever;  // form 1's split threshold (dis_set_refine_split)
     int last_kernels = -1;      // kernels of the graph the most recent call replayed (-1: none)
     unsigned int* wq = nullptr;  // the search work queue in the arena (lc.wq while enabled)
     // probe: events recorded around one launch group in every call (also inside graphs)

@@ -112,9 +112,12 @@ inline Jobs<J> device_jobs(const J* dev, int n)
 }
 
 // Refinement scratch plane indices (per channel c: intermediate, data; then shared planes).
-// Intermediate (6 C): I1w, Ix, Iy, Iz, Ixz, Iyz.  Data (9 C): sqrt(b0)(Ix, Iy, Iz),
-// sqrt(bx)(Ixx, Ixy, Ixz), sqrt(by)(Ixy, Iyy, Iyz).  System (6): A11 A12 A22 b1 b2 psiS.
-// Increment (2): du, dv.
+// Intermediate (6 C): the mean image (I0 + I1w)/2, I_z = I1w - I0, I_x, I_y (the last two in the
+// per-sweep form only), two free planes (an increment of the fused form, channel 0).  Data
+// (9 C, per-sweep form): sqrt(b0)(Ix, Iy, Iz), sqrt(bx)(Ixx, Ixy, Ixz), sqrt(by)(Ixy, Iyy, Iyz).
+// System (6, per-sweep form; the fused form keeps an increment in the first two): A11 A12 A22
+// b1 b2 psiS.  Increment (2): du, dv.  (The FP64 differentiable form indexes its own scratch with
+// these functions, its six intermediate planes holding I1w, I_x, I_y, I_z, I_xz, I_yz.)
 __host__ __device__ inline int rs_mid(int C, int c, int k) { return c * 6 + k; }
 __host__ __device__ inline int rs_dat(int C, int c, int k) { return 6 * C + c * 9 + k; }
 __host__ __device__ inline int rs_sys(int C, int k) { return 15 * C + k; }
@@ -171,12 +174,14 @@ long long fb_scratch_ints(int w, int h, int ps, int stride);
 // (tile_base, tiles_x), `tiles` in all, and the tiled form runs where the stride allows it.
 cudaError_t launch_densify(const Jobs<LevelJob>& js, long long total, long long tiles, int ps, int stride,
                            const LaunchCfg& lc, cudaStream_t s);
+constexpr long long kRefineSplitNever = 1LL << 62;
 struct RefineArgs {
     int outer, inner;
     float delta, gamma, alpha, omega;
     int fused = 1;      // 0: per-sweep launches; 1: each pass in one fused launch up to
-                        // kRefineFusedMaxPixels per launch, in two above; 2: one fused launch,
+                        // split_px pixels per launch, in two above; 2: one fused launch,
                         // 3: two fused launches per pass, whenever inner allows
+    long long split_px = kRefineSplitNever;  // form 1's threshold
     int C = 1;          // channels of every job of the launch
     int dof = 2;        // 1: stereo, the vertical increment stays 0
 };
@@ -184,7 +189,6 @@ struct RefineArgs {
 // (2 half-sweeps each) run in one launch, the halo being as wide as the half-sweeps.
 constexpr int kRefineTile = 32;
 constexpr int kRefineMaxFusedInner = 5;
-constexpr long long kRefineFusedMaxPixels = 1LL << 17;  // larger launches split each pass in two
 inline long long refine_tiles(int w, int h)
 {
     return (long long)((w + kRefineTile - 1) / kRefineTile) * ((h + kRefineTile - 1) / kRefineTile);

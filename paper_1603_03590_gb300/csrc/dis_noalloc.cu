@@ -87,7 +87,7 @@ extern "C" dis_status dis_refine_level_noalloc(const float* I0, const float* I1,
     long long tiles = 0;
     dis::set_refine_tiles(J, tiles);
     dis::RefineArgs a{outer, inner, delta, gamma, alpha, omega};
-    a.fused = 1;  // launch form 1: one fused launch per outer pass, two above kRefineFusedMaxPixels
+    a.fused = 1;  // launch form 1 with its default threshold: one fused launch per outer pass
     a.C = channels;
     e = dis::launch_refine(dis::single_job(J), (long long)w * h, (long long)h * ((w + 1) / 2), tiles, a,
                            dis::stage_launch_cfg(), (cudaStream_t)stream);

@@ -79,9 +79,11 @@ __device__ __forceinline__ void refine_dvals(const float (&ix)[9], const float (
     const float Ixx = sobel_x9(ix), Ixy = sobel_y9(ix), Iyy = sobel_y9(iy);
     const float Ixz = sobel_x9(iz), Iyz = sobel_y9(iz);
     const float Ix = ix[4], Iy = iy[4], Iz = iz[4];
-    const float s0 = 1.0f / sqrtf(fmaf(Ix, Ix, fmaf(Iy, Iy, 0.01f)));
-    const float sx = 1.0f / sqrtf(fmaf(Ixx, Ixx, fmaf(Ixy, Ixy, 0.01f)));
-    const float sy = 1.0f / sqrtf(fmaf(Ixy, Ixy, fmaf(Iyy, Iyy, 0.01f)));
+    // sqrt(beta) by the hardware reciprocal square root (2 ulp): the normalisers only scale the
+    // rows of the data terms
+    const float s0 = rsqrtf(fmaf(Ix, Ix, fmaf(Iy, Iy, 0.01f)));
+    const float sx = rsqrtf(fmaf(Ixx, Ixx, fmaf(Ixy, Ixy, 0.01f)));
+    const float sy = rsqrtf(fmaf(Ixy, Ixy, fmaf(Iyy, Iyy, 0.01f)));
     d[0] = s0 * Ix;
     d[1] = s0 * Iy;
     d[2] = s0 * Iz;
@@ -103,12 +105,13 @@ __device__ __forceinline__ void refine_energy_acc(const float (&d)[9], float du,
     EG = fmaf(eX, eX, fmaf(eY, eY, EG));
 }
 
-// Lagged weights psi = weight * Psi'(E) of the two data terms.
+// Lagged weights psi = weight * Psi'(E) = weight / (2 sqrt(E + eps^2)) of the two data terms
+// (hardware reciprocal square root, 2 ulp).
 __device__ __forceinline__ void refine_psi(float EI, float EG, float delta, float gamma, float& psiI, float& psiG)
 {
     const float eps2 = 1.0e-6f;
-    psiI = delta / (2.0f * sqrtf(EI + eps2));
-    psiG = gamma / (2.0f * sqrtf(EG + eps2));
+    psiI = (0.5f * delta) * rsqrtf(EI + eps2);
+    psiG = (0.5f * gamma) * rsqrtf(EG + eps2);
 }
 
 // One channel's share of the 2x2 data system A dU = b with the weights psi frozen.
@@ -128,8 +131,8 @@ __device__ __forceinline__ void refine_system_acc(const float (&d)[9], float psi
 // Smoothness weight alpha * Psi'(|grad(u + du)|^2) from the four central differences.
 __device__ __forceinline__ float refine_smooth_weight(float ux, float uy, float vx, float vy, float alpha)
 {
-    const float ES = ux * ux + uy * uy + vx * vx + vy * vy;
-    return alpha / (2.0f * sqrtf(ES + 1.0e-6f));
+    const float ES = fmaf(ux, ux, fmaf(uy, uy, fmaf(vx, vx, __fmul_rn(vy, vy))));
+    return (0.5f * alpha) * rsqrtf(ES + 1.0e-6f);
 }
 
 // Central difference 0.5 * ((U_r + dU_r) - (U_l + dU_l)) of one component.
@@ -157,7 +160,7 @@ __device__ __forceinline__ void refine_sor_update(float a11, float a12, float a2
             r1 = fmaf(wq, (Uq[q].x + duq[q]) - Up.x, r1);
         }
         const float m11 = a11 + sw;
-        if (m11 > 0.0f) du = (1.0f - omega) * du + omega * (r1 * __frcp_rn(m11));
+        if (m11 > 0.0f) du = (1.0f - omega) * du + omega * __fdividef(r1, m11);
         return;
     }
     float sw = 0.0f, r1 = b1, r2 = b2;
@@ -172,7 +175,7 @@ __device__ __forceinline__ void refine_sor_update(float a11, float a12, float a2
     const float m11 = a11 + sw, m12 = a12, m22 = a22 + sw;
     const float det = m11 * m22 - m12 * m12;
     if (det > 0.0f) {
-        const float id = __frcp_rn(det);  // the correctly rounded 1 / det
+        const float id = __fdividef(1.0f, det);  // hardware reciprocal (det < 2^126: the weights are bounded)
         const float d1 = (m22 * r1 - m12 * r2) * id;
         const float d2 = (m11 * r2 - m12 * r1) * id;
         du = (1.0f - omega) * du + omega * d1;
@@ -580,8 +583,8 @@ __global__ void __launch_bounds__(PassGeom<K, C>::threads, PassGeom<K, C>::min_b
         const bool interior = x1 >= 0 && y1 >= 0 && x1 + S1 <= w && y1 + S1 <= h;
         auto sweep = [&](auto inner_tag) {
             constexpr bool INNER = decltype(inner_tag)::value;  // no image border in R1
-#pragma unroll 1
-            for (int j = 0; j < K; ++j) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {  // unrolled: the square's side is a constant
                 const int colour = (j + j0) & 1;  // the second half of a pass continues the alternation
                 const int m = K - 1 - j, side = kTile + 2 * m, prow = side / 2;
                 const int xo = bx0 - m, yo = by0 - m;
@@ -723,7 +726,7 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
     // The fused form recomputes the halo: at 10 half-sweeps in one launch a block forms the
     // systems of 2.6x the tile's pixels and sweeps 1.5x on average; a pass split into two
     // launches of 5 forms them twice on 1.7x and sweeps 1.2x, at three blocks per SM instead of
-    // two.  mode 1 takes one launch up to kRefineFusedMaxPixels per launch, two above; mode 2 / 3
+    // two.  mode 1 takes one launch up to a.split_px pixels per launch, two above; mode 2 / 3
     // force one; mode 0 (and passes of more than five sweeps) run the per-sweep kernels.
     const bool fused = a.fused != 0 && a.inner > 0 && a.inner <= kRefineMaxFusedInner && total_tiles > 0;
     refine_prep_kernel<<<gp, 256, 0, s>>>(js, total_pix, fused ? 0 : 1);
@@ -740,7 +743,7 @@ cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long lo
         refine_apply_kernel<<<gp, 256, 0, s>>>(js, total_pix, rs_du(a.C, 0));
         return cudaGetLastError();
     }
-    const int chunks = (a.fused == 3 || (a.fused == 1 && total_pix > kRefineFusedMaxPixels)) ? 2 : 1;
+    const int chunks = (a.fused == 3 || (a.fused == 1 && total_pix > a.split_px)) ? 2 : 1;
     int fin = -1;
     cudaError_t e = a.C == 1 ? launch_fused<1>(js, total_tiles, a, chunks, fin, lc, s)
                              : launch_fused<3>(js, total_tiles, a, chunks, fin, lc, s);

@@ -86,6 +86,8 @@ _SIGS = {
     "dis_search_variants": (_i, [_i, ctypes.POINTER(_i), _i]),
     "dis_get_tuning": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "dis_last_call_kernels": (_i, [_vp, ctypes.POINTER(_i)]),
+    "dis_set_refine_split": (_i, [_vp, _i64]),
+    "dis_get_refine_split": (_i, [_vp, ctypes.POINTER(_i64)]),
     "dis_set_probe": (_i, [_vp, _i, _i]),
     "dis_set_refine_fusion": (_i, [_vp, _i]),
     "dis_set_work_queue": (_i, [_vp, _i]),
@@ -271,6 +273,18 @@ def dis_get_tuning(handle, patch_size):
     v, r = _i(), _i()
     _check(_lib.dis_get_tuning(handle, patch_size, ctypes.byref(v), ctypes.byref(r)), handle)
     return v.value, r.value
+
+
+def dis_set_refine_split(handle, pixels):
+    """Refinement form 1 splits passes of launches above `pixels` (< 0: never)."""
+    _check(_lib.dis_set_refine_split(handle, pixels), handle)
+
+
+def dis_get_refine_split(handle):
+    """Split threshold of refinement form 1 (-1: never split)."""
+    v = _i64()
+    _check(_lib.dis_get_refine_split(handle, ctypes.byref(v)), handle)
+    return v.value
 
 
 def dis_last_call_kernels(handle):

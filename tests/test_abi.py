@@ -128,6 +128,9 @@ def test_trace_and_probe_argument_checks_need_no_gpu(dis):
     assert lib.dis_set_probe(None, 3, 0) == dis.DIS_ERR_INVALID_ARG
     assert lib.dis_set_refine_fusion(None, 1) == dis.DIS_ERR_INVALID_ARG
     assert lib.dis_set_work_queue(None, 1) == dis.DIS_ERR_INVALID_ARG
+    assert lib.dis_set_refine_split(None, ctypes.c_int64(1)) == dis.DIS_ERR_INVALID_ARG
+    assert lib.dis_get_refine_split(None, None) == dis.DIS_ERR_INVALID_ARG
+    assert lib.dis_last_call_kernels(None, None) == dis.DIS_ERR_INVALID_ARG
     assert lib.dis_get_tuning(None, 8, None, None) == dis.DIS_ERR_INVALID_ARG
     assert lib.dis_probe_ms(None, None) == dis.DIS_ERR_INVALID_ARG
     assert lib.dis_trace_batched(None, None, 1, None, None, None, 0, None) == dis.DIS_ERR_INVALID_ARG

@@ -11,7 +11,7 @@ map is not smooth at the scale of that step everywhere: the robust weights Psi'(
 1 / (2 sqrt(a^2 + eps^2)), eps = 0.001, bend sharply where residuals are near eps, and bilinear
 cells and the max(1, |d|) branch give kinks.  A coordinate is therefore compared only when its
 central difference has converged at step h (halving the step changes it by less than 0.3 of
-the tolerance) and no discrete decision (the oracle's decision trace) flips within h/2 of the
+the tolerance) and no discrete decision (the oracle's decision trace) flips within h of the
 point; the others are counted and reported.
 """
 import multiprocessing as mp
@@ -51,9 +51,11 @@ def fd_compare(I0, I1, rec, init, kw, grads, seed, want, max_draw, split=(0.4, 0
     differences of the oracle's frozen map at seeded coordinates of I0, I1 and the initial flow
     (in the proportions `split`), drawn in rounds until `want` of them are comparable (at most
     `max_draw` drawn).  A coordinate is comparable when no decision of the oracle's trace flips
-    within h/2 of it and its central difference has converged at step h (halving the step
-    changes it by less than 0.3 of the tolerance).  Returns (errors, drawn, flips, unconverged);
-    errors are (relative error, kind, index, analytic, FD)."""
+    within h of it (all four stencil points take the centre's decisions: a boundary between h/2
+    and h would bend the step-h difference alone) and its central difference has converged at
+    step h (halving the step changes it by less than 0.3 of the tolerance).  Returns (errors,
+    drawn, flips, unconverged); errors are (relative error, kind, index, analytic, FD at h, FD at
+    h/2)."""
     rng = np.random.default_rng(seed)
     steps = (H_STEP, -H_STEP, 0.5 * H_STEP, -0.5 * H_STEP)
     sizes = {"I0": I0.size, "I1": I1.size, "init": init.size}
@@ -71,9 +73,9 @@ def fd_compare(I0, I1, rec, init, kw, grads, seed, want, max_draw, split=(0.4, 0
             res = pool.map(_fd_task, [(k, i, st) for k, i in coords for st in steps], chunksize=4)
             for c, (k, i) in enumerate(coords):
                 (lp, hp), (lm, hm), (lp2, hp2), (lm2, hm2) = res[4 * c:4 * c + 4]
-                # a decision boundary within h/2 of the point makes every central difference
-                # return the mean of the two one-sided slopes, whatever the step: not comparable
-                if hp2 != h0 or hm2 != h0:
+                # a decision boundary within h of the point bends the central differences
+                # towards the mean of the two one-sided slopes: not comparable
+                if hp != h0 or hm != h0 or hp2 != h0 or hm2 != h0:
                     flips += 1
                     continue
                 fd = (lp - lm) / (2 * H_STEP)
@@ -84,9 +86,9 @@ def fd_compare(I0, I1, rec, init, kw, grads, seed, want, max_draw, split=(0.4, 0
                     unconverged += 1
                     continue
                 an = grads[k].reshape(-1)[i]
-                errs.append((abs(an - fd) / max(abs(fd), 1e-12), k, i, an, fd))
+                errs.append((abs(an - fd) / max(abs(fd), 1e-12), k, i, an, fd, fd2))
     errs.sort(reverse=True)
-    print("%s vs FD (step %g): %d coordinates compared of %d drawn; excluded: %d with a decision flip within h/2, "
+    print("%s vs FD (step %g): %d coordinates compared of %d drawn; excluded: %d with a decision flip within h, "
           "%d whose FD has not converged at that step; worst: %s"
           % (label, H_STEP, len(errs), drawn, flips, unconverged, errs[:5]))
     return errs, drawn, flips, unconverged

@@ -15,7 +15,8 @@ import pytest
 
 import oracle
 from paper_1603_03590_gb300 import synth
-from test_gpu_parity import (STAGE_TOL, check_e2e, gpu_level_images, host, oracle_e2e, oracle_params, to_dev)
+from test_gpu_parity import (STAGE_TOL, check_e2e, gpu_level_images, host, oracle_e2e, oracle_e2e_many, oracle_params,
+                             to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -148,14 +149,16 @@ def test_e2e_fb(env, name, preset, kw):
     assert np.array_equal(got_f, host(f2))
     q = oracle_params(p)
     q.fb = 1
-    # The medium preset at 320x240 is ill-conditioned: under two 1e-4 perturbations of I1 the FP64
-    # oracle's own flow moves by more than 0.01 px at 2.0 % of this pair's pixels without the
-    # consistency and at 4.2 % with it (the merged fields take in the other direction's outlier
-    # patches too); those pixels are not determined at FP32 resolution.  The determined ones are
-    # held to the usual bar.
-    cap = 0.06 if preset == "medium" else 0.03
-    check_e2e(name + " forward", got_f, oracle_e2e(I0, I1, q), gt, max_unstable=cap)
-    check_e2e(name + " backward", got_b, oracle_e2e(I1, I0, q), max_unstable=cap)
+    # The medium preset at 320x240 is ill-conditioned: under the perturbations of I1 of
+    # test_gpu_parity.oracle_e2e the FP64 oracle's own flow moves by more than the stability
+    # tolerance at several per cent of this pair's pixels, more with the consistency than
+    # without it (the merged fields take in the other direction's outlier patches too); those
+    # pixels are not determined at FP32 resolution, and four perturbations instead of two find
+    # them.  The determined ones are held to the usual bar.
+    cap, reps = (0.06, 4) if preset == "medium" else (0.03, 2)
+    fwd, bwd = oracle_e2e_many([(I0, I1, q, {}), (I1, I0, q, {})], reps)
+    check_e2e(name + " forward", got_f, fwd, gt, max_unstable=cap)
+    check_e2e(name + " backward", got_b, bwd, max_unstable=cap)
     plain_q = oracle_params(p)
     plain_q.fb = 0
     assert np.abs(oracle.dis_flow(I0, I1, plain_q) - oracle.dis_flow(I0, I1, q)).max() > 1e-3

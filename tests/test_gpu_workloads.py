@@ -26,7 +26,7 @@ import pytest
 
 import oracle
 from paper_1603_03590_gb300 import synth
-from test_gpu_parity import STAGE_TOL, check_e2e, host, ndimage_smooth, oracle_params
+from test_gpu_parity import STAGE_TOL, check_e2e, host, ndimage_smooth, oracle_e2e_many, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -51,32 +51,9 @@ def _gen(args):
     return synth.workload_pair(name, i)
 
 
-def _oracle_flow(args):
-    """One FP64 oracle run (in a spawned process): I1 perturbed by 1e-4 on the 0..255 scale
-    when `seed` is given (the perturbation of test_gpu_parity.oracle_e2e)."""
-    I0, I1, kw, seed = args
-    if seed is not None:
-        I1 = I1.astype(np.float64) + np.random.default_rng(seed).standard_normal(I1.shape) * (1e-4 / 255.0)
-    return oracle.dis_flow(I0, I1, oracle.params(**kw))
-
-
 def oracle_e2e_parallel(cases):
-    """(flow, spread) of test_gpu_parity.oracle_e2e for every (I0, I1, oracle keyword
-    parameters) case, all oracle runs side by side in spawned processes."""
-    tasks = [(I0, I1, kw, seed) for I0, I1, kw in cases for seed in (None, 1, 2)]
-    with mp.get_context("spawn").Pool(min(len(tasks), os.cpu_count() or 1)) as pool:
-        res = pool.map(_oracle_flow, tasks, chunksize=1)
-    out = []
-    for c in range(len(cases)):
-        ref, f1, f2 = res[3 * c:3 * c + 3]
-        out.append((ref, np.maximum(np.abs(f1 - ref).max(-1), np.abs(f2 - ref).max(-1))))
-    return out
-
-
-def oracle_kw(p):
-    """oracle_params(p) as plain keyword values (picklable for the worker processes)."""
-    q = oracle_params(p)
-    return {name: getattr(q, name) for name, _ in q._fields_}
+    """(flow, spread) of test_gpu_parity.oracle_e2e for every (I0, I1, oracle params) case."""
+    return oracle_e2e_many([(I0, I1, q, {}) for I0, I1, q in cases])
 
 
 def generate(name, n):
@@ -120,7 +97,7 @@ def test_mixed_batch_of_64_pairs(env):
         ks = [k for k, (a, _, _) in enumerate(pairs) if a.shape == shp]
         picked += ks[:3] if shp == (240, 320) else ks[:1]
     assert {pairs[k][0].shape for k in picked} == set(synth_shapes()), "the seeded draw holds every resolution"
-    refs = oracle_e2e_parallel([(pairs[k][0], pairs[k][1], oracle_kw(p)) for k in picked])
+    refs = oracle_e2e_parallel([(pairs[k][0], pairs[k][1], oracle_params(p)) for k in picked])
     for k, rs in zip(picked, refs):
         I0, I1, gt = pairs[k]
         check_e2e("mixed pair %d (%dx%d, medium)" % (k, I0.shape[1], I0.shape[0]), batched[k], rs, gt)
@@ -164,7 +141,7 @@ def test_rgb_4k_batch_of_4(env):
     assert np.array_equal(plain0, runs[0][0])
     # pair 0 end to end against the oracle
     I0, I1, gt = pairs[0]
-    (ref,) = oracle_e2e_parallel([(I0, I1, oracle_kw(p))])
+    (ref,) = oracle_e2e_parallel([(I0, I1, oracle_params(p))])
     check_e2e("rgb 3840x2160 pair 0 (dense, 7 levels)", runs[0][0], ref, gt)
 
     # the finest level's refinement alone, on the full frame, against the oracle on crops

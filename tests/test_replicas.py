@@ -163,3 +163,18 @@ def test_bench_defaults_keep_the_timing_rules(monkeypatch):
     bench.main()
     assert seen["warmup"] == 3
 
+
+
+def test_bench_parity_block_uses_the_tests_determination():
+    """The bench's parity block classifies pixels as the end-to-end parity tests do."""
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    import test_gpu_parity
+    assert (bench.PERTURB, bench.STABLE_TOL) == (test_gpu_parity.PERTURB, test_gpu_parity.STABLE_TOL)
+    ref = np.zeros((4, 5, 2))
+    got = ref + 1e-3
+    spread = np.zeros((4, 5))
+    spread[0, 0] = 1.0  # one pixel not determined
+    st = bench.parity_stats(got, ref, spread, ref)
+    assert st["stable_frac"] == 19 / 20 and abs(st["stable_mean_abs_du"] - 1e-3) < 1e-15
