@@ -16,6 +16,7 @@
 // which the (atomically listed) patches arrive, so the result is deterministic.  Only 32-bit
 // conversions run per term (64-bit ones would run on the slow FP64 pipe).
 #include <algorithm>
+#include <climits>
 
 #include "dis_device.cuh"
 
@@ -53,7 +54,7 @@ __device__ __forceinline__ void own_sums(const LevelJob& J, int x, int y, int ps
             const int i = ii > ihi ? nx - 1 : ii;
             const float2 up = J.pu[(long long)j * nx + i];
             const float d = sample_shift(J.S1, w, h, pitch, x, y, up.x, up.y) - i0;
-            const float wt = __frcp_rn(fmaxf(1.0f, fabsf(d)));  // the correctly rounded 1 / max(1, |d|)
+            const float wt = __fdividef(1.0f, fmaxf(1.0f, fabsf(d)));  // 1 / max(1, |d|), hardware reciprocal
             nu = fmaf(wt, up.x, nu);
             nv = fmaf(wt, up.y, nv);
             Z += wt;
@@ -86,9 +87,11 @@ __global__ void __launch_bounds__(256) densify_kernel(const __grid_constant__ Jo
 // of the job's 32 x 32 refinement tiles), a thread per pixel.  Every pixel of a patch samples I1
 // with the patch's displacement, so the parts of the bilinear sample that depend on the patch
 // alone (the clamped displacement's floor and fraction) and the patch flow are staged once per
-// band for all patches that cover it, instead of once per (pixel, patch).  Each pixel then runs
-// the loop of own_sums over the staged patches in the same row-major order with the same
-// operations: the result equals densify_kernel's bit for bit.  Covering patches per band and
+// band for all patches that cover it, instead of once per (pixel, patch); so is, for a patch whose
+// four taps stay inside the frame at every pixel of the band, the offset of its taps from the
+// pixel (then no pixel clamps them).  Each pixel then runs the loop of own_sums over the staged
+// patches in the same row-major order with the same operations on the same samples: the result
+// equals densify_kernel's bit for bit.  Covering patches per band and
 // axis: at most (30 + ps) / stride + 1 regular ones and the last one, so at most 17 for
 // ps <= 16 and stride >= 3.
 constexpr int kDensTile = kRefineTile;
@@ -100,6 +103,7 @@ constexpr int kDensThreads = kDensTile * kDensRows;
 struct DensPatch {
     float ax, ay, u, v;  // fraction of the clamped displacement, patch flow
 };
+constexpr int kOutside = INT_MIN;  // a staged patch whose taps leave the frame somewhere in the band
 
 template <int SC>
 __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid_constant__ Jobs<LevelJob> js,
@@ -109,6 +113,7 @@ __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid
     static_assert(SC >= 3, "the staged table holds kDensAxis patches per axis");
     __shared__ DensPatch tab[kDensAxis * kDensAxis];
     __shared__ int2 cell[kDensAxis * kDensAxis];  // integer part of the clamped displacement
+    __shared__ int offs[kDensAxis * kDensAxis];   // tap offset from the pixel, or kOutside
     for (long long g = blockIdx.x; g < bands; g += gridDim.x) {
         const long long t = g / kDensBands;
         const LevelJob& J = job_ref(js, find_job(js, t, &LevelJob::tile_base));
@@ -136,7 +141,11 @@ __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid
             const float vc = fminf(fmaxf(up.y, -1.0e7f), 1.0e7f);
             const float fu = floorf(uc), fv = floorf(vc);
             tab[q] = DensPatch{uc - fu, vc - fv, up.x, up.y};
-            cell[q] = make_int2((int)fu, (int)fv);
+            const int cx = (int)fu, cy = (int)fv;
+            cell[q] = make_int2(cx, cy);
+            // every pixel of the band samples rows y + cy, y + cy + 1 and columns x + cx, x + cx + 1
+            const bool inside = tx0 + cx >= 0 && tx1 + cx + 1 <= w - 1 && ty0 + cy >= 0 && ty1 + cy + 1 <= h - 1;
+            offs[q] = inside ? cy * pitch + cx : kOutside;  // |cy| < h: no overflow when inside
         }
         __syncthreads();
         const int x = tx0 + (int)(threadIdx.x % kDensTile), y = ty0 + (int)(threadIdx.x / kDensTile);
@@ -146,6 +155,7 @@ __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid
             cover_range<SC>(x, w, ps, stride, nx, ilo, ihi, ilast);
             cover_range<SC>(y, h, ps, stride, ny, jlo, jhi, jlast);
             const float i0 = __ldg(J.S0 + (long long)y * pitch + x);
+            const float* s1px = J.S1 + (long long)y * pitch + x;
             float nu = 0.0f, nv = 0.0f, Z = 0.0f;
             const int jend = jhi + (jlast ? 1 : 0), iend = ihi + (ilast ? 1 : 0);
             for (int jj = jlo; jj <= jend; ++jj) {
@@ -153,16 +163,29 @@ __global__ void __launch_bounds__(kDensThreads) densify_tile_kernel(const __grid
                 for (int ii = ilo; ii <= iend; ++ii) {
                     const int q = row + (ii > ihi ? nreg_x : ii - ib);
                     const DensPatch P = tab[q];
-                    const int2 c = cell[q];
-                    const int xi = x + c.x, yi = y + c.y;
-                    const int x0 = clampi(xi, 0, w - 1), x1 = clampi(xi + 1, 0, w - 1);
-                    const int y0 = clampi(yi, 0, h - 1), y1 = clampi(yi + 1, 0, h - 1);
-                    const float* r0 = J.S1 + (long long)y0 * pitch;
-                    const float* r1 = J.S1 + (long long)y1 * pitch;
-                    const float pa = __ldg(r0 + x0), pb = __ldg(r0 + x1), pc = __ldg(r1 + x0), pd = __ldg(r1 + x1);
+                    const int off = offs[q];
+                    float pa, pb, pc, pd;
+                    if (off != kOutside) {
+                        const float* p = s1px + off;
+                        pa = __ldg(p);
+                        pb = __ldg(p + 1);
+                        pc = __ldg(p + pitch);
+                        pd = __ldg(p + pitch + 1);
+                    } else {
+                        const int2 c = cell[q];
+                        const int xi = x + c.x, yi = y + c.y;
+                        const int x0 = clampi(xi, 0, w - 1), x1 = clampi(xi + 1, 0, w - 1);
+                        const int y0 = clampi(yi, 0, h - 1), y1 = clampi(yi + 1, 0, h - 1);
+                        const float* r0 = J.S1 + (long long)y0 * pitch;
+                        const float* r1 = J.S1 + (long long)y1 * pitch;
+                        pa = __ldg(r0 + x0);
+                        pb = __ldg(r0 + x1);
+                        pc = __ldg(r1 + x0);
+                        pd = __ldg(r1 + x1);
+                    }
                     const float top = fmaf(P.ax, pb - pa, pa), bot = fmaf(P.ax, pd - pc, pc);
                     const float d = fmaf(P.ay, bot - top, top) - i0;
-                    const float wt = __frcp_rn(fmaxf(1.0f, fabsf(d)));  // as in own_sums
+                    const float wt = __fdividef(1.0f, fmaxf(1.0f, fabsf(d)));  // as in own_sums
                     nu = fmaf(wt, P.u, nu);
                     nv = fmaf(wt, P.v, nv);
                     Z += wt;
@@ -406,7 +429,7 @@ __global__ void __launch_bounds__(kFbThreads, 6) densify_fb_kernel(const __grid_
                     const float top = fmaf(ax, p01 - p00, p00), bot = fmaf(ax, p11 - p10, p10);
                     const float d = s0[a] - fmaf(ay, bot - top, top);
                     const float wt = footprint_1d(x - pc.x, u.x, ps) * footprint_1d(y - pc.y, u.y, ps) *
-                                     __frcp_rn(fmaxf(1.0f, fabsf(d)));
+                                     __fdividef(1.0f, fmaxf(1.0f, fabsf(d)));
                     acc[0][a] += __float2int_rn(wt * su);
                     acc[1][a] += __float2int_rn(wt * sv);
                     acc[2][a] += __float2int_rn(wt * sz);
