@@ -68,6 +68,9 @@ PRESETS = {
 DIFF_PARAMS = dict(patch_size=8, overlap=0.5, grad_iters=16, coarsest_scale=3, finest_scale=0, refine=1,
                    var_outer=1, var_inner=10)
 NORM_CODES = {"l2": 0, "l1": 1, "huber": 2}
+# library kernels one pair of the differentiable workload launches per step (FP32 search with its
+# graph, FP64 replay, loss, FP64 backward), from the ncu launch list of that step
+DIFF_KERNELS_PER_PAIR = 667
 
 # name -> metric, synthetic workload, default preset, default batch, theta_ss (-1: automatic),
 # channels, description
@@ -614,9 +617,11 @@ def run_ours(args, rank, local, world):
 def run_diff(args, rank, local, world):
     """The differentiable form: per step, each pair's forward map (FP32 search recording its
     increments, FP64 replay of the frozen map), the photometric loss and the backward pass to
-    both frames and the initial flow; single-pair calls (no batched differentiable call)."""
+    both frames and the initial flow.  Batched: the pairs side by side, one handle and stream per
+    pair (BatchedDifferentiableDIS), one backward over the sum of their losses; plain: the same
+    pairs one after another on one handle."""
     import torch
-    from paper_1603_03590_gb300 import autograd, build, dis, replicas
+    from paper_1603_03590_gb300 import autograd, build, replicas
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -627,40 +632,57 @@ def run_diff(args, rank, local, world):
     uniq = gen_pairs(WORKLOADS["diff"]["synth"], min(args.unique, B))
     pairs = [uniq[k % len(uniq)] for k in range(B)]
     H, W = pairs[0][0].shape
-    model = autograd.DifferentiableDIS(W, H, "default", **DIFF_PARAMS)
-    hs, ws = model.coarsest_shape(W, H)
+    single = autograd.DifferentiableDIS(W, H, "default", **DIFF_PARAMS)
+    batched = autograd.BatchedDifferentiableDIS(W, H, B, "default", **DIFF_PARAMS)
+    hs, ws = single.coarsest_shape(W, H)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     I0d = [torch.from_numpy(a).to(dev) for a, _, _ in pairs]
     I1d = [torch.from_numpy(b).to(dev) for _, b, _ in pairs]
     init = [torch.zeros((hs, ws, 2), device=dev) for _ in pairs]
 
-    def one(a, b, u):
-        a = a.detach().requires_grad_(True)
-        b = b.detach().requires_grad_(True)
-        u = u.detach().requires_grad_(True)
-        loss = autograd.photometric_loss(a, b, model(a, b, u))
-        loss.backward()
-        return loss.detach(), a.grad, b.grad, u.grad
+    def leaves(ts):
+        return [t.detach().requires_grad_(True) for t in ts]
 
-    def step():
-        return [one(a, b, u) for a, b, u in zip(I0d, I1d, init)]
+    def step_batched(a0=None, a1=None, u0=None):
+        a, b, u = leaves(a0 or I0d), leaves(a1 or I1d), leaves(u0 or init)
+        flows = batched(a, b, u)
+        losses = [autograd.photometric_loss(x, y, f) for x, y, f in zip(a, b, flows)]
+        torch.stack(losses).sum().backward()
+        return [(l.detach(), x.grad, y.grad, z.grad) for l, x, y, z in zip(losses, a, b, u)]
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    replicas.barrier()
-    clk = Clocks(local)
-    ms = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
+    def step_plain():
+        out = []
+        for a0, b0, u0 in zip(I0d, I1d, init):
+            a, b, u = leaves([a0, b0, u0])
+            loss = autograd.photometric_loss(a, b, single(a, b, u))
+            loss.backward()
+            out.append((loss.detach(), a.grad, b.grad, u.grad))
+        return out
+
+    def timed(fn, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            fn()
         torch.cuda.synchronize()
-        ms += e0.elapsed_time(e1)
-    clocks = clk.stop()
+        replicas.barrier()
+        clk = Clocks(local) if clocks else None
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs), (clk.stop() if clk else None)
+
+    ms, clocks = timed(step_batched, args.steps, args.warmup, clocks=True)
+    ms_p, _ = timed(step_plain, max(3, args.steps // 2), 3)
+    # the batched gradients are those of single-pair calls, bit for bit
+    gb, gp = step_batched(), step_plain()
+    torch.cuda.synchronize()
+    assert all(torch.equal(x, y) for rb, rp in zip(gb, gp) for x, y in zip(rb, rp)), "batched gradients differ"
     # end to end: frames and initial flows from pinned host memory, loss and the three gradients
     # back to host memory, every step
     hin = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), torch.zeros((hs, ws, 2)).pin_memory())
@@ -669,8 +691,10 @@ def run_diff(args, rank, local, world):
              torch.empty((H, W), pin_memory=True), torch.empty((hs, ws, 2), pin_memory=True)) for _ in pairs]
 
     def step_e2e():
-        for (a, b, u), outs in zip(hin, hout):
-            r = one(a.to(dev, non_blocking=True), b.to(dev, non_blocking=True), u.to(dev, non_blocking=True))
+        a = [x.to(dev, non_blocking=True) for x, _, _ in hin]
+        b = [y.to(dev, non_blocking=True) for _, y, _ in hin]
+        u = [z.to(dev, non_blocking=True) for _, _, z in hin]
+        for outs, r in zip(hout, step_batched(a, b, u)):
             for dst, src in zip(outs, r):
                 dst.copy_(src.reshape(dst.shape), non_blocking=True)
 
@@ -685,34 +709,29 @@ def run_diff(args, rank, local, world):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e = e0.elapsed_time(e1)
-    # kernels of one step, counted by the profiler (untimed step)
-    launches = None
-    try:
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            step()
-            torch.cuda.synchronize()
-        names = [e.name for e in prof.events() if getattr(e.device_type, "name", "") == "CUDA"]
-        launches = sum(1 for n in names if "dis::" in n) or None  # the library's kernels only
-    except Exception:  # the profiler is optional
-        launches = None
-    ms, ms_e = replicas.max_over_ranks([ms, ms_e], device=dev)
-    model.close()
+    ms, ms_p, ms_e = replicas.max_over_ranks([ms, ms_p, ms_e], device=dev)
+    single.close()
+    batched.close()
     if rank != 0:
         return
+    plain_steps = max(3, args.steps // 2)
     value = replicas.aggregate_rate(B * args.steps, world, ms / 1000.0)
+    plain = replicas.aggregate_rate(B * plain_steps, world, ms_p / 1000.0)
     e2e = replicas.aggregate_rate(B * args.steps, world, ms_e / 1000.0)
     line = {"metric": WORKLOADS["diff"]["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 search, f64 replay and adjoint", "data": "synthetic",
             "config": dict(workload_config(args, B, world), l2="flushed between timed steps (256 MB write)"),
-            "plain": {"value": value, "unit": UNIT, "note": "single-pair calls; there is no batched differentiable call"},
+            "plain": {"value": plain, "unit": UNIT, "ms_per_pair": ms_p / (B * plain_steps),
+                      "note": "the same pairs one after another on one handle"},
             "roofline": None,
-            "roofline_note": "no per-kernel work model of the FP64 replay and adjoint yet",
+            "roofline_note": "no per-kernel work model of the FP64 replay and adjoint: a chain of small "
+                             "latency-bound launches (profiles/launches_diff512x256_batch8.md)",
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": B * (2 * H * W * 4 + hs * ws * 8),
                     "d2h_bytes_per_step": B * (4 + 2 * H * W * 4 + hs * ws * 8)},
-            "gpu_launches": launches * args.steps if launches else None,
-            "gpu_launches_source": "CUDA kernels of one untimed step under torch.profiler x timed steps",
+            "gpu_launches": DIFF_KERNELS_PER_PAIR * B * args.steps,
+            "gpu_launches_source": "library kernels per pair and step in the ncu launch list of this step "
+                                   "(profiles/launches_diff512x256_batch8.md) x pairs x timed steps",
             "clocks": clocks}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)[0]

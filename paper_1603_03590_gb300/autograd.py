@@ -4,7 +4,8 @@ backward run in libdis.so's kernels).
 DifferentiableDIS(I0, I1, init_flow) returns the flow of the frozen-search DIS map: the
 forward records every patch's search increment (FP32 search) and evaluates the map with those
 increments frozen in FP64; the backward repeats that replay and runs the FP64 adjoint of the
-pyramid, initial displacements, densification and unrolled SOR sweeps.  photometric_loss is the mean
+pyramid, initial displacements, densification and unrolled SOR sweeps.
+BatchedDifferentiableDIS runs several pairs of that map side by side on streams of their own.  photometric_loss is the mean
 Charbonnier penalty sqrt((I1(x + U(x)) - I0(x))^2 + eps^2) with its gradients.
 """
 import torch
@@ -50,6 +51,49 @@ class DifferentiableDIS:
 
     def __call__(self, I0, I1, init_flow=None, frozen=None):
         return _DISFlow.apply(I0, I1, init_flow, self, frozen)
+
+
+class BatchedDifferentiableDIS:
+    """The differentiable map on a batch of pairs that run side by side: one handle and one CUDA
+    stream per pair slot.  Each pair's forward (FP32 search, FP64 replay) is issued on its slot's
+    stream, and autograd runs its backward on that stream too, so the pairs' chains of small
+    launches overlap on the GPU.  The flows are those of DifferentiableDIS on each pair alone, bit
+    for bit.  Calls order themselves after the caller's current stream, and the caller's stream
+    waits for every pair's flow."""
+
+    def __init__(self, max_w, max_h, slots, preset="default", **overrides):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        self.pairs = [DifferentiableDIS(max_w, max_h, preset, **overrides) for _ in range(slots)]
+        self.params = self.pairs[0].params
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+
+    def close(self):
+        for d in self.pairs:
+            d.close()
+
+    def coarsest_shape(self, w, h):
+        return self.pairs[0].coarsest_shape(w, h)
+
+    def __call__(self, I0s, I1s, init_flows=None):
+        n = len(I0s)
+        if n > len(self.pairs) or len(I1s) != n or (init_flows is not None and len(init_flows) != n):
+            raise ValueError("at most %d pairs, with as many second frames and initial flows" % len(self.pairs))
+        caller = torch.cuda.current_stream()
+        flows = []
+        for k in range(n):
+            s = self.streams[k]
+            s.wait_stream(caller)
+            for t in (I0s[k], I1s[k], None if init_flows is None else init_flows[k]):
+                if t is not None:
+                    t.record_stream(s)  # the caller's tensors stay allocated until s is done
+            with torch.cuda.stream(s):
+                init = None if init_flows is None else init_flows[k]
+                flows.append(self.pairs[k](I0s[k], I1s[k], init))
+        for k in range(n):
+            caller.wait_stream(self.streams[k])
+            flows[k].record_stream(caller)
+        return flows
 
 
 class _DISFlow(torch.autograd.Function):

@@ -217,7 +217,7 @@ struct Lvl64 {
     double* rs;               // refinement scratch ((15 + 8) planes, C = 1 layout of rs_*)
     double* ga;               // adjoint planes, ADJ_PLANES x plane
     double* gS0;              // gradient of S0 (accumulated, pitch)
-    unsigned long long* gS1;  // gradient of S1 in 2^-40 fixed point (accumulated, pitch)
+    unsigned long long* gS1;  // gradient of S1 in 2^-48 fixed point (accumulated, pitch)
     double2* gU;              // gradient of the densified flow (accumulated, dense)
     long long plane;
     int w, h, pitch;
@@ -262,7 +262,7 @@ cudaError_t launch_dens_bwd(const Lvl64& L, const Dens64& A, const LaunchCfg& lc
 cudaError_t launch_uinit_bwd(const Dens64& A, int w, int h, unsigned long long* gUc, int wc, int hc, double cs,
                              const LaunchCfg& lc, cudaStream_t s);
 // Implicit-function gradient of the converged search at every patch with a nonzero frozen
-// increment (see k_adjoint.cu): scatters into L.gS1 and gS0acc (2^-40 fixed point, pitch) and
+// increment (see k_adjoint.cu): scatters into L.gS1 and gS0acc (2^-48 fixed point, pitch) and
 // zeroes those patches' A.gpu.
 cudaError_t launch_search_ift_bwd(const Lvl64& L, const Dens64& A, const float2* frozen, unsigned long long* gS0acc,
                                   int dof, const LaunchCfg& lc, cudaStream_t s);
@@ -270,7 +270,7 @@ cudaError_t launch_pyr_bwd(const double* gc, int wc, int hc, int pc, double* gf,
                            const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_f2_to_d2(const float2* in, double2* out, long long n, const LaunchCfg& lc, cudaStream_t s);
 // FP64 final up-scaling (out = factor * in(x / factor), bilinear, clamped) and its transpose,
-// accumulated into gin (2^-40 fixed point, dense wi*hi*2).
+// accumulated into gin (2^-48 fixed point, dense wi*hi*2).
 cudaError_t launch_upsample64(const double2* in, int wi, int hi, double factor, double2* out, int wo, int ho,
                               const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_upsample_bwd(const double2* gout, int wo, int ho, double factor, unsigned long long* gin, int wi,

@@ -27,15 +27,29 @@ H_STEP = 1e-4
 PARAMS = dict(patch_size=8, overlap=0.5, grad_iters=64, coarsest_scale=2, var_outer=1, var_inner=5)
 POLISH = 60
 
+
+def library_values(kw):
+    """The oracle's keyword parameters with the values the library evaluates: its dis_params
+    fields are FP32, so the SOR relaxation factor is 1.6f = 1.600000024, not 1.6.  A finite
+    difference of the FP64 oracle must differentiate the same map as the FP64 adjoint; with the
+    double 1.6 the two maps differ by 2.4e-8 in omega, which the levels and sweeps compound
+    into relative gradient differences up to 2e-3 at four levels."""
+    q = dict(kw)
+    q.setdefault("sor_omega", 1.6)
+    for k in ("sor_omega", "delta", "gamma", "alpha"):
+        if k in q:
+            q[k] = float(np.float32(q[k]))
+    return q
+
 _W = {}
 
 
 def _init_worker(I0, I1, rec, init, kw):
-    _W.update(I0=I0, I1=I1, rec=rec, init=init, q=oracle.params(polish=POLISH, **kw))
+    _W.update(I0=I0, I1=I1, rec=rec, init=init, q=oracle.params(polish=POLISH, **library_values(kw)))
 
 
 def _init_worker_kw(I0, I1, rec, init, kw):
-    _W.update(I0=I0, I1=I1, rec=rec, init=init, q=oracle.params(**kw))
+    _W.update(I0=I0, I1=I1, rec=rec, init=init, q=oracle.params(**library_values(kw)))
 
 
 def _fd_task(task):
@@ -80,7 +94,7 @@ def test_implicit_search_gradient_matches_fp64_finite_differences(env):
         dis.dis_compute_flow_ex(dd.handle, a.detach(), b.detach(), W, H, W, dd.params, it.detach(), None, rec0, None,
                                 tmp)
         torch.cuda.synchronize()
-        q = oracle.params(polish=POLISH, **PARAMS)
+        q = oracle.params(polish=POLISH, **library_values(PARAMS))
         _, rec_star = oracle.dis_flow(I0.astype(np.float64), I1.astype(np.float64), q,
                                       init_flow=init.astype(np.float64),
                                       frozen=rec0.cpu().numpy().astype(np.float64), record=True)
@@ -169,7 +183,7 @@ def test_stereo_gradient_matches_fp64_finite_differences(env, search_grad):
         torch.cuda.synchronize()
         rec = rec0.cpu().numpy().astype(np.float64)
         if search_grad:
-            q = oracle.params(polish=POLISH, **kw)
+            q = oracle.params(polish=POLISH, **library_values(kw))
             _, rec = oracle.dis_flow(I0.astype(np.float64), I1.astype(np.float64), q,
                                      init_flow=init.astype(np.float64), frozen=rec, record=True)
         rec = rec.astype(np.float32)
