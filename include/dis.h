@@ -436,8 +436,9 @@ dis_status dis_backward(dis_handle* h, const float* I0, const float* I1, int w, 
  *    with that device current) and caches it; make that first call before any stream capture.
  *    cudaDeviceReset on a device releases the array with its context, which leaves the cached
  *    address stale: do not call this entry point on a device after resetting it.
- *  - It always uses refinement launch form 1 (dis_set_refine_fusion mode 1: one fused launch per
- *    outer pass, two above 128 Ki pixels); all launch forms give the same flow bit for bit.
+ *  - It always uses refinement launch form 1 (dis_set_refine_fusion mode 1) with the default
+ *    split threshold: one fused launch per outer pass; all launch forms give the same flow bit
+ *    for bit.
  *  - All calls share the one array, which keeps the last call's contents (the call itself
  *    zeroes what must start at zero).  Calls whose GPU work overlaps - on different streams
  *    or host threads - race on it: serialise them (e.g. one stream).

@@ -5,8 +5,8 @@ DifferentiableDIS(I0, I1, init_flow) returns the flow of the frozen-search DIS m
 forward records every patch's search increment (FP32 search) and evaluates the map with those
 increments frozen in FP64; the backward repeats that replay and runs the FP64 adjoint of the
 pyramid, initial displacements, densification and unrolled SOR sweeps.
-BatchedDifferentiableDIS runs several pairs of that map side by side on streams of their own.  photometric_loss is the mean
-Charbonnier penalty sqrt((I1(x + U(x)) - I0(x))^2 + eps^2) with its gradients.
+BatchedDifferentiableDIS runs several pairs of that map side by side on streams of their own.
+photometric_loss is the mean Charbonnier penalty sqrt((I1(x + U(x)) - I0(x))^2 + eps^2) with its gradients.
 """
 import torch
 
@@ -27,16 +27,53 @@ class DifferentiableDIS:
     The patch searches are replayed from their recorded increments (recorded by the FP32 search
     of each call, or given as `frozen`, dis_levels' total_patches x 2).  search_grad=0 (default)
     treats the increments as constants; search_grad=1 differentiates the converged search by the
-    implicit-function theorem (pass increments of converged searches)."""
+    implicit-function theorem (pass increments of converged searches).
+
+    An instance keeps the buffers of its library calls (frames, increments, workspace, results)
+    and issues its work on the stream current at each call: use one instance per stream."""
 
     def __init__(self, max_w, max_h, preset="default", **overrides):
         self.params = dis.dis_default_params(preset, channels=1, **overrides)
         self.handle = dis.dis_create(max_w, max_h, 1, 1)
+        self._stage = None
+        self._token = None
 
     def close(self):
         if self.handle:
+            if self._stage is not None:
+                torch.cuda.synchronize(self._stage["ws"].device)  # graphs may still read the staging
+                self._stage = None
             dis.dis_destroy(self.handle)
             self.handle = None
+
+    def _staging(self, I0, n, init):
+        """Buffers the library calls read and write.  Their addresses stay the same from call to
+        call, so the library replays each call's chain of launches as one CUDA graph (it keys
+        its graphs on the call's pointers); inputs are copied in and results copied out."""
+        H, W = I0.shape
+        key = (I0.device, H, W, n, None if init is None else tuple(init.shape))
+        st = self._stage
+        if st is None or st["key"] != key:
+            dev = I0.device
+            nbytes = dis.dis_backward_workspace_bytes(W, H, self.params)
+            st = dict(key=key, ws=torch.empty(nbytes, device=dev, dtype=torch.uint8), nbytes=nbytes,
+                      I0=torch.empty((H, W), device=dev), I1=torch.empty((H, W), device=dev),
+                      rec=torch.empty((n, 2), device=dev), flow=torch.empty((H, W, 2), device=dev),
+                      gflow=torch.empty((H, W, 2), device=dev), gI0=torch.empty((H, W), device=dev),
+                      gI1=torch.empty((H, W), device=dev),
+                      init=None if init is None else torch.empty_like(init),
+                      gInit=None if init is None else torch.empty_like(init))
+            self._stage, self._token = st, None
+        return st
+
+    def _stage_inputs(self, st, token, I0, I1, init, rec):
+        if self._token is not token:  # the staging holds another call's inputs
+            st["I0"].copy_(I0)
+            st["I1"].copy_(I1)
+            if init is not None:
+                st["init"].copy_(init)
+            st["rec"].copy_(rec)
+            self._token = token
 
     def __del__(self):
         try:
@@ -114,11 +151,13 @@ class _DISFlow(torch.autograd.Function):
             if tuple(rec.shape) != (n, 2):
                 raise ValueError("frozen increments must be (%d, 2)" % n)
         # ... and the map with those increments frozen is evaluated in FP64
-        nbytes = dis.dis_backward_workspace_bytes(W, H, p)
-        ws = torch.empty(nbytes, device=I0c.device, dtype=torch.uint8)
-        flow = torch.empty((H, W, 2), device=I0c.device, dtype=torch.float32)
-        dis.dis_replay_flow(owner.handle, I0c, I1c, W, H, W, p, init, rec, flow, ws, nbytes)
-        ctx.owner = owner
+        st = owner._staging(I0c, n, init)
+        token = object()
+        owner._stage_inputs(st, token, I0c, I1c, init, rec)
+        dis.dis_replay_flow(owner.handle, st["I0"], st["I1"], W, H, W, p, st["init"], st["rec"], st["flow"], st["ws"],
+                            st["nbytes"])
+        flow = st["flow"].clone()
+        ctx.owner, ctx.token = owner, token
         ctx.has_init = init is not None
         ctx.save_for_backward(I0c, I1c, init if init is not None else torch.empty(0, device=I0c.device), rec)
         return flow
@@ -128,14 +167,14 @@ class _DISFlow(torch.autograd.Function):
         I0, I1, init, rec = ctx.saved_tensors
         owner, p = ctx.owner, ctx.owner.params
         H, W = I0.shape
-        nbytes = dis.dis_backward_workspace_bytes(W, H, p)
-        ws = torch.empty(nbytes, device=I0.device, dtype=torch.uint8)
-        gI0, gI1 = torch.empty_like(I0), torch.empty_like(I1)
         it = init if ctx.has_init else None
-        gInit = torch.empty_like(init) if ctx.has_init else None
-        dis.dis_backward(owner.handle, I0, I1, W, H, W, p, it, rec, grad_flow.contiguous(), gI0, gI1, W, gInit, ws,
-                         nbytes)
-        return gI0, gI1, gInit, None, None
+        st = owner._staging(I0, rec.shape[0], it)
+        owner._stage_inputs(st, ctx.token, I0, I1, it, rec)
+        st["gflow"].copy_(grad_flow)
+        dis.dis_backward(owner.handle, st["I0"], st["I1"], W, H, W, p, st["init"], st["rec"], st["gflow"], st["gI0"],
+                         st["gI1"], W, st["gInit"], st["ws"], st["nbytes"])
+        gInit = st["gInit"].clone() if ctx.has_init else None
+        return st["gI0"].clone(), st["gI1"].clone(), gInit, None, None
 
 
 class _PhotometricLoss(torch.autograd.Function):

@@ -565,6 +565,26 @@ dis_status upload_jobs(dis_handle* hd, const Plan& plan, cudaStream_t s)
     return DIS_OK;
 }
 
+}  // namespace
+
+// The kernel nodes of a captured graph: the kernels every replay of it launches.
+int dis_host::graph_kernel_nodes(cudaGraph_t graph)
+{
+    size_t nn = 0;
+    int kernels = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+            for (size_t k = 0; k < nn; ++k) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nodes[k], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+            }
+    }
+    return kernels;
+}
+
+namespace {
+
 dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaStream_t s)
 {
     cudaError_t e;
@@ -593,17 +613,7 @@ dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaS
             return cuda_fail(hd, le, "kernel launch (capture)");
         }
         if (e != cudaSuccess) return cuda_fail(hd, e, "graph capture end");
-        // count the kernel nodes: the kernels every replay of this graph launches
-        size_t nn = 0;
-        kernels = 0;
-        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
-            std::vector<cudaGraphNode_t> nodes(nn);
-            if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
-                for (size_t k = 0; k < nn; ++k) {
-                    cudaGraphNodeType ty;
-                    if (cudaGraphNodeGetType(nodes[k], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
-                }
-        }
+        kernels = dis_host::graph_kernel_nodes(graph);
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(hd, e, "graph instantiate");
@@ -773,6 +783,7 @@ void dis_destroy(dis_handle* h)
     if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
     if (h->jobs_ev) cudaEventSynchronize(h->jobs_ev);
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
     if (h->probe_a) cudaEventDestroy(h->probe_a);
     if (h->probe_b) cudaEventDestroy(h->probe_b);
     if (h->hs.cs_in) cudaStreamSynchronize(h->hs.cs_in);

@@ -9,7 +9,9 @@
 // in the caller's workspace) and runs the adjoint kernels in reverse order.  No device memory
 // is allocated: everything lives in the caller's workspace.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -210,74 +212,12 @@ dis_status check_common(dis_handle* hd, const float* I0, const float* I1, int W,
     return DIS_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int64_t dis_backward_workspace_bytes(int width, int height, const dis_params* p)
+// The backward pass of one pair (the chain of launches dis_backward issues).
+cudaError_t backward(const Ctx& c, const float* I0, const float* I1, int W, int H, int64_t pitch, const float* init_flow,
+                     const float* frozen, const float* grad_flow, float* grad_I0, float* grad_I1, int64_t grad_pitch,
+                     float* grad_init_flow)
 {
-    std::string e;
-    if (validate_params(p, e) != DIS_OK || width < 1 || height < 1) return -1;
-    BwdLayout L;
-    if (layout(width, height, *p, L, e) != DIS_OK) return -1;
-    return (int64_t)L.total;
-}
-
-int64_t dis_photometric_loss_scratch_bytes(int width, int height, int64_t pitch, int channels)
-{
-    if (width < 1 || height < 1 || pitch < width || channels < 1) return -1;
-    return (int64_t)(al(sizeof(unsigned long long) * (size_t)pitch * height * channels) + sizeof(double) * 2048);
-}
-
-dis_status dis_photometric_loss(const float* I0, const float* I1, int w, int h, int64_t pitch, int channels,
-                                const float* flow, float eps, double* loss_out, float* grad_flow, float* grad_I0,
-                                float* grad_I1, void* scratch, int64_t scratch_bytes, void* stream)
-{
-    if (!I0 || !I1 || !flow || !loss_out || !grad_flow || !grad_I0 || !grad_I1 || !scratch || w < 1 || h < 1 ||
-        pitch < w || channels < 1 || channels > 3 || !(eps > 0.0f))
-        return set_fail(nullptr, DIS_ERR_INVALID_ARG, "dis_photometric_loss: bad pointer, size or eps");
-    const int64_t need = dis_photometric_loss_scratch_bytes(w, h, pitch, channels);
-    if (scratch_bytes < need) return set_fail(nullptr, DIS_ERR_INVALID_ARG, "dis_photometric_loss: scratch too small");
-    cudaStream_t s = (cudaStream_t)stream;
-    const dis::LaunchCfg lc = dis::stage_launch_cfg();
-    auto* acc = static_cast<unsigned long long*>(scratch);
-    const size_t acc_bytes = al(sizeof(unsigned long long) * (size_t)pitch * h * channels);
-    auto* partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + acc_bytes);
-    cudaError_t e = cudaMemsetAsync(acc, 0, acc_bytes, s);
-    if (e == cudaSuccess)
-        e = dis::launch_loss(I0, I1, w, h, (int)pitch, channels, reinterpret_cast<const float2*>(flow), eps, partials,
-                             2048, loss_out, reinterpret_cast<float2*>(grad_flow), grad_I0, acc, lc, s);
-    if (e == cudaSuccess)
-        e = dis::launch_fx_to_float(acc, (int)pitch, grad_I1, (int)pitch, w, h * channels, 1.0, false, lc, s);
-    return e == cudaSuccess ? DIS_OK : set_cuda_fail(nullptr, e, "dis_photometric_loss");
-}
-
-dis_status dis_replay_flow(dis_handle* hd, const float* I0, const float* I1, int W, int H, int64_t pitch,
-                           const dis_params* p, const float* init_flow, const float* frozen, float* flow_out,
-                           void* workspace, int64_t workspace_bytes, void* stream)
-{
-    BwdLayout L;
-    dis_status st = check_common(hd, I0, I1, W, H, pitch, p, frozen, workspace, workspace_bytes, L);
-    if (st != DIS_OK) return st;
-    if (!flow_out) return set_fail(hd, DIS_ERR_INVALID_ARG, "dis_replay_flow: flow_out is NULL");
-    const Ctx c{L, static_cast<char*>(workspace), *p, hd->lc, (cudaStream_t)stream};
-    cudaError_t e = replay(c, I0, I1, pitch, init_flow, frozen);
-    if (e == cudaSuccess)
-        e = dis::launch_d2_to_f2(c.D2(L.U[0]), reinterpret_cast<float2*>(flow_out), (long long)W * H, c.lc, c.s);
-    return e == cudaSuccess ? DIS_OK : set_cuda_fail(hd, e, "dis_replay_flow");
-}
-
-dis_status dis_backward(dis_handle* hd, const float* I0, const float* I1, int W, int H, int64_t pitch,
-                        const dis_params* p, const float* init_flow, const float* frozen, const float* grad_flow,
-                        float* grad_I0, float* grad_I1, int64_t grad_pitch, float* grad_init_flow, void* workspace,
-                        int64_t workspace_bytes, void* stream)
-{
-    BwdLayout L;
-    dis_status st = check_common(hd, I0, I1, W, H, pitch, p, frozen, workspace, workspace_bytes, L);
-    if (st != DIS_OK) return st;
-    if (!grad_flow || !grad_I0 || !grad_I1 || grad_pitch < W || (grad_init_flow && !init_flow))
-        return set_fail(hd, DIS_ERR_INVALID_ARG, "dis_backward: bad gradient pointer or pitch");
-    const Ctx c{L, static_cast<char*>(workspace), *p, hd->lc, (cudaStream_t)stream};
+    const BwdLayout& L = c.L;
     cudaStream_t s = c.s;
     const dis::LaunchCfg& lc = c.lc;
     cudaError_t e = cudaMemsetAsync(c.ws, 0, L.acc_end, s);
@@ -368,6 +308,148 @@ dis_status dis_backward(dis_handle* hd, const float* I0, const float* I1, int W,
     if (e == cudaSuccess && grad_init_flow)
         e = dis::launch_fx_to_float(c.U64(L.gInit), 2 * L.w[L.ss], grad_init_flow, 2 * L.w[L.ss], 2 * L.w[L.ss],
                                     L.h[L.ss], 1.0, false, lc, s);
+    return e;
+}
+
+// The key of a differentiable-form call: its kind, every pointer and size, the parameters.
+std::vector<int64_t> call_key(int kind, std::initializer_list<int64_t> args, const dis_params& p)
+{
+    std::vector<int64_t> k{kind};
+    k.insert(k.end(), args);
+    const int32_t* pw = reinterpret_cast<const int32_t*>(&p);  // every field is 4 bytes wide
+    for (size_t i = 0; i < sizeof(dis_params) / 4; ++i) k.push_back(pw[i]);
+    return k;
+}
+
+int64_t ptr_key(const void* q) { return (int64_t)reinterpret_cast<uintptr_t>(q); }
+
+// Runs record(stream) on `s`.  The differentiable form is a chain of several hundred short
+// launches whose issue, not their work, bounds a call; a call seen before (same key) is
+// captured once into a CUDA graph on the handle's capture stream and replayed with one launch
+// from then on.  A key seen for the first time launches directly, so callers whose buffers
+// change at every call pay no capture.
+template <class Record>
+cudaError_t run_graphed(dis_handle* hd, const std::vector<int64_t>& key, cudaStream_t s, Record&& record)
+{
+    if (!hd->use_graphs) {
+        hd->last_kernels = -1;
+        return record(s);
+    }
+    for (auto& g : hd->bwd_graphs)
+        if (g.key == key) {
+            hd->last_kernels = g.kernels;
+            return cudaGraphLaunch(g.exec, s);
+        }
+    auto seen = std::find(hd->bwd_seen.begin(), hd->bwd_seen.end(), key);
+    if (seen == hd->bwd_seen.end()) {
+        if (hd->bwd_seen.size() >= 16) hd->bwd_seen.erase(hd->bwd_seen.begin());
+        hd->bwd_seen.push_back(key);
+        hd->last_kernels = -1;
+        return record(s);
+    }
+    hd->bwd_seen.erase(seen);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(hd->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t le = record(hd->cap_stream);
+    e = cudaStreamEndCapture(hd->cap_stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return le != cudaSuccess ? le : e;
+    }
+    const int kernels = graph_kernel_nodes(graph);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    if (hd->bwd_graphs.size() >= 8) {
+        cudaGraphExecDestroy(hd->bwd_graphs.front().exec);
+        hd->bwd_graphs.erase(hd->bwd_graphs.begin());
+    }
+    hd->bwd_graphs.push_back({key, exec, kernels});
+    hd->last_kernels = kernels;
+    return cudaGraphLaunch(exec, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t dis_backward_workspace_bytes(int width, int height, const dis_params* p)
+{
+    std::string e;
+    if (validate_params(p, e) != DIS_OK || width < 1 || height < 1) return -1;
+    BwdLayout L;
+    if (layout(width, height, *p, L, e) != DIS_OK) return -1;
+    return (int64_t)L.total;
+}
+
+int64_t dis_photometric_loss_scratch_bytes(int width, int height, int64_t pitch, int channels)
+{
+    if (width < 1 || height < 1 || pitch < width || channels < 1) return -1;
+    return (int64_t)(al(sizeof(unsigned long long) * (size_t)pitch * height * channels) + sizeof(double) * 2048);
+}
+
+dis_status dis_photometric_loss(const float* I0, const float* I1, int w, int h, int64_t pitch, int channels,
+                                const float* flow, float eps, double* loss_out, float* grad_flow, float* grad_I0,
+                                float* grad_I1, void* scratch, int64_t scratch_bytes, void* stream)
+{
+    if (!I0 || !I1 || !flow || !loss_out || !grad_flow || !grad_I0 || !grad_I1 || !scratch || w < 1 || h < 1 ||
+        pitch < w || channels < 1 || channels > 3 || !(eps > 0.0f))
+        return set_fail(nullptr, DIS_ERR_INVALID_ARG, "dis_photometric_loss: bad pointer, size or eps");
+    const int64_t need = dis_photometric_loss_scratch_bytes(w, h, pitch, channels);
+    if (scratch_bytes < need) return set_fail(nullptr, DIS_ERR_INVALID_ARG, "dis_photometric_loss: scratch too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    const dis::LaunchCfg lc = dis::stage_launch_cfg();
+    auto* acc = static_cast<unsigned long long*>(scratch);
+    const size_t acc_bytes = al(sizeof(unsigned long long) * (size_t)pitch * h * channels);
+    auto* partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + acc_bytes);
+    cudaError_t e = cudaMemsetAsync(acc, 0, acc_bytes, s);
+    if (e == cudaSuccess)
+        e = dis::launch_loss(I0, I1, w, h, (int)pitch, channels, reinterpret_cast<const float2*>(flow), eps, partials,
+                             2048, loss_out, reinterpret_cast<float2*>(grad_flow), grad_I0, acc, lc, s);
+    if (e == cudaSuccess)
+        e = dis::launch_fx_to_float(acc, (int)pitch, grad_I1, (int)pitch, w, h * channels, 1.0, false, lc, s);
+    return e == cudaSuccess ? DIS_OK : set_cuda_fail(nullptr, e, "dis_photometric_loss");
+}
+
+dis_status dis_replay_flow(dis_handle* hd, const float* I0, const float* I1, int W, int H, int64_t pitch,
+                           const dis_params* p, const float* init_flow, const float* frozen, float* flow_out,
+                           void* workspace, int64_t workspace_bytes, void* stream)
+{
+    BwdLayout L;
+    dis_status st = check_common(hd, I0, I1, W, H, pitch, p, frozen, workspace, workspace_bytes, L);
+    if (st != DIS_OK) return st;
+    if (!flow_out) return set_fail(hd, DIS_ERR_INVALID_ARG, "dis_replay_flow: flow_out is NULL");
+    const auto key = call_key(0, {ptr_key(I0), ptr_key(I1), W, H, pitch, ptr_key(init_flow), ptr_key(frozen),
+                                  ptr_key(flow_out), ptr_key(workspace)}, *p);
+    const cudaError_t e = run_graphed(hd, key, (cudaStream_t)stream, [&](cudaStream_t s) {
+        const Ctx c{L, static_cast<char*>(workspace), *p, hd->lc, s};
+        cudaError_t e = replay(c, I0, I1, pitch, init_flow, frozen);
+        if (e == cudaSuccess)
+            e = dis::launch_d2_to_f2(c.D2(L.U[0]), reinterpret_cast<float2*>(flow_out), (long long)W * H, c.lc, s);
+        return e;
+    });
+    return e == cudaSuccess ? DIS_OK : set_cuda_fail(hd, e, "dis_replay_flow");
+}
+
+dis_status dis_backward(dis_handle* hd, const float* I0, const float* I1, int W, int H, int64_t pitch,
+                        const dis_params* p, const float* init_flow, const float* frozen, const float* grad_flow,
+                        float* grad_I0, float* grad_I1, int64_t grad_pitch, float* grad_init_flow, void* workspace,
+                        int64_t workspace_bytes, void* stream)
+{
+    BwdLayout L;
+    dis_status st = check_common(hd, I0, I1, W, H, pitch, p, frozen, workspace, workspace_bytes, L);
+    if (st != DIS_OK) return st;
+    if (!grad_flow || !grad_I0 || !grad_I1 || grad_pitch < W || (grad_init_flow && !init_flow))
+        return set_fail(hd, DIS_ERR_INVALID_ARG, "dis_backward: bad gradient pointer or pitch");
+    const auto key = call_key(1, {ptr_key(I0), ptr_key(I1), W, H, pitch, ptr_key(init_flow), ptr_key(frozen),
+                                  ptr_key(grad_flow), ptr_key(grad_I0), ptr_key(grad_I1), grad_pitch,
+                                  ptr_key(grad_init_flow), ptr_key(workspace)}, *p);
+    const cudaError_t e = run_graphed(hd, key, (cudaStream_t)stream, [&](cudaStream_t s) {
+        return backward(Ctx{L, static_cast<char*>(workspace), *p, hd->lc, s}, I0, I1, W, H, pitch, init_flow, frozen,
+                        grad_flow, grad_I0, grad_I1, grad_pitch, grad_init_flow);
+    });
     return e == cudaSuccess ? DIS_OK : set_cuda_fail(hd, e, "dis_backward");
 }
 

@@ -33,6 +33,11 @@ struct dis_handle {
         int kernels;  // kernel nodes of the captured graph
     };
     std::vector<Graph> graphs;
+    // graphs of the differentiable form's calls (dis_replay_flow, dis_backward), keyed on every
+    // pointer, size and parameter of the call: a key is captured the second time it is seen,
+    // so calls whose buffers change every time launch directly instead of capturing each time
+    std::vector<Graph> bwd_graphs;
+    std::vector<std::vector<int64_t>> bwd_seen;
     dis::LaunchCfg lc{};
     bool use_graphs = true;
     int search_lanes[17] = {};  // autotuned lanes per patch by patch size (0 = default)
@@ -68,4 +73,5 @@ dis_status validate_params(const dis_params* p, std::string& err);
 dis_status levels_of(int W, int H, const dis_params& p, int& ss, int& sf, std::string& err);
 dis_status set_fail(dis_handle* h, dis_status st, const std::string& msg);
 dis_status set_cuda_fail(dis_handle* h, cudaError_t e, const char* what);
+int graph_kernel_nodes(cudaGraph_t graph);
 }  // namespace dis_host

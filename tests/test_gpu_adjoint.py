@@ -211,6 +211,50 @@ def test_adjoint_matches_fp64_finite_differences(env):
     assert_within_tolerance(errs)
 
 
+def test_repeated_calls_replay_a_graph_bit_exact(env):
+    """A differentiable-form call seen before (same buffers, sizes and parameters) is replayed as
+    one CUDA graph: the first call launches directly, the second captures, the third replays; all
+    three give the same flow and gradients bit for bit."""
+    torch, dis, ag, dev = env
+    W, H = 512, 256
+    I0, I1 = _pair(3100)
+    dd = ag.DifferentiableDIS(W, H, **PARAMS)
+    try:
+        hs, ws_ = dd.coarsest_shape(W, H)
+        p = dd.params
+        a, b = torch.tensor(I0, device=dev), torch.tensor(I1, device=dev)
+        it = torch.full((hs, ws_, 2), 0.25, device=dev)
+        n = dis.dis_levels(W, H, p)[2]
+        rec = torch.empty((n, 2), device=dev)
+        tmp = torch.empty((H, W, 2), device=dev)
+        dis.dis_compute_flow_ex(dd.handle, a, b, W, H, W, p, it, None, rec, None, tmp)
+        nb = dis.dis_backward_workspace_bytes(W, H, p)
+        ws = torch.empty(nb, device=dev, dtype=torch.uint8)
+        flow = torch.empty((H, W, 2), device=dev)
+        g = torch.from_numpy(np.random.default_rng(5).normal(0, 1e-3, (H, W, 2)).astype(np.float32)).to(dev)
+        outs = [torch.empty((H, W), device=dev), torch.empty((H, W), device=dev), torch.empty_like(it)]
+        flows, grads, kernels = [], [], []
+        for _ in range(3):
+            flow.fill_(float("nan"))
+            dis.dis_replay_flow(dd.handle, a, b, W, H, W, p, it, rec, flow, ws, nb)
+            kf = dis.dis_last_call_kernels(dd.handle)
+            for o in outs:
+                o.fill_(float("nan"))
+            dis.dis_backward(dd.handle, a, b, W, H, W, p, it, rec, g, outs[0], outs[1], W, outs[2], ws, nb)
+            kernels.append((kf, dis.dis_last_call_kernels(dd.handle)))
+            torch.cuda.synchronize()
+            flows.append(flow.clone())
+            grads.append([o.clone() for o in outs])
+        assert kernels[0] == (-1, -1), kernels
+        assert kernels[1] == kernels[2] and min(kernels[1]) > 100, kernels
+        assert bool(torch.isfinite(flows[0]).all()) and all(bool(torch.isfinite(o).all()) for o in grads[0])
+        for k in (1, 2):
+            assert torch.equal(flows[k], flows[0])
+            assert all(torch.equal(x, y) for x, y in zip(grads[k], grads[0]))
+    finally:
+        dd.close()
+
+
 def test_batch_of_eight_pairs(env):
     """The eight 512x256 pairs of the differentiable workload: every pair's gradient (to I0, I1
     and a smooth initial flow) through single-pair calls on one handle against FP64 central
