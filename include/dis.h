@@ -392,7 +392,11 @@ dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, flo
  * forward-backward consistency); with finest_scale > 0 the final bilinear up-scaling (and its
  * transpose) is part of F, with dof 1 the stereo refinement.  The search norm does not enter F (it only decides the recorded increments).  frozen: dis_levels' total_patches x 2 floats, coarsest level first; init_flow
  * (nullable): level theta_ss resolution, dense, 2 floats per pixel.  Nothing is allocated: the
- * caller passes a device workspace of dis_backward_workspace_bytes bytes. */
+ * caller passes a device workspace of dis_backward_workspace_bytes bytes.  Each call is a chain
+ * of several hundred short launches: a call whose pointers, sizes and parameters all equal those
+ * of an earlier call on the handle (the handle remembers the last 16 such keys and keeps graphs
+ * of the last 8) is captured once into a CUDA graph and replayed with one launch after that,
+ * with the same results bit for bit (environment DIS_NO_GRAPH=1 at dis_create: never). */
 
 /* Photometric loss L = mean over channels and pixels of sqrt((I1(x + U(x)) - I0(x))^2 + eps^2)
  * (Charbonnier, eps = 0.001 by default) on the [0,1] scale, and its gradient with respect to
