@@ -21,14 +21,14 @@ cudaError_t launch_search(const Jobs<LevelJob>& js, long long total, int ps, int
         switch (lanes) {
             case 4: return launch_lp<4, 16, 8, 5>(js, total, ps, stride, iters, lc, s);
             case 16: return launch_lp<16, 4, 8>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<8, 8, 8, 6>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<8, 8, 8, 8>(js, total, ps, stride, iters, lc, s);
         }
     }
     if (ps == 12) {
         switch (lanes) {
             case 8: return launch_lp<8, 18, 12>(js, total, ps, stride, iters, lc, s);
             case 32: return launch_lp<32, 5, 12>(js, total, ps, stride, iters, lc, s);
-            default: return launch_lp<16, 9, 12, 5, false>(js, total, ps, stride, iters, lc, s);
+            default: return launch_lp<16, 9, 12, 7, true>(js, total, ps, stride, iters, lc, s);
         }
     }
     if (ps < 8) {

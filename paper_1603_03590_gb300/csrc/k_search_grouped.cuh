@@ -6,7 +6,7 @@
 // l, l + LPP, ... (PPL of them).  The prologue stages the (ps+2)^2 window of I0 around the
 // patch in shared memory, computes the Sobel/8 gradients S' = grad T of the mean-normalised
 // template T, leaves T (in the window) and S' in shared memory (registers stay free for
-// occupancy: 24 warps per SM at 12x12) and forms, by group shuffle reductions, the 2x2 Hessian
+// occupancy: 28 warps per SM at 12x12, 32 at 8x8) and forms, by group shuffle reductions, the 2x2 Hessian
 // H' = sum S'^T S', sum S' and sum T.
 //
 // Iterations.  u is shared by the whole patch, so while the integer part of u stays in one cell
@@ -41,6 +41,8 @@
 #include "dis_device.cuh"
 
 namespace dis {
+
+constexpr int kSearchThreads = 128;  // threads per block of the grouped search
 
 template <int LPP>
 __device__ __forceinline__ float group_sum(float v, unsigned mask)
@@ -96,13 +98,15 @@ __device__ __forceinline__ void group_sum12(float (&Q)[12], unsigned gmask, int 
 }
 
 // PSC: compile-time patch size (0: the runtime `ps_rt`).  MINB: resident blocks per SM the
-// register allocation must allow (chosen per variant so that nothing spills).  GSM: template
-// gradients in shared memory (else in registers; measured per variant, see launch_search).
+// register allocation must allow (chosen per variant by measurement: the default 12x12 and 8x8
+// variants run at 7 and 8 blocks, which spills a few registers (36 and 12 bytes per thread) and
+// gains more in latency hiding than the spills cost).  GSM: template gradients in shared memory (else in
+// registers; measured per variant, see launch_search).
 // DOF / ROBUST: the modes above; `norm` (1 L1, 2 Huber) and `huber_b` are read by ROBUST only.
 // TERM: term2 > 0 makes a patch stop after the first update whose squared step length is at most
 // term2 (early termination on a small step; 0: the fixed count, ended early only where exact).
 template <int LPP, int PPL, int PSC, int MINB, bool GSM, int DOF = 2, bool ROBUST = false, bool TERM = false>
-__global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
+__global__ void __launch_bounds__(kSearchThreads, MINB) search_kernel(const __grid_constant__ Jobs<LevelJob> js, long long total,
                                                      int ps_rt, int stride, int iters, int norm, float huber_b,
                                                      float term2, unsigned int* __restrict__ wq)
 {
@@ -117,6 +121,10 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
     float* win = smem + (wib * GPW + grp) * (ws * ws + (GSM ? 2 * n : 0));  // the group's I0 window,
     float* gxs = win + ws * ws;                                             // then (GSM) the template
     float* gys = gxs + n;                                                   // gradients
+    // after the groups' regions, per thread: the offset ky * pitch + kx of each of its patch
+    // pixels k = gl + LPP m (set per patch), so that a rebuild addresses a pixel's taps from the
+    // cell's two row pointers
+    int* offs = reinterpret_cast<int*>(smem + (kSearchThreads / LPP) * (ws * ws + (GSM ? 2 * n : 0))) + threadIdx.x;
     const float inv_n = 1.0f / (float)n;
     // Patch assignment.  Every group starts on patch (its index in the grid); with a work queue
     // it then takes the next unclaimed patch (patch costs vary several-fold with the texture and
@@ -147,6 +155,13 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
             for (int t = gl; t < ws * ws; t += LPP) {
                 const int a = t % ws, b = t / ws;
                 win[t] = __ldg(J.S0 + (long long)clampi(py - 1 + b, 0, h - 1) * pitch + clampi(px - 1 + a, 0, w - 1));
+            }
+            if constexpr (!ROBUST) {
+#pragma unroll
+                for (int m = 0; m < PPL; ++m) {
+                    const int k = gl + LPP * m;
+                    if (k < n) offs[m * kSearchThreads] = (k / ps) * pitch + k % ps;
+                }
             }
             __syncwarp(gmask);
             float s0 = 0.0f, h00 = 0.0f, h01 = 0.0f, h11 = 0.0f, sgx = 0.0f, sgy = 0.0f, sT = 0.0f;
@@ -338,6 +353,9 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                         const bool inside = xi >= 0 && yi >= 0 && xi + ps <= w - 1 && yi + ps <= h - 1;
 #pragma unroll
                         for (int q = 0; q < NQ; ++q) Q[q] = 0.0f;
+                        // inside the image: the first pixel's top-left tap
+                        const float* r0 = J.S1;
+                        if (inside) r0 += (long long)yi * pitch + xi;
                         // raw tap sums: Q[t] = sum tap_t, Q[4 + t] = sum gx tap_t, Q[8 + t] = sum
                         // gy tap_t for the taps t = a, b, c, d; the cell sums follow below.  (Sums
                         // relative to the patch mean would be residual-sized, but cost 4 more adds
@@ -347,16 +365,16 @@ __global__ void __launch_bounds__(128, MINB) search_kernel(const __grid_constant
                         for (int m = 0; m < PPL; ++m) {
                             const int k = gl + LPP * m;
                             if (k < n) {
-                                const int kx = k % ps, ky = k / ps;
                                 const float gx = GSM ? gxs[k] : gxr[GSM ? 0 : m];
                                 float tp[4];
                                 if (inside) {
-                                    const float* p = J.S1 + (long long)(yi + ky) * pitch + (xi + kx);
-                                    tp[0] = __ldg(p);
-                                    tp[1] = __ldg(p + 1);
-                                    tp[2] = __ldg(p + pitch);
-                                    tp[3] = __ldg(p + pitch + 1);
+                                    const int o = offs[m * kSearchThreads];
+                                    tp[0] = __ldg(r0 + o);
+                                    tp[1] = __ldg(r0 + o + 1);
+                                    tp[2] = __ldg(r0 + (o + pitch));
+                                    tp[3] = __ldg(r0 + (o + pitch) + 1);
                                 } else {
+                                    const int kx = k % ps, ky = k / ps;
                                     const int x0 = clampi(xi + kx, 0, w - 1), x1 = clampi(xi + kx + 1, 0, w - 1);
                                     const float* r0 = J.S1 + (long long)clampi(yi + ky, 0, h - 1) * pitch;
                                     const float* r1 = J.S1 + (long long)clampi(yi + ky + 1, 0, h - 1) * pitch;
@@ -451,8 +469,9 @@ static cudaError_t launch_lp(const Jobs<LevelJob>& js, long long total, int ps, 
                              const LaunchCfg& lc, cudaStream_t s, int norm = 0, float huber_b = 0.0f,
                              float term2 = 0.0f)
 {
-    const int threads = 128, wpb = threads / 32, per_block = wpb * (32 / LPP);
-    const size_t smem = (size_t)per_block * ((ps + 2) * (ps + 2) + (GSM ? 2 * ps * ps : 0)) * sizeof(float);
+    const int threads = kSearchThreads, wpb = threads / 32, per_block = wpb * (32 / LPP);
+    const size_t smem = (size_t)per_block * ((ps + 2) * (ps + 2) + (GSM ? 2 * ps * ps : 0)) * sizeof(float) +
+                        (size_t)PPL * threads * sizeof(int);
     static int occ = 0;
     if (occ == 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, search_kernel<LPP, PPL, PSC, MINB, GSM, DOF, ROBUST, TERM>, threads,

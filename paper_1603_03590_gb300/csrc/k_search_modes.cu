@@ -9,10 +9,11 @@ template <int DOF, bool ROBUST>
 static cudaError_t launch_mode(const Jobs<LevelJob>& js, long long total, int ps, int stride, int iters, int norm,
                                float huber_b, float term2, int lanes, const LaunchCfg& lc, cudaStream_t s)
 {
-    // the robust form keeps four coefficients per pixel in registers: fewer resident blocks
-    // (chosen so that nothing spills); wider groups hold fewer pixels per lane
-    constexpr int MB8 = ROBUST ? (DOF == 1 ? 3 : 4) : 6, MB12 = ROBUST ? (DOF == 1 ? 2 : 3) : 5;
-    constexpr int MBW = ROBUST ? (DOF == 1 ? 4 : 5) : 6;
+    // resident blocks per SM, measured: the robust form keeps four coefficients per pixel in
+    // registers, so fewer blocks (chosen so that nothing spills); the 12x12 16-lane L2 form runs
+    // six blocks at the cost of a few spilled registers; wider groups hold fewer pixels per lane
+    constexpr int MB8 = ROBUST ? (DOF == 1 ? 3 : 4) : 6, MB12 = ROBUST ? (DOF == 1 ? 2 : 3) : 6;
+    constexpr int MBW = ROBUST ? (DOF == 1 ? 4 : 5) : 6, MB32 = ROBUST ? MBW : 5;
     if (ps == 8) {
         if (lanes == 16)
             return launch_lp<16, 4, 8, MBW, true, DOF, ROBUST, true>(js, total, ps, stride, iters, lc, s, norm, huber_b, term2);
@@ -20,7 +21,7 @@ static cudaError_t launch_mode(const Jobs<LevelJob>& js, long long total, int ps
     }
     if (ps == 12) {
         if (lanes == 32)
-            return launch_lp<32, 5, 12, MBW, true, DOF, ROBUST, true>(js, total, ps, stride, iters, lc, s, norm, huber_b, term2);
+            return launch_lp<32, 5, 12, MB32, true, DOF, ROBUST, true>(js, total, ps, stride, iters, lc, s, norm, huber_b, term2);
         return launch_lp<16, 9, 12, MB12, true, DOF, ROBUST, true>(js, total, ps, stride, iters, lc, s, norm, huber_b, term2);
     }
     if (ps < 8) return launch_lp<8, 7, 0, 4, true, DOF, ROBUST, true>(js, total, ps, stride, iters, lc, s, norm, huber_b, term2);
