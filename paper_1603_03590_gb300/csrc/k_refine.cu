@@ -408,7 +408,12 @@ __global__ void __launch_bounds__(PassGeom<K, C>::threads, PassGeom<K, C>::min_b
     constexpr int HS0 = S0 / 2, HE0 = S0 * S0 / 2, HS1 = S1 / 2, HE1 = S1 * S1 / 2;
     constexpr int E0 = S0 * S0;
     extern __shared__ float4 sm4[];
-    float2* r0 = reinterpret_cast<float2*>(sm4);  // planes: (a11, a12) (a22, b1) (b2, psiS) [(EI, EG) or psi]
+    // R0 planes: (a11, a12) (a22, b1) as float2, then b2 and psiS as two float planes (a float
+    // plane per value keeps the four neighbour reads of psiS in a sweep free of bank conflicts),
+    // then, for three channels, (EI, EG)
+    float2* r0 = reinterpret_cast<float2*>(sm4);
+    float* rb2 = reinterpret_cast<float*>(r0 + 2 * E0);
+    float* rps = rb2 + E0;
     float* Ab = reinterpret_cast<float*>(reinterpret_cast<char*>(sm4) + G::bytes_r0);
     float* Az = Ab + WA * SA;
     float* Bx = Az + WA * SA;
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(PassGeom<K, C>::threads, PassGeom<K, C>::min_b
                         refine_system_acc(d, psiI, psiG, a11, a12, a22, b1, b2);
                         r0[ci] = make_float2(a11, a12);
                         r0[E0 + ci] = make_float2(a22, b1);
-                        r0[2 * E0 + ci].x = b2;
+                        rb2[ci] = b2;
                     } else if (sweep_c == 0) {
                         float2 e = c == 0 ? make_float2(0.0f, 0.0f) : r0[3 * E0 + ci];
                         refine_energy_acc(d, du, dv, e.x, e.y);
@@ -513,12 +518,12 @@ __global__ void __launch_bounds__(PassGeom<K, C>::threads, PassGeom<K, C>::min_b
                         if (c > 0) {
                             s01 = r0[ci];
                             s23 = r0[E0 + ci];
-                            s4 = r0[2 * E0 + ci].x;
+                            s4 = rb2[ci];
                         }
                         refine_system_acc(d, psiI, psiG, s01.x, s01.y, s23.x, s23.y, s4);
                         r0[ci] = s01;
                         r0[E0 + ci] = s23;
-                        r0[2 * E0 + ci].x = s4;
+                        rb2[ci] = s4;
                     }
                 }
                 __syncthreads();
@@ -561,7 +566,7 @@ __global__ void __launch_bounds__(PassGeom<K, C>::threads, PassGeom<K, C>::min_b
             const float vx = refine_cdiff(R.y, R.w, L.y, L.w);
             const float uy = refine_cdiff(Dn.x, Dn.z, Up.x, Up.z);
             const float vy = refine_cdiff(Dn.y, Dn.w, Up.y, Up.w);
-            r0[2 * E0 + c * HE0 + ly * HS0 + (lx >> 1)].y = refine_smooth_weight(ux, uy, vx, vy, alpha);
+            rps[c * HE0 + ly * HS0 + (lx >> 1)] = refine_smooth_weight(ux, uy, vx, vy, alpha);
         }
         if constexpr (PHASE == 2) {
             // the sweeps continue from the first half's increment
@@ -608,15 +613,16 @@ __global__ void __launch_bounds__(PassGeom<K, C>::threads, PassGeom<K, C>::min_b
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const float4 v = r1[INNER ? n1[q] : (in[q] ? n1[q] : i1)];
-                        psq[q] = r0[2 * E0 + (INNER ? n0[q] : (in[q] ? n0[q] : i0))].y;
+                        psq[q] = rps[INNER ? n0[q] : (in[q] ? n0[q] : i0)];
                         Uq[q] = make_float2(v.x, v.y);
                         duq[q] = v.z;
                         dvq[q] = v.w;
                     }
                     float4 me = r1[i1];
-                    const float2 s01 = r0[i0], s23 = r0[E0 + i0], s45 = r0[2 * E0 + i0];
+                    const float2 s01 = r0[i0], s23 = r0[E0 + i0];
+                    const float s4 = rb2[i0], s5 = rps[i0];
                     float du = me.z, dv = me.w;
-                    refine_sor_update(s01.x, s01.y, s23.x, s23.y, s45.x, s45.y, in, psq, Uq, duq, dvq,
+                    refine_sor_update(s01.x, s01.y, s23.x, s23.y, s4, s5, in, psq, Uq, duq, dvq,
                                       make_float2(me.x, me.y), omega, dof, du, dv);
                     me.z = du;
                     me.w = dv;
