@@ -483,7 +483,7 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
         return ce;
     };
     for (const Phase& ph : plan.phases) {
-        const char* tab = hd->jobs_dev + ph.off;
+        const char* tab = hd->jobs_cur + ph.off;
         switch (ph.kind) {
             case Phase::PREP:
                 e = traced(DIS_LAUNCH_PREP, 0, [&] {
@@ -552,16 +552,31 @@ cudaError_t record_plan(dis_handle* hd, const Plan& plan, const dis_params& p, c
 dis_status upload_jobs(dis_handle* hd, const Plan& plan, cudaStream_t s)
 {
     cudaError_t e;
-    if (!hd->jobs_valid || hd->jobs_last != plan.blob) {
-        if ((e = cudaEventSynchronize(hd->jobs_ev)) != cudaSuccess) return cuda_fail(hd, e, "job upload wait");
-        std::memcpy(hd->jobs_pinned, plan.blob.data(), plan.blob.size());
-        if ((e = cudaMemcpyAsync(hd->jobs_dev, hd->jobs_pinned, plan.blob.size(), cudaMemcpyHostToDevice, s)) !=
-            cudaSuccess)
+    int slot = -1;
+    for (int k = 0; k < dis_handle::kJobSlots && slot < 0; ++k)
+        if (hd->jobs_ok[k] && hd->jobs_blob[k] == plan.blob) slot = k;
+    if (slot >= 0) {
+        // resident: a call on another stream than the upload's waits for that upload
+        if (hd->jobs_stream[slot] != s && (e = cudaStreamWaitEvent(s, hd->jobs_ev[slot], 0)) != cudaSuccess)
+            return cuda_fail(hd, e, "job table wait");
+    } else {
+        slot = 0;  // replace the least recently used table
+        for (int k = 1; k < dis_handle::kJobSlots; ++k)
+            if (hd->jobs_stamp[k] < hd->jobs_stamp[slot]) slot = k;
+        char* pin = hd->jobs_pinned + (size_t)slot * hd->jobs_bytes;
+        if ((e = cudaEventSynchronize(hd->jobs_ev[slot])) != cudaSuccess) return cuda_fail(hd, e, "job upload wait");
+        std::memcpy(pin, plan.blob.data(), plan.blob.size());
+        if ((e = cudaMemcpyAsync(hd->jobs_dev + (size_t)slot * hd->jobs_bytes, pin, plan.blob.size(),
+                                 cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return cuda_fail(hd, e, "job upload");
-        if ((e = cudaEventRecord(hd->jobs_ev, s)) != cudaSuccess) return cuda_fail(hd, e, "job upload event");
-        hd->jobs_last = plan.blob;
-        hd->jobs_valid = true;
+        if ((e = cudaEventRecord(hd->jobs_ev[slot], s)) != cudaSuccess) return cuda_fail(hd, e, "job upload event");
+        hd->jobs_blob[slot] = plan.blob;
+        hd->jobs_ok[slot] = true;
+        hd->jobs_stream[slot] = s;
     }
+    hd->jobs_stamp[slot] = ++hd->jobs_clock;
+    hd->jobs_slot = slot;
+    hd->jobs_cur = hd->jobs_dev + (size_t)slot * hd->jobs_bytes;
     return DIS_OK;
 }
 
@@ -597,8 +612,11 @@ dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaS
     }
     cudaGraphExec_t exec = nullptr;
     int kernels = -1;
+    // a graph's kernels read the job table of one slot
+    std::vector<int64_t> key = plan.key;
+    key.push_back(hd->jobs_slot);
     for (auto& g : hd->graphs)
-        if (g.key == plan.key) {
+        if (g.key == key) {
             exec = g.exec;
             kernels = g.kernels;
         }
@@ -621,7 +639,7 @@ dis_status run_plan(dis_handle* hd, const Plan& plan, const dis_params& p, cudaS
             cudaGraphExecDestroy(hd->graphs.front().exec);
             hd->graphs.erase(hd->graphs.begin());
         }
-        hd->graphs.push_back({plan.key, exec, kernels});
+        hd->graphs.push_back({key, exec, kernels});
     }
     if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(hd, e, "graph launch");
     hd->last_kernels = kernels;
@@ -745,7 +763,7 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
     off = align_up(off + sizeof(float) * h->rs_floats, kAlign);
     h->slot_bytes = off;
     h->jobs_bytes = align_up((size_t)max_batch * (4 + 2 * L) * 256 + 4096, kAlign);
-    h->arena_bytes = h->slot_bytes * max_batch + h->jobs_bytes + kAlign;  // + the search work queue
+    h->arena_bytes = h->slot_bytes * max_batch + dis_handle::kJobSlots * h->jobs_bytes + kAlign;  // + the work queue
     cudaError_t e = cudaMalloc(&h->arena, h->arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -753,7 +771,7 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
         return fail(nullptr, DIS_ERR_OUT_OF_MEMORY, std::string("arena allocation failed: ") + cudaGetErrorString(e));
     }
     h->jobs_dev = h->arena + h->slot_bytes * max_batch;
-    unsigned int* wq = (unsigned int*)(h->jobs_dev + h->jobs_bytes);
+    unsigned int* wq = (unsigned int*)(h->jobs_dev + dis_handle::kJobSlots * h->jobs_bytes);
     // zeroed before dis_create returns: the caller's stream may be one that does not wait for
     // the legacy default stream, on which cudaMemset runs
     if ((e = cudaMemset(wq, 0, 2 * sizeof(unsigned int))) != cudaSuccess ||
@@ -762,13 +780,14 @@ dis_status dis_create(dis_handle** out, int max_w, int max_h, int max_batch, int
         dis_destroy(h);
         return fail(nullptr, DIS_ERR_CUDA, std::string("handle setup failed: ") + cudaGetErrorString(e));
     }
-    if ((e = cudaMallocHost(&h->jobs_pinned, h->jobs_bytes)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&h->jobs_ev, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    e = cudaMallocHost(&h->jobs_pinned, dis_handle::kJobSlots * h->jobs_bytes);
+    for (int k = 0; k < dis_handle::kJobSlots && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&h->jobs_ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess || (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         dis_destroy(h);
         return fail(nullptr, DIS_ERR_CUDA, std::string("handle setup failed: ") + cudaGetErrorString(e));
     }
-    cudaEventRecord(h->jobs_ev, h->cap_stream);
+    for (int k = 0; k < dis_handle::kJobSlots; ++k) cudaEventRecord(h->jobs_ev[k], h->cap_stream);
     h->lc = dis::query_launch_cfg();
     h->lc.wq = h->wq = wq;
     const char* ng = std::getenv("DIS_NO_GRAPH");
@@ -781,7 +800,8 @@ void dis_destroy(dis_handle* h)
 {
     if (!h) return;
     if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
-    if (h->jobs_ev) cudaEventSynchronize(h->jobs_ev);
+    for (int k = 0; k < dis_handle::kJobSlots; ++k)
+        if (h->jobs_ev[k]) cudaEventSynchronize(h->jobs_ev[k]);
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
     if (h->probe_a) cudaEventDestroy(h->probe_a);
@@ -798,7 +818,8 @@ void dis_destroy(dis_handle* h)
     if (h->hs.cs_out) cudaStreamDestroy(h->hs.cs_out);
     if (h->arena) cudaFree(h->arena);
     if (h->jobs_pinned) cudaFreeHost(h->jobs_pinned);
-    if (h->jobs_ev) cudaEventDestroy(h->jobs_ev);
+    for (int k = 0; k < dis_handle::kJobSlots; ++k)
+        if (h->jobs_ev[k]) cudaEventDestroy(h->jobs_ev[k]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
@@ -1216,7 +1237,7 @@ dis_status dis_densify_level_fb(dis_handle* hd, const float* I0, const float* I1
     dis_status st = upload_jobs(hd, plan, s);
     if (st != DIS_OK) return st;
     const long long np = (long long)J[0].nx * J[0].ny;
-    cudaError_t e = dis::launch_densify_fb(dis::device_jobs(reinterpret_cast<const LevelJob*>(hd->jobs_dev), 2), 2 * np,
+    cudaError_t e = dis::launch_densify_fb(dis::device_jobs(reinterpret_cast<const LevelJob*>(hd->jobs_cur), 2), 2 * np,
                                            2 * dis::refine_tiles(w, h), 2, ps, stride, hd->lc, s);
     return e == cudaSuccess ? DIS_OK : cuda_fail(hd, e, "dis_densify_level_fb");
 }

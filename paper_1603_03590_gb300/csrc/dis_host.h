@@ -20,12 +20,21 @@ struct dis_handle {
     std::vector<size_t> off_img, off_U, off_pu, off_pui, off_pst;  // per level, within a slot
     size_t off_rs = 0;
     size_t rs_floats = 0;  // capacity of the refinement scratch (floats)
-    char* jobs_dev = nullptr;
+    // job tables kept on the device: a call whose tables equal a resident one uploads nothing
+    // (callers that alternate between buffer sets, such as the host-buffer call's two staging
+    // halves, keep one table per set)
+    static constexpr int kJobSlots = 4;
+    char* jobs_dev = nullptr;     // kJobSlots tables of jobs_bytes each
     size_t jobs_bytes = 0;
-    char* jobs_pinned = nullptr;
-    cudaEvent_t jobs_ev = nullptr;
-    bool jobs_valid = false;
-    std::vector<char> jobs_last;
+    char* jobs_pinned = nullptr;  // kJobSlots pinned staging areas of the uploads
+    cudaEvent_t jobs_ev[kJobSlots] = {};       // each slot's latest upload ...
+    cudaStream_t jobs_stream[kJobSlots] = {};  // ... and the stream it was issued on
+    bool jobs_ok[kJobSlots] = {};
+    std::vector<char> jobs_blob[kJobSlots];
+    unsigned long long jobs_stamp[kJobSlots] = {};  // last use, for replacement
+    unsigned long long jobs_clock = 0;
+    int jobs_slot = 0;               // slot of the latest upload_jobs
+    const char* jobs_cur = nullptr;  // its device table
     cudaStream_t cap_stream = nullptr;
     struct Graph {
         std::vector<int64_t> key;
