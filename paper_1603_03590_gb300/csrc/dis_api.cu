@@ -276,8 +276,10 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.h = h;
             J.C = C;
             J.scale = p.intensity_scale;
+            J.vec = ((reinterpret_cast<uintptr_t>(J.I0) | reinterpret_cast<uintptr_t>(J.I1)) & 15) == 0 &&
+                    pairs[i].pitch % 4 == 0;
             J.base = base;
-            base += (long long)w * h;
+            base += h;
             plan.key.push_back(w);
             plan.key.push_back(h);
             plan.key.push_back(pairs[i].pitch);
@@ -306,7 +308,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.out_plane = (long long)J.pout * J.hout;
             J.nplanes = nplanes;
             J.base = base;
-            base += (long long)nplanes * J.wout * J.hout;
+            base += (long long)nplanes * J.hout;
             t.push_back(J);
         }
         plan.phases.push_back({Phase::PYR, push_table(plan.blob, t), (int)t.size(), base, 0, 0, s});
@@ -428,7 +430,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.ho = pairs[i].h;
             J.factor = (float)(1 << fsf);
             J.base = base;
-            base += (long long)J.wo * J.ho;
+            base += J.ho;
         }
         for (int i = 0; fb && i < n; ++i) {
             if (!pairs[i].flow_b) continue;
@@ -442,7 +444,7 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.ho = pairs[i].h;
             J.factor = (float)(1 << fsf);
             J.base = base;
-            base += (long long)J.wo * J.ho;
+            base += J.ho;
             t.push_back(J);
         }
         plan.phases.push_back({Phase::UP, push_table(plan.blob, t), (int)t.size(), base, 0, 0, fsf});
@@ -1104,7 +1106,7 @@ dis_status dis_pyr_down(const float* in, int w, int h, int64_t in_pitch, float* 
     J.hout = (h + 1) / 2;
     J.pout = (int)out_pitch;
     J.nplanes = 1;
-    cudaError_t e = dis::launch_pyr_down(dis::single_job(J), (long long)J.wout * J.hout, stage_lc(), (cudaStream_t)stream);
+    cudaError_t e = dis::launch_pyr_down(dis::single_job(J), J.hout, stage_lc(), (cudaStream_t)stream);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_pyr_down");
 }
 
@@ -1325,7 +1327,7 @@ dis_status dis_upsample_flow(const float* Uin, int wi, int hi, float factor, flo
     J.wo = wo;
     J.ho = ho;
     J.factor = factor;
-    cudaError_t e = dis::launch_upsample(dis::single_job(J), (long long)wo * ho, stage_lc(), (cudaStream_t)stream);
+    cudaError_t e = dis::launch_upsample(dis::single_job(J), ho, stage_lc(), (cudaStream_t)stream);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_upsample_flow");
 }
 

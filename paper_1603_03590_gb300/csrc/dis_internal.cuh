@@ -56,7 +56,7 @@ struct PyrJob {
     const float* in;
     float* out;
     long long in_plane, out_plane;
-    long long base;  // first flattened (plane, output pixel) item
+    long long base;  // first flattened (plane, output row) of the job
     int win, hin, pin, wout, hout, pout, nplanes;
 };
 
@@ -70,8 +70,9 @@ struct PrepJob {
     float* P0;  // null when the channel planes are not needed (C == 1 or no refinement)
     float* P1;
     long long out_plane;
-    long long base;
+    long long base;  // first flattened row of the job
     int w, h, in_pitch, out_pitch, C;
+    int vec;  // the input rows start on 16-byte boundaries (float4 loads)
     float scale;
 };
 
@@ -79,7 +80,7 @@ struct PrepJob {
 struct UpJob {
     const float2* in;
     float2* out;
-    long long base;
+    long long base;  // first flattened output row of the job
     int wi, hi, wo, ho;
     float factor;
 };
@@ -136,8 +137,8 @@ struct LaunchCfg {
 };
 
 // Launchers (return the launch error).  `total` = number of flattened items.
-cudaError_t launch_prep(const Jobs<PrepJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
-cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_prep(const Jobs<PrepJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t launch_sobel(const float* in, int w, int h, int pitch, float* gx, float* gy, int out_pitch,
                          const LaunchCfg& lc, cudaStream_t s);
 // lanes: lanes per patch (0 or 1 = the lane-per-patch form; see search_lane_options).  planes:
@@ -201,7 +202,7 @@ inline void set_refine_tiles(LevelJob& J, long long& tile_base)
 }
 cudaError_t launch_refine(const Jobs<LevelJob>& js, long long total_pix, long long total_half, long long total_tiles,
                           const RefineArgs& a, const LaunchCfg& lc, cudaStream_t s);
-cudaError_t launch_upsample(const Jobs<UpJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_upsample(const Jobs<UpJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s);
 
 LaunchCfg query_launch_cfg();
 

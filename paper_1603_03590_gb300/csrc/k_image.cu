@@ -1,61 +1,106 @@
 // Pyramid and resampling kernels of DIS (Sec. 3.1: image pyramid with theta_sd = 2 and
 // image gradients; up-scaling of the flow to full resolution).  All are streaming stencils
-// bound by memory bandwidth: thread per output pixel, read-only loads through L1.
+// bound by memory bandwidth, with read-only loads through L1.
 #include "dis_device.cuh"
 
 namespace dis {
 
+// Work split of the batched kernels below: one output row per block iteration.  The job of the
+// row is found once (a search over the jobs' first rows, `base`), not once per pixel, and the
+// block's threads cover the row with several pixels per thread in flight (four consecutive
+// pixels per step in prep_kernel, unrolled steps in the others).
+
 // Level 0: multiply the caller's [0,1] frames by intensity_scale, write the channel mean
 // (the search image) and, for colour input, the scaled channel planes.
-__global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ Jobs<PrepJob> js, long long total)
+__global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ Jobs<PrepJob> js, long long rows)
 {
-    for (long long g = gtid(); g < total; g += gstride()) {
-        const PrepJob& J = job_ref(js, find_job(js, g, &PrepJob::base));
-        const int k = (int)(g - J.base);  // < w * h < 2^31
-        const int y = k / J.w, x = k - y * J.w;
-        const long long io = (long long)y * J.in_pitch + x, oo = (long long)y * J.out_pitch + x;
-        float a = 0.0f, b = 0.0f;
-        for (int c = 0; c < J.C; ++c) {
-            const float v0 = J.scale * __ldg(J.I0 + c * J.in_plane + io);
-            const float v1 = J.scale * __ldg(J.I1 + c * J.in_plane + io);
-            if (J.P0) {
-                J.P0[c * J.out_plane + oo] = v0;
-                J.P1[c * J.out_plane + oo] = v1;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const PrepJob& J = job_ref(js, find_job(js, r, &PrepJob::base));
+        const int y = (int)(r - J.base), w = J.w, C = J.C;
+        const long long io = (long long)y * J.in_pitch, oo = (long long)y * J.out_pitch;
+        const float inv = 1.0f / (float)C;
+        const float scale = J.scale;
+        for (int x4 = 4 * threadIdx.x; x4 < w; x4 += 4 * blockDim.x) {
+            float a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, b[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const int nq = min(4, w - x4);
+            for (int c = 0; c < C; ++c) {
+                const float* __restrict__ p0 = J.I0 + c * J.in_plane + io + x4;
+                const float* __restrict__ p1 = J.I1 + c * J.in_plane + io + x4;
+                float v0[4], v1[4];
+                if (J.vec && nq == 4) {
+                    const float4 q0 = __ldg(reinterpret_cast<const float4*>(p0));
+                    const float4 q1 = __ldg(reinterpret_cast<const float4*>(p1));
+                    v0[0] = q0.x, v0[1] = q0.y, v0[2] = q0.z, v0[3] = q0.w;
+                    v1[0] = q1.x, v1[1] = q1.y, v1[2] = q1.z, v1[3] = q1.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        v0[q] = q < nq ? __ldg(p0 + q) : 0.0f;
+                        v1[q] = q < nq ? __ldg(p1 + q) : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v0[q] *= scale;
+                    v1[q] *= scale;
+                    a[q] += v0[q];
+                    b[q] += v1[q];
+                }
+                if (J.P0) {
+                    float* o0 = J.P0 + c * J.out_plane + oo + x4;
+                    float* o1 = J.P1 + c * J.out_plane + oo + x4;
+                    for (int q = 0; q < nq; ++q) {
+                        o0[q] = v0[q];
+                        o1[q] = v1[q];
+                    }
+                }
             }
-            a += v0;
-            b += v1;
+            float* s0 = J.S0 + oo + x4;
+            float* s1 = J.S1 + oo + x4;
+            if (nq == 4) {  // output rows start on 128-byte boundaries
+                reinterpret_cast<float4*>(s0)[0] = make_float4(a[0] * inv, a[1] * inv, a[2] * inv, a[3] * inv);
+                reinterpret_cast<float4*>(s1)[0] = make_float4(b[0] * inv, b[1] * inv, b[2] * inv, b[3] * inv);
+            } else {
+                for (int q = 0; q < nq; ++q) {
+                    s0[q] = a[q] * inv;
+                    s1[q] = b[q] * inv;
+                }
+            }
         }
-        const float inv = 1.0f / (float)J.C;
-        J.S0[oo] = a * inv;
-        J.S1[oo] = b * inv;
     }
 }
 
 // One pyramid step: out(x, y) = sum_{i,j} k_i k_j in(2x + i, 2y + j), k = [1 4 6 4 1] / 16,
-// indices clamped (replicated border).  Rows are blurred first, then the column.
-__global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ Jobs<PyrJob> js, long long total)
+// indices clamped (replicated border).  Rows are blurred first, then the column.  A block row
+// is one output row of one plane.
+__global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ Jobs<PyrJob> js, long long rows)
 {
-    for (long long g = gtid(); g < total; g += gstride()) {
-        const PyrJob& J = job_ref(js, find_job(js, g, &PyrJob::base));
-        const int k = (int)(g - J.base);  // < planes * w * h < 2^31
-        const int npix = J.wout * J.hout;
-        const int p = k / npix;
-        const int r = k - p * npix;
-        const int y = r / J.wout, x = r - y * J.wout;
-        const float* in = J.in + p * J.in_plane;
-        const int xs[5] = {clampi(2 * x - 2, 0, J.win - 1), clampi(2 * x - 1, 0, J.win - 1), min(2 * x, J.win - 1),
-                           clampi(2 * x + 1, 0, J.win - 1), clampi(2 * x + 2, 0, J.win - 1)};
-        const float kw[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
-        float acc = 0.0f;
+    const float kw[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const PyrJob& J = job_ref(js, find_job(js, r, &PyrJob::base));
+        const int rr = (int)(r - J.base);
+        const int p = rr / J.hout, y = rr - p * J.hout;
+        const float* __restrict__ in = J.in + p * J.in_plane;
+        const float* rowp[5];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            const float* row = in + (long long)clampi(2 * y + j - 2, 0, J.hin - 1) * J.pin;
-            float h = kw[0] * __ldg(row + xs[0]);
+        for (int j = 0; j < 5; ++j) rowp[j] = in + (long long)clampi(2 * y + j - 2, 0, J.hin - 1) * J.pin;
+        float* out = J.out + p * J.out_plane + (long long)y * J.pout;
+        const int win = J.win;
+#pragma unroll 2
+        for (int x = threadIdx.x; x < J.wout; x += blockDim.x) {
+            const int xs[5] = {clampi(2 * x - 2, 0, win - 1), clampi(2 * x - 1, 0, win - 1), min(2 * x, win - 1),
+                               clampi(2 * x + 1, 0, win - 1), clampi(2 * x + 2, 0, win - 1)};
+            float acc = 0.0f;
 #pragma unroll
-            for (int i = 1; i < 5; ++i) h = fmaf(kw[i], __ldg(row + xs[i]), h);
-            acc = fmaf(kw[j], h, acc);
+            for (int j = 0; j < 5; ++j) {
+                const float* row = rowp[j];
+                float h = kw[0] * __ldg(row + xs[0]);
+#pragma unroll
+                for (int i = 1; i < 5; ++i) h = fmaf(kw[i], __ldg(row + xs[i]), h);
+                acc = fmaf(kw[j], h, acc);
+            }
+            out[x] = acc;
         }
-        J.out[p * J.out_plane + (long long)y * J.pout + x] = acc;
     }
 }
 
@@ -79,16 +124,27 @@ __global__ void __launch_bounds__(256) sobel_kernel(const float* __restrict__ in
     }
 }
 
-// Uout(x) = factor * Uin(x / factor), bilinear with clamping (Sec. 3.1, last paragraph).
-__global__ void __launch_bounds__(256) upsample_kernel(const __grid_constant__ Jobs<UpJob> js, long long total)
+// Uout(x) = factor * Uin(x / factor), bilinear with clamping (Sec. 3.1, last paragraph).  A
+// block row is one output row.
+__global__ void __launch_bounds__(256) upsample_kernel(const __grid_constant__ Jobs<UpJob> js, long long rows)
 {
-    for (long long g = gtid(); g < total; g += gstride()) {
-        const UpJob& J = job_ref(js, find_job(js, g, &UpJob::base));
-        const int k = (int)(g - J.base);  // < w * h < 2^31
-        const int y = k / J.wo, x = k - y * J.wo;
-        const float2 v = sample_flow(J.in, J.wi, J.hi, (float)x / J.factor, (float)y / J.factor);
-        J.out[k] = make_float2(J.factor * v.x, J.factor * v.y);
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const UpJob& J = job_ref(js, find_job(js, r, &UpJob::base));
+        const int y = (int)(r - J.base);
+        float2* out = J.out + (long long)y * J.wo;
+        const float fy = (float)y / J.factor;
+#pragma unroll 4
+        for (int x = threadIdx.x; x < J.wo; x += blockDim.x) {
+            const float2 v = sample_flow(J.in, J.wi, J.hi, (float)x / J.factor, fy);
+            out[x] = make_float2(J.factor * v.x, J.factor * v.y);
+        }
     }
+}
+
+static int grid_rows(long long rows, const LaunchCfg& lc)
+{
+    const long long cap = (long long)lc.sm_count * lc.max_blocks_256;
+    return (int)(rows < 1 ? 1 : rows < cap ? rows : cap);
 }
 
 static int grid_for(long long total, int threads, const LaunchCfg& lc)
@@ -99,17 +155,17 @@ static int grid_for(long long total, int threads, const LaunchCfg& lc)
     return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_prep(const Jobs<PrepJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s)
+cudaError_t launch_prep(const Jobs<PrepJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s)
 {
-    if (total <= 0) return cudaSuccess;
-    prep_kernel<<<grid_for(total, 256, lc), 256, 0, s>>>(js, total);
+    if (rows <= 0) return cudaSuccess;
+    prep_kernel<<<grid_rows(rows, lc), 256, 0, s>>>(js, rows);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s)
+cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s)
 {
-    if (total <= 0) return cudaSuccess;
-    pyr_down_kernel<<<grid_for(total, 256, lc), 256, 0, s>>>(js, total);
+    if (rows <= 0) return cudaSuccess;
+    pyr_down_kernel<<<grid_rows(rows, lc), 256, 0, s>>>(js, rows);
     return cudaGetLastError();
 }
 
@@ -122,10 +178,10 @@ cudaError_t launch_sobel(const float* in, int w, int h, int pitch, float* gx, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_upsample(const Jobs<UpJob>& js, long long total, const LaunchCfg& lc, cudaStream_t s)
+cudaError_t launch_upsample(const Jobs<UpJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s)
 {
-    if (total <= 0) return cudaSuccess;
-    upsample_kernel<<<grid_for(total, 256, lc), 256, 0, s>>>(js, total);
+    if (rows <= 0) return cudaSuccess;
+    upsample_kernel<<<grid_rows(rows, lc), 256, 0, s>>>(js, rows);
     return cudaGetLastError();
 }
 
