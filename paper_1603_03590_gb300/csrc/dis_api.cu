@@ -307,9 +307,18 @@ dis_status build_plan(dis_handle* hd, const std::vector<PairIn>& pairs, const di
             J.in_plane = (long long)J.pin * J.hin;
             J.out_plane = (long long)J.pout * J.hout;
             J.nplanes = nplanes;
-            J.base = base;
-            base += (long long)nplanes * J.hout;
             t.push_back(J);
+        }
+        long long u8 = 0, u2 = 0;
+        for (const PyrJob& J : t) {
+            u8 += dis::pyr_units(J.wout, J.hout, J.nplanes, 8);
+            u2 += dis::pyr_units(J.wout, J.hout, J.nplanes, 2);
+        }
+        const int band = dis::pyr_band(u8, u2, hd->lc.sm_count);
+        for (PyrJob& J : t) {
+            J.band = band;
+            J.base = base;
+            base += dis::pyr_units(J.wout, J.hout, J.nplanes, band);
         }
         plan.phases.push_back({Phase::PYR, push_table(plan.blob, t), (int)t.size(), base, 0, 0, s});
     }
@@ -1106,7 +1115,10 @@ dis_status dis_pyr_down(const float* in, int w, int h, int64_t in_pitch, float* 
     J.hout = (h + 1) / 2;
     J.pout = (int)out_pitch;
     J.nplanes = 1;
-    cudaError_t e = dis::launch_pyr_down(dis::single_job(J), J.hout, stage_lc(), (cudaStream_t)stream);
+    const dis::LaunchCfg lc = stage_lc();
+    J.band = dis::pyr_band(dis::pyr_units(J.wout, J.hout, 1, 8), dis::pyr_units(J.wout, J.hout, 1, 2), lc.sm_count);
+    cudaError_t e = dis::launch_pyr_down(dis::single_job(J), dis::pyr_units(J.wout, J.hout, 1, J.band), lc,
+                                         (cudaStream_t)stream);
     return e == cudaSuccess ? DIS_OK : cuda_fail(nullptr, e, "dis_pyr_down");
 }
 

@@ -56,8 +56,9 @@ struct PyrJob {
     const float* in;
     float* out;
     long long in_plane, out_plane;
-    long long base;  // first flattened (plane, output row) of the job
+    long long base;  // first flattened work unit of the job (pyr_units: plane, band, column chunk)
     int win, hin, pin, wout, hout, pout, nplanes;
+    int band;  // output rows per work unit (pyr_band)
 };
 
 // Level-0 preparation: scale the caller's frames, form the channel mean.
@@ -138,7 +139,11 @@ struct LaunchCfg {
 
 // Launchers (return the launch error).  `total` = number of flattened items.
 cudaError_t launch_prep(const Jobs<PrepJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s);
-cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long units, const LaunchCfg& lc, cudaStream_t s);
+// Work units of a pyramid job: its planes x bands of `band` output rows x chunks of output
+// columns; and the band height for a call (8, 2 or 1) from its unit counts at band 8 and 2.
+long long pyr_units(int wout, int hout, int nplanes, int band);
+int pyr_band(long long units_at_full_band, long long units_at_band2, int sm_count);
 cudaError_t launch_sobel(const float* in, int w, int h, int pitch, float* gx, float* gy, int out_pitch,
                          const LaunchCfg& lc, cudaStream_t s);
 // lanes: lanes per patch (0 or 1 = the lane-per-patch form; see search_lane_options).  planes:

@@ -5,10 +5,10 @@
 
 namespace dis {
 
-// Work split of the batched kernels below: one output row per block iteration.  The job of the
-// row is found once (a search over the jobs' first rows, `base`), not once per pixel, and the
-// block's threads cover the row with several pixels per thread in flight (four consecutive
-// pixels per step in prep_kernel, unrolled steps in the others).
+// Work split of the batched kernels below: one output row (preparation, up-scaling) or one band
+// of output rows (pyramid) per block iteration.  The job is found once per row or band (a
+// search over the jobs' first units, `base`), not once per pixel, and the block's threads cover
+// the row with several pixels per thread in flight.
 
 // Level 0: multiply the caller's [0,1] frames by intensity_scale, write the channel mean
 // (the search image) and, for colour input, the scaled channel planes.
@@ -71,37 +71,82 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ Jobs<
 }
 
 // One pyramid step: out(x, y) = sum_{i,j} k_i k_j in(2x + i, 2y + j), k = [1 4 6 4 1] / 16,
-// indices clamped (replicated border).  Rows are blurred first, then the column.  A block row
-// is one output row of one plane.
-__global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ Jobs<PyrJob> js, long long rows)
+// indices clamped (replicated border).  Rows are blurred first, then the column.  A block
+// iteration is a band of J.band (<= kPyrBand) output rows by kPyrChunk output columns of one
+// plane: the horizontal blurs of the band's 2 band + 3 input rows are computed once into
+// shared memory (an input row serves up to three output rows), then every output sums five of
+// them, in the same order as a per-pixel evaluation.  The host picks the band height per call:
+// the tallest band that still gives every SM several units.
+constexpr int kPyrBand = 8, kPyrChunk = 256;
+
+__global__ void __launch_bounds__(kPyrChunk) pyr_down_kernel(const __grid_constant__ Jobs<PyrJob> js, long long units)
 {
+    __shared__ float hb[2 * kPyrBand + 3][kPyrChunk];
     const float kw[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
-    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-        const PyrJob& J = job_ref(js, find_job(js, r, &PyrJob::base));
-        const int rr = (int)(r - J.base);
-        const int p = rr / J.hout, y = rr - p * J.hout;
+    const int xx = threadIdx.x;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const PyrJob& J = job_ref(js, find_job(js, u, &PyrJob::base));
+        const int bh = J.band;
+        const int bands = (J.hout + bh - 1) / bh, chunks = (J.wout + kPyrChunk - 1) / kPyrChunk;
+        const int rr = (int)(u - J.base);
+        const int p = rr / (bands * chunks), rem = rr - p * (bands * chunks);
+        const int band = rem / chunks, cx = rem - band * chunks;
+        const int y0 = band * bh, ny = min(bh, J.hout - y0);
+        const int x = cx * kPyrChunk + xx;
+        const bool on = x < J.wout;
         const float* __restrict__ in = J.in + p * J.in_plane;
-        const float* rowp[5];
-#pragma unroll
-        for (int j = 0; j < 5; ++j) rowp[j] = in + (long long)clampi(2 * y + j - 2, 0, J.hin - 1) * J.pin;
-        float* out = J.out + p * J.out_plane + (long long)y * J.pout;
         const int win = J.win;
-#pragma unroll 2
-        for (int x = threadIdx.x; x < J.wout; x += blockDim.x) {
+        if (bh == 1) {  // one output row: its five input rows' blurs are used once, no staging
+            if (on) {
+                const int xs[5] = {clampi(2 * x - 2, 0, win - 1), clampi(2 * x - 1, 0, win - 1), min(2 * x, win - 1),
+                                   clampi(2 * x + 1, 0, win - 1), clampi(2 * x + 2, 0, win - 1)};
+                float acc = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const float* row = in + (long long)clampi(2 * y0 + j - 2, 0, J.hin - 1) * J.pin;
+                    float h = kw[0] * __ldg(row + xs[0]);
+#pragma unroll
+                    for (int i = 1; i < 5; ++i) h = fmaf(kw[i], __ldg(row + xs[i]), h);
+                    acc = fmaf(kw[j], h, acc);
+                }
+                J.out[p * J.out_plane + (long long)y0 * J.pout + x] = acc;
+            }
+            continue;  // uniform over the block: no barrier is skipped by part of it
+        }
+        if (on) {
             const int xs[5] = {clampi(2 * x - 2, 0, win - 1), clampi(2 * x - 1, 0, win - 1), min(2 * x, win - 1),
                                clampi(2 * x + 1, 0, win - 1), clampi(2 * x + 2, 0, win - 1)};
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                const float* row = rowp[j];
+            for (int jr = 0; jr < 2 * ny + 3; ++jr) {
+                const float* row = in + (long long)clampi(2 * y0 - 2 + jr, 0, J.hin - 1) * J.pin;
                 float h = kw[0] * __ldg(row + xs[0]);
 #pragma unroll
                 for (int i = 1; i < 5; ++i) h = fmaf(kw[i], __ldg(row + xs[i]), h);
-                acc = fmaf(kw[j], h, acc);
+                hb[jr][xx] = h;
             }
-            out[x] = acc;
         }
+        __syncthreads();
+        if (on) {
+            float* out = J.out + p * J.out_plane + (long long)y0 * J.pout + x;
+            for (int yy = 0; yy < ny; ++yy) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 5; ++j) acc = fmaf(kw[j], hb[2 * yy + j][xx], acc);
+                out[(long long)yy * J.pout] = acc;
+            }
+        }
+        __syncthreads();  // hb is refilled by the next band
     }
+}
+
+long long pyr_units(int wout, int hout, int nplanes, int band)
+{
+    return (long long)nplanes * ((hout + band - 1) / band) * ((wout + kPyrChunk - 1) / kPyrChunk);
+}
+
+int pyr_band(long long units_at_full_band, long long units_at_band2, int sm_count)
+{
+    const long long want = 4LL * sm_count;  // units that keep every SM busy for a few rounds
+    return units_at_full_band >= want ? kPyrBand : units_at_band2 >= want ? 2 : 1;
 }
 
 // Sobel / 8 with replicated border (standalone form of the operator the search computes in
@@ -162,10 +207,10 @@ cudaError_t launch_prep(const Jobs<PrepJob>& js, long long rows, const LaunchCfg
     return cudaGetLastError();
 }
 
-cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long rows, const LaunchCfg& lc, cudaStream_t s)
+cudaError_t launch_pyr_down(const Jobs<PyrJob>& js, long long units, const LaunchCfg& lc, cudaStream_t s)
 {
-    if (rows <= 0) return cudaSuccess;
-    pyr_down_kernel<<<grid_rows(rows, lc), 256, 0, s>>>(js, rows);
+    if (units <= 0) return cudaSuccess;
+    pyr_down_kernel<<<grid_rows(units, lc), kPyrChunk, 0, s>>>(js, units);
     return cudaGetLastError();
 }
 
