@@ -99,7 +99,7 @@ WORKLOADS = {
 # of the launch is read once, so it grows with the pairs), by (workload, preset, search variant),
 # with the summary that holds the capture.
 TRAFFIC = {
-    ("flow", "dense", 16): (17.82e6 / 4, "profiles/search_kernel_dense1024x436_ncu.md (4-pair launch)"),
+    ("flow", "dense", 16): (17.83e6 / 4, "profiles/search_kernel_dense1024x436_ncu.md (4-pair launch)"),
 }
 
 
